@@ -1,0 +1,194 @@
+"""ctypes front end of the FP64 oracle (test infrastructure only).
+
+Each function wraps one entry point of trd_oracle.c; see that file for the
+passage of the paper each one follows.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+_d = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_f = np.ctypeslib.ndpointer(dtype=np.float32, flags="C_CONTIGUOUS")
+_i = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+STATUS_PROP_FAIL, STATUS_STOPPED, STATUS_SEED_INVALID = 1, 2, 4
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        L.ora_propagate.argtypes = [_d, _d, C.c_double, C.c_double, C.c_void_p, C.c_void_p]
+        L.ora_propagate.restype = C.c_int
+        L.ora_rotate.argtypes = [_d, _d, C.c_double, C.c_double, C.c_void_p, C.c_void_p]
+        L.ora_rotate.restype = C.c_int
+        L.ora_material.argtypes = [_d, _d]
+        L.ora_material.restype = C.c_int
+        L.ora_bethe.argtypes = [C.c_double]
+        L.ora_bethe.restype = C.c_double
+        L.ora_highland.argtypes = [C.c_double, C.c_double, C.c_double]
+        L.ora_highland.restype = C.c_double
+        L.ora_update.argtypes = [_d, _d, C.c_int, _d, C.c_int]
+        L.ora_update.restype = C.c_double
+        L.ora_chi2.argtypes = [_d, _d, C.c_int, _d]
+        L.ora_chi2.restype = C.c_double
+        L.ora_cov_is_pd.argtypes = [_d]
+        L.ora_cov_is_pd.restype = C.c_int
+        L.ora_constants.argtypes = [_d, C.c_int]
+        L.ora_constants.restype = None
+        L.ora_follow.restype = C.c_int
+        L.ora_to_layer.argtypes = [_d, _d, C.c_void_p, C.c_int, _d, _i, C.c_void_p]
+        L.ora_to_layer.restype = C.c_int
+        L.ora_candidates.argtypes = [_d, _d, C.c_int, C.c_int, C.c_int, _i, _f, _f, _f, _f, _f,
+                                     _f, _d, _i, C.c_int, _i, _d]
+        L.ora_candidates.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _vec(a, n):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64).copy())
+    assert a.shape == (n,)
+    return a
+
+
+def propagate(st, cov, x_to, bz, with_cov=True):
+    """Helix transport to radius x_to.  Returns (ok, st, cov, J[5,5])."""
+    s, c = _vec(st, 7), _vec(cov, 15)
+    J = np.zeros(25)
+    ok = lib().ora_propagate(s, c, float(x_to), float(bz), J.ctypes.data, None) == 0
+    return ok, s, c, J.reshape(5, 5)
+
+
+def rotate(st, cov, alpha_new, bz):
+    """Rotation into the frame of azimuth alpha_new.  Returns (ok, st, cov, J)."""
+    s, c = _vec(st, 7), _vec(cov, 15)
+    J = np.zeros(25)
+    ok = lib().ora_rotate(s, c, float(alpha_new), float(bz), J.ctypes.data, None) == 0
+    return ok, s, c, J.reshape(5, 5)
+
+
+def material(st, cov):
+    s, c = _vec(st, 7), _vec(cov, 15)
+    ok = lib().ora_material(s, c) == 0
+    return ok, s, c
+
+
+def bethe(bg: float) -> float:
+    return lib().ora_bethe(float(bg))
+
+
+def highland(p: float, beta: float, xx0: float) -> float:
+    return lib().ora_highland(float(p), float(beta), float(xx0))
+
+
+def update(st, cov, layer, meas, joseph=False):
+    """Kalman update with meas = (y_tl, z_tl, vyy, vzz, vyz).  Returns (chi2, st, cov)."""
+    s, c = _vec(st, 7), _vec(cov, 15)
+    chi2 = lib().ora_update(s, c, int(layer), _vec(meas, 5), int(bool(joseph)))
+    return chi2, s, c
+
+
+def chi2(st, cov, layer, meas):
+    return lib().ora_chi2(_vec(st, 7), _vec(cov, 15), int(layer), _vec(meas, 5))
+
+
+def cov_is_pd(cov) -> bool:
+    return bool(lib().ora_cov_is_pd(_vec(cov, 15)))
+
+
+def constants() -> dict:
+    names = ["n_sectors", "n_stacks", "n_layers", "n_chambers", "x_layer0", "dx_layer",
+             "stack_length", "z_min", "tilt_deg", "drift_length", "lorentz_deg", "c_light",
+             "max_snp"]
+    out = np.zeros(len(names))
+    lib().ora_constants(out, len(names))
+    return dict(zip(names, out.tolist()))
+
+
+def _f32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+
+
+def follow(seeds: dict, tracklets: dict, params: dict, seed_index=None, brute=False,
+           n_threads=0) -> dict:
+    """Run the FP64 follower.  seeds/tracklets are the FP32 input arrays
+    (the same ones the library reads).  Returns numpy arrays keyed like the
+    library's results, plus 'margin' [6, n] and 'nroad' [6, n]."""
+    L = lib()
+    n = int(seeds["alpha"].shape[0])
+    m = int(tracklets["chamber"].shape[0])
+    if seed_index is None:
+        n_out, sidx = n, None
+    else:
+        sidx = np.ascontiguousarray(np.asarray(seed_index, dtype=np.int32))
+        n_out = int(sidx.shape[0])
+    cov = _f32(seeds["cov"]).reshape(15, n)
+    pd = np.array([params["bz"], params["n_sigma_road"], params["chi2_cut"], params["p_miss"],
+                   params["dy_gate_sigma"]], dtype=np.float64)
+    pi = np.array([params["n_hyp"], params["max_missing"], params["res_mode"],
+                   params["material_on"]], dtype=np.int32)
+    st = np.zeros((7, n_out))
+    cv = np.zeros((15, n_out))
+    chi2_ = np.zeros(n_out)
+    ntrk = np.zeros(n_out, np.int32)
+    nmiss = np.zeros(n_out, np.int32)
+    status = np.zeros(n_out, np.int32)
+    ids = np.zeros((6, n_out), np.int32)
+    margin = np.zeros((6, n_out))
+    nroad = np.zeros((6, n_out), np.int32)
+    keep = [_f32(seeds[k]) for k in ("alpha", "x", "y", "z", "snp", "tgl", "q2pt")]
+    tk = [np.ascontiguousarray(np.asarray(tracklets["chamber"], dtype=np.int32))] + [
+        _f32(tracklets[k]) for k in ("y", "z", "dy", "vyy", "vzz", "vyz")]
+    args = [C.c_int(n)] + [a.ctypes.data_as(C.c_void_p) for a in keep] + [
+        cov.ctypes.data_as(C.c_void_p), C.c_int(m)] + [a.ctypes.data_as(C.c_void_p) for a in tk] + [
+        pd.ctypes.data_as(C.c_void_p), pi.ctypes.data_as(C.c_void_p), C.c_int(n_out),
+        sidx.ctypes.data_as(C.c_void_p) if sidx is not None else None, C.c_int(int(brute)),
+        C.c_int(n_threads)] + [a.ctypes.data_as(C.c_void_p) for a in
+                               (st, cv, chi2_, ntrk, nmiss, status, ids, margin, nroad)]
+    rc = L.ora_follow(*args)
+    if rc != 0:
+        raise ValueError(f"ora_follow rejected its arguments ({rc})")
+    return dict(alpha=st[0], x=st[1], par=st[2:7], cov=cv, chi2=chi2_, n_trk=ntrk,
+                n_miss=nmiss, status=status, tracklet_id=ids, margin=margin, nroad=nroad)
+
+
+def to_layer(st, cov, sector, layer, params):
+    """Carry a state to the plane of `layer` (transport, sector change,
+    material).  Returns (ok, st, cov, sector, chamber)."""
+    s, c = _vec(st, 7), _vec(cov, 15)
+    sec = C.c_int(int(sector))
+    ch = C.c_int(-1)
+    pd, pi = _params_arrays(params)
+    ok = lib().ora_to_layer(s, c, C.byref(sec), int(layer), pd, pi, C.byref(ch)) == 0
+    return ok, s, c, sec.value, ch.value
+
+
+def candidates(st, cov, layer, chamber, tracklets, params, max_out=4096):
+    """Accepted tracklets (input ids, chi2) of `chamber` for a state at `layer`."""
+    tk = [np.ascontiguousarray(np.asarray(tracklets["chamber"], dtype=np.int32))] + [
+        _f32(tracklets[k]) for k in ("y", "z", "dy", "vyy", "vzz", "vyz")]
+    pd, pi = _params_arrays(params)
+    ids = np.zeros(max_out, np.int32)
+    ch2 = np.zeros(max_out)
+    n = lib().ora_candidates(_vec(st, 7), _vec(cov, 15), int(layer), int(chamber),
+                             int(tk[0].shape[0]), *tk, pd, pi, max_out, ids, ch2)
+    n = min(n, max_out)
+    return ids[:n].copy(), ch2[:n].copy()
+
+
+def _params_arrays(params):
+    pd = np.array([params["bz"], params["n_sigma_road"], params["chi2_cut"], params["p_miss"],
+                   params["dy_gate_sigma"]], dtype=np.float64)
+    pi = np.array([params["n_hyp"], params["max_missing"], params["res_mode"],
+                   params["material_on"]], dtype=np.int32)
+    return pd, pi
+
+
+__all__ = ["propagate", "rotate", "material", "bethe", "highland", "update", "chi2",
+           "cov_is_pd", "constants", "follow", "to_layer", "candidates", "lib"]
