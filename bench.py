@@ -1,0 +1,326 @@
+#!/usr/bin/env python3
+"""Benchmark of the TRD tracklet follower (arXiv:2003.03174, Sec. 3) on B300.
+
+One step = one pass of the whole hot path over one synthetic Run-3-like
+timeframe (200,000 seeds, ~1M tracklets, N = 1, 3-sigma road, chi2 < 15, at
+most 2 missing layers): rebuild the resident tracklet index, then follow every
+seed through the 6 layers.  The metric is TRD-matched tracks per second
+(tracks that end with >= 2 attached tracklets, Sec. 3.1).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank follows its own timeframe (independent seeds, no
+collective on the data path: weak scaling); rank 0 prints one JSON line.
+`--impl reference` times the FP64 oracle on the host cores on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "TRD-matched tracks/s on 1 B300 (FP32 vs FP64 oracle); served timeframe p50/p99"
+UNIT = "matched tracks/s"
+WORKLOAD = "timeframe"
+# Algorithmic bytes of the follower per seed: the seed (22 floats) read once,
+# the result (23 floats + 9 int32) written once, and the tracklet records
+# (two float4 rows) that lie inside the road, averaged over the timeframe
+# workload (mean in-road tracklets per seed measured by the oracle on a
+# sample: see the design doc).
+SEED_BYTES = 88
+RESULT_BYTES = 128
+RECORD_BYTES = 32
+IN_ROAD_PER_SEED = 15.75
+FOLLOW_BYTES_PER_SEED = SEED_BYTES + RESULT_BYTES + RECORD_BYTES * IN_ROAD_PER_SEED
+L2_FLUSH_BYTES = 512 << 20
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), power=float(parts[3]),
+                                 hw=parts[5], hwt=parts[6], swt=parts[7], pcap=parts[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("pcap", "sw_power_cap")):
+                if r[key].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows),
+                "sm_max_mhz": max(r["smax"] for r in rows), "reasons": sorted(reasons),
+                "samples": len(rows), "power_w_max": max(r["power"] for r in rows)}
+
+
+def cpu_baseline(tf, sample_seeds: int, reps: int = 1):
+    """The FP64 oracle, as it stands, on the host cores over a bounded sample."""
+    from oracle import oracle as O
+    n = tf.n_seeds
+    sel = np.arange(0, n, max(1, n // sample_seeds))[:sample_seeds].astype(np.int32)
+    O.follow(tf.seeds, tf.tracklets, tf.params, seed_index=sel[:64])  # load + warm
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        r = O.follow(tf.seeds, tf.tracklets, tf.params, seed_index=sel)
+    dt = (time.perf_counter() - t0) / reps
+    matched = int((r["n_trk"] >= 2).sum())
+    return dict(value=matched / dt, unit=UNIT, cores=os.cpu_count(), kind="oracle",
+                sample=f"{len(sel)} of {n} seeds (every {n // len(sel)}th) against all "
+                       f"{tf.n_tracklets} tracklets; chamber bucketing included; {dt:.2f} s",
+                seconds=dt, seeds=len(sel), matched=matched)
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    from synth import make_workload
+    tf = make_workload(WORKLOAD, seed=0)
+    sample = args.ref_sample
+    times, matched = [], 0
+    for _ in range(args.warmup):
+        cpu_baseline(tf, min(sample, 512))
+    for _ in range(args.steps):
+        cb = cpu_baseline(tf, sample)
+        times.append(cb["seconds"])
+        matched = cb["matched"]
+    total = sum(times)
+    value = matched * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD}: 200000 seeds, ~1M tracklets, N=1, 3-sigma road, "
+                               f"chi2<15, <=2 missing", "sample_seeds": sample,
+                   "l2": "host run (no GPU)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": f"{sample} seeds of 200000 per step against all tracklets"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    from paper_2003_03174_b300 import trd
+    from synth import make_workload
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ctx = trd.Context(local)
+
+    tf = make_workload(WORKLOAD, seed=rank)  # each rank: its own timeframe
+    seeds = trd.to_device(tf.seeds, dev)
+    trk = trd.to_device(tf.tracklets, dev)
+    n = tf.n_seeds
+    stream = torch.cuda.Stream(device=dev)
+    index = ctx.index_create(tf.n_tracklets, args.bin_width)
+    res = trd.alloc_results(n, dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        index.rebuild(trk, stream=stream)
+        ctx.follow(seeds, index, tf.params, results=res, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize()
+    matched = int((res["n_trk"] >= 2).sum().item())
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                flush.add_(1.0)  # write 512 MB: evict L2 between timed steps
+                ev[k][0].record(stream)
+                index.rebuild(trk, stream=stream)
+                ev[k][1].record(stream)
+                ctx.follow(seeds, index, tf.params, results=res, stream=stream)
+                ev[k][2].record(stream)
+        torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    step_ms = [a.elapsed_time(c) for a, _, c in ev]
+    follow_ms = [b.elapsed_time(c) for _, b, c in ev]
+    index_ms = [a.elapsed_time(b) for a, b, _ in ev]
+    total_s = sum(step_ms) / 1e3
+    if ws > 1:
+        t = torch.tensor([total_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+        m = torch.tensor([matched], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(m)
+        matched_all = float(m.item())
+    else:
+        matched_all = float(matched)
+    value = matched_all * args.steps / total_s
+
+    # end to end: pinned host inputs -> device, index + follow, results -> host
+    host_in = {k: torch.from_numpy(v).pin_memory() for k, v in tf.seeds.items()}
+    host_trk = {k: torch.from_numpy(v).pin_memory() for k, v in tf.tracklets.items()}
+    host_out = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in res.items()}
+    h2d = sum(v.numel() * v.element_size() for v in list(host_in.values()) + list(host_trk.values()))
+    d2h = sum(v.numel() * v.element_size() for v in host_out.values())
+    dev_in = {k: torch.empty_like(v, device=dev) for k, v in host_in.items()}
+    dev_trk = {k: torch.empty_like(v, device=dev) for k, v in host_trk.items()}
+    e_steps = max(3, args.steps // 2)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        for it in range(e_steps + 1):
+            if it == 1:
+                e0.record(stream)
+            for k, v in host_in.items():
+                dev_in[k].copy_(v, non_blocking=True)
+            for k, v in host_trk.items():
+                dev_trk[k].copy_(v, non_blocking=True)
+            index.rebuild(dev_trk, stream=stream)
+            ctx.follow(dev_in, index, tf.params, results=res, stream=stream)
+            for k, v in res.items():
+                host_out[k].copy_(v, non_blocking=True)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_s = e0.elapsed_time(e1) / 1e3
+    e2e_matched = int((host_out["n_trk"] >= 2).sum().item())
+    e2e_value = e2e_matched * ws * e_steps / e2e_s
+
+    peaks = _peaks()
+    hbm = peaks.get("hbm_gbs")
+    follow_avg_s = statistics.mean(follow_ms) / 1e3
+    achieved = n * FOLLOW_BYTES_PER_SEED / follow_avg_s / 1e9
+    roof = {"bound": "hbm", "kernel": "k_follow<1,1>", "achieved": achieved,
+            "peak": hbm if hbm else 6400.0, "unit": "GB/s",
+            "peak_source": "measured" if hbm else "fallback",
+            "frac": achieved / (hbm if hbm else 6400.0), "traffic": None,
+            "algorithmic_bytes_per_launch": n * FOLLOW_BYTES_PER_SEED,
+            "follow_ms": statistics.mean(follow_ms), "index_ms": statistics.mean(index_ms)}
+    launches_per_step = 6  # count, 3 scan kernels, scatter, follow
+    clocks = clk.summary()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded Pb-Pb-like timeframe: truth helices, 90% efficient "
+                    "tracklets, 30% noise)",
+            "config": {"workload": f"{WORKLOAD}: {n} seeds, {tf.n_tracklets} tracklets per rank, "
+                                   f"N=1, 3-sigma road, chi2<15, <=2 missing",
+                       "seeds_per_rank": n, "tracklets_per_rank": tf.n_tracklets,
+                       "matched_per_rank_step": matched, "l2": "flushed (512 MB write) between steps",
+                       "index_y_bin_cm": args.bin_width or 2.0,
+                       "parallelism": f"replicas x{ws} (independent timeframes)"},
+            "roofline": roof,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h),
+                    "path": "pinned host -> cudaMemcpyAsync -> trd_index_rebuild + trd_follow -> host"},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clocks,
+            "seeds_per_s": n * ws * args.steps / total_s,
+        }
+        if ws == 1 and not args.no_cpu_baseline:
+            cb = cpu_baseline(tf, args.cpu_sample)
+            line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--bin-width", type=float, default=0.0)
+    ap.add_argument("--cpu-sample", type=int, default=40_000)
+    ap.add_argument("--ref-sample", type=int, default=20_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    return run_reference(args) if args.impl == "reference" else run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,192 @@
+/*
+ * trd_abi.h -- C ABI of the B300 TRD tracklet follower (libtrd.so).
+ *
+ * The library matches extrapolated ITS-TPC seed tracks to TRD tracklets with
+ * a Kalman filter that keeps the best N hypotheses per layer (arXiv:2003.03174,
+ * Sec. 3 and Fig. 2).  All compute runs in hand-written FP32 CUDA kernels for
+ * sm_103a; there is no CPU fallback: every entry point that needs the GPU
+ * returns TRD_ECUDA when no usable device is present.
+ *
+ * Conventions used by every call:
+ *   - Return value: TRD_OK (0) or a negative TRD_E* code.  No call aborts the
+ *     process or leaves a CUDA error pending on success.
+ *   - Units: cm, GeV/c, Tesla.  Angles in radians.
+ *   - Track state in the local frame of a sector: alpha (azimuth of the frame),
+ *     x (radius of the reference plane), and five parameters
+ *     p = (y, z, snp = sin(phi), tgl = tan(lambda), q2pt = q/pT).
+ *   - Covariance: 15 terms, lower triangle row by row:
+ *     c00 c10 c11 c20 c21 c22 c30 c31 c32 c33 c40 c41 c42 c43 c44.
+ *   - Arrays are structure-of-arrays, FP32 unless stated.  A "[k][n]" array is
+ *     k rows of n contiguous values (row r of track i at r*n + i).
+ *   - Geometry: 18 sectors x 5 stacks x 6 layers (Sec. 3); chamber id =
+ *     sector*30 + stack*6 + layer in 0..539; layer planes at x = 300 + 12.6 l;
+ *     sector s centred at alpha = (s + 0.5) * 20 degrees; stacks of 18 pad rows
+ *     of 8 cm covering z in [-360, 360); pads tilted by +2 degrees on even and
+ *     -2 degrees on odd layers.
+ *   - Streams: `stream` arguments are cudaStream_t values passed as void*;
+ *     NULL means the legacy default stream.  Calls that take a stream are
+ *     asynchronous with respect to the host unless stated.
+ */
+#ifndef TRD_ABI_H
+#define TRD_ABI_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define TRD_API __attribute__((visibility("default")))
+#else
+#define TRD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes -------------------------------------------------------- */
+#define TRD_OK 0
+#define TRD_EINVAL (-1)   /* invalid argument (null pointer, bad size, bad parameter) */
+#define TRD_ENOMEM (-2)   /* device or pinned host allocation failed */
+#define TRD_EAGAIN (-3)   /* resource temporarily full, or result not ready yet */
+#define TRD_ETIMEOUT (-4) /* a bounded device wait ran out */
+#define TRD_ECUDA (-5)    /* a CUDA runtime call failed (no device, launch error, ...) */
+
+/* ---- per-track status bits (trd_results_t.status) ----------------------- */
+#define TRD_ST_OK 0           /* followed through all 6 layers */
+#define TRD_ST_PROP_FAIL 1    /* every hypothesis failed transport (|snp| >= 0.95) at some layer */
+#define TRD_ST_STOPPED 2      /* no extension left: missing-layer budget spent, no candidate */
+#define TRD_ST_SEED_INVALID 4 /* seed |snp| >= 0.95 or covariance not positive definite */
+
+#define TRD_N_LAYERS 6
+#define TRD_N_CHAMBERS 540
+#define TRD_MAX_HYP 8 /* largest N (hypotheses kept per layer) the kernels support */
+
+typedef struct trd_ctx trd_ctx_t;
+typedef struct trd_index trd_index_t;
+
+/* Seeds: ITS-TPC tracks extrapolated towards the TRD (Sec. 3), in any frame
+ * alpha.  Device pointers, each n floats; cov is [15][n].  Read only.      */
+typedef struct {
+    const float *alpha, *x, *y, *z, *snp, *tgl, *q2pt;
+    const float *cov;
+    int32_t n;
+} trd_seeds_t;
+
+/* Tracklets: the FEE straight-line fits of Sec. 3 (local y at the chamber's
+ * reference radius, z of the pad row, deflection dy over the 3 cm drift), with
+ * their 2x2 covariance (vyy, vzz, vyz).  chamber in 0..539; tracklets with a
+ * chamber id outside that range, a non-finite y/z/dy, or a negative variance
+ * are left out of the index and counted (trd_index_info).  Device pointers,
+ * each n entries.  Read only.                                               */
+typedef struct {
+    const int32_t *chamber;
+    const float *y, *z, *dy, *vyy, *vzz, *vyz;
+    int32_t n;
+} trd_tracklets_t;
+
+/* Follower parameters.
+ *   bz            solenoid field (T); the Lorentz angle sign follows it (Fig. 3)
+ *   n_sigma_road  half-width of the search road in sigma of the residual (Sec. 3)
+ *   chi2_cut      a candidate needs chi2 (y and z only, 2 dof) below this (Sec. 3)
+ *   p_miss        score penalty of a layer without a tracklet
+ *   dy_gate_sigma deflection deviation allowed, in sigma (4 in Sec. 3)
+ *   n_hyp         hypotheses kept per layer, N_candidates of Sec. 3 (1..TRD_MAX_HYP)
+ *   max_missing   layers a hypothesis may skip
+ *   res_mode      0: tracklet y variance from the input; 1: from the resolution
+ *                 parametrisation in sin(phi) of the track (Sec. 3, Fig. 3)
+ *   material_on   1: one material step (scattering + energy loss) per layer  */
+typedef struct {
+    float bz, n_sigma_road, chi2_cut, p_miss, dy_gate_sigma;
+    int32_t n_hyp, max_missing, res_mode, material_on;
+} trd_params_t;
+
+/* Results: device pointers written by trd_follow, caller-owned.
+ *   alpha, x [n]; par [5][n]; cov [15][n]; chi2 [n] (sum of the attached
+ *   tracklets' chi2); n_trk, n_miss, status [n] (int32); tracklet_id [6][n]
+ *   (int32, index into the caller's tracklet arrays, -1 = no tracklet).
+ * The state is the best hypothesis after its last completed layer.         */
+typedef struct {
+    float *alpha, *x, *par, *cov, *chi2;
+    int32_t *n_trk, *n_miss, *status, *tracklet_id;
+} trd_results_t;
+
+/* ---- context ---------------------------------------------------------------
+ * trd_ctx_create: bind to CUDA device `device` (makes it current on the calling
+ * thread) and read its properties.  *ctx is owned by the caller and released
+ * with trd_ctx_destroy.  Errors: TRD_EINVAL (ctx NULL), TRD_ECUDA (no such
+ * device, or the device is not sm_103), TRD_ENOMEM.                         */
+TRD_API int trd_ctx_create(int device, trd_ctx_t **ctx);
+TRD_API int trd_ctx_destroy(trd_ctx_t *ctx);
+
+/* Number of SMs of the context's device (for sizing), or a negative code. */
+TRD_API int trd_ctx_sm_count(const trd_ctx_t *ctx);
+
+/* ---- tracklet index (Sec. 3: "all tracklets inside a search road") --------
+ * trd_index_build: bucket the tracklets by (chamber, pad row, y bin) with a
+ * counting sort on `stream`, and record each chamber's largest vyy and vzz.
+ * Buckets of one (chamber, pad row) are contiguous in y, so a road query is
+ * one contiguous range per pad row.  y_bin_width (cm, > 0; 0 selects 2 cm)
+ * sets the bin size.  The library allocates and owns the index (*out, freed
+ * by trd_index_free); the input arrays may be reused once `stream` has passed
+ * the build.  Errors: TRD_EINVAL, TRD_ENOMEM, TRD_ECUDA.                     */
+TRD_API int trd_index_build(trd_ctx_t *ctx, const trd_tracklets_t *tracklets, float y_bin_width,
+                    void *stream, trd_index_t **out);
+TRD_API int trd_index_free(trd_index_t *index);
+
+/* Resident-index pattern for repeated timeframes: trd_index_create allocates
+ * an index for up to `capacity` tracklets (library-owned, freed by
+ * trd_index_free); trd_index_rebuild refills it from new tracklets on
+ * `stream` without allocating (TRD_EINVAL if n > capacity).  Work that still
+ * reads the previous contents must be ordered before the rebuild on the
+ * caller's streams.                                                         */
+TRD_API int trd_index_create(trd_ctx_t *ctx, int32_t capacity, float y_bin_width, trd_index_t **out);
+TRD_API int trd_index_rebuild(trd_index_t *index, const trd_tracklets_t *tracklets, void *stream);
+
+/* Synchronises with the index's build stream, then reports the number of
+ * tracklets indexed and the number rejected as invalid.                     */
+TRD_API int trd_index_info(const trd_index_t *index, int32_t *n_indexed, int32_t *n_rejected,
+                   int32_t *n_buckets);
+
+/* Copies the index to host memory (synchronises with its build stream), for
+ * inspection and tests.  offsets: n_buckets + 1 int32 (bucket b holds
+ * entries offsets[b] .. offsets[b+1]-1; bucket = (chamber*18 + pad row) *
+ * n_ybins + y bin); ids: n_indexed int32 input indices in bucket order.
+ * Either pointer may be NULL.  Host pointers, caller-owned.                 */
+TRD_API int trd_index_copy_out(const trd_index_t *index, int32_t *offsets, int32_t *ids);
+
+/* ---- the follower (Sec. 3) -------------------------------------------------
+ * trd_follow: for every seed, rotate it into the sector of its position,
+ * then for layers 0..5: transport the helix and covariance to the layer plane
+ * (changing sector at the edge), apply the material step, query the index
+ * inside the n-sigma road, test each candidate (pad-tilt-corrected chi2 of y
+ * and z, dy gate), keep the best n_hyp extensions (a layer may be skipped
+ * while max_missing allows), and update with the chosen tracklet.  Selection
+ * order: lowest score (sum of chi2 plus p_miss per missing layer), then
+ * parent rank, then tracklet id, a missing layer last.
+ * All pointers are device pointers owned by the caller; results are written
+ * asynchronously on `stream`.  The index must have been built on `stream` or
+ * on a stream `stream` has synchronised with.
+ * Errors: TRD_EINVAL (NULL pointers, n < 0, n_hyp outside 1..TRD_MAX_HYP,
+ * non-positive road/cut), TRD_ECUDA (launch failure).                       */
+TRD_API int trd_follow(trd_ctx_t *ctx, const trd_seeds_t *seeds, const trd_index_t *index,
+               const trd_params_t *params, trd_results_t *out, void *stream);
+
+/* trd_follow with explicit launch shape (used by the autotuner):
+ * lanes_per_track in {1, 2, 4, 8} (0 = smallest power of two >= n_hyp; 1
+ * needs n_hyp = 1), block_threads a multiple of 32 in 32..128 (0 = 128).    */
+TRD_API int trd_follow_tuned(trd_ctx_t *ctx, const trd_seeds_t *seeds, const trd_index_t *index,
+                     const trd_params_t *params, trd_results_t *out, void *stream,
+                     int lanes_per_track, int block_threads);
+
+/* Geometry constants the library was built with, for cross-checks:
+ * out[0..12] = n_sectors, n_stacks, n_layers, n_chambers, x_layer0,
+ * dx_layer, stack_length, z_min, tilt_deg, drift_length, lorentz_deg,
+ * c_light, max_snp.  Host only; needs no GPU.                               */
+TRD_API int trd_geometry(double *out, int n);
+
+/* Library version string (static storage).  Host only. */
+TRD_API const char *trd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TRD_ABI_H */

@@ -1,0 +1,747 @@
+// follow.cu -- the FP32 TRD tracklet follower (arXiv:2003.03174, Sec. 3).
+//
+// One group of G lanes follows one seed; lane q holds hypothesis q (N <= G).
+// Per layer every live lane transports its hypothesis to the layer plane,
+// scans the index over the road and keeps its own best N extensions; the
+// group then merges the lanes' lists with shuffles into the best N overall,
+// and every lane adopts one winner (parent state by shuffle) and applies the
+// Kalman update.  With N = 1 the group is a single thread per seed, which
+// keeps 32x more seeds in flight than a warp per seed: the per-layer chain of
+// dependent loads (road offsets, then records) is latency-bound, so memory
+// parallelism comes from many independent seeds per SM.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "trd_device.cuh"
+#include "trd_internal.h"
+
+namespace trd {
+
+struct Params {
+    float bz, road, cut, pmiss, gate;
+    int nhyp, maxmiss, resmode, material;
+};
+
+struct SeedsView {
+    const float *alpha, *x, *y, *z, *snp, *tgl, *q2pt, *cov;
+    int n;
+};
+
+struct ResultsView {
+    float *alpha, *x, *par, *cov, *chi2;
+    int32_t *ntrk, *nmiss, *status, *ids;
+};
+
+// ---- transport (exact helix in homogeneous Bz) -----------------------------
+// sin(phi) grows linearly with x at rate rho = -c Bz q/pT; the chord has
+// slope (f0+f1)/(r0+r1); the arc is chord * asin(w)/w with w = rho chord / 2.
+__device__ __forceinline__ void asin_over_series(float w, float *g, float *dg)
+{
+    const float w2 = w * w;
+    if (fabsf(w) < 0.3f) {
+        *g = 1.0f + w2 * (1.0f / 6.0f + w2 * (3.0f / 40.0f + w2 * (5.0f / 112.0f + w2 * (35.0f / 1152.0f))));
+        *dg = w * (1.0f / 3.0f + w2 * (0.3f + w2 * (15.0f / 56.0f + w2 * (35.0f / 144.0f))));
+    } else {
+        const float a = asinf(w);
+        *g = a / w;
+        *dg = (w * rsqrtf(1.0f - w2) - a) / w2;
+    }
+}
+
+__device__ bool propagate(TrackState &s, df xk, float bz)
+{
+    const float dx = df_to_f(df_add(xk, df_neg(s.x)));
+    const float f0 = s.f;
+    const float drho_dk = -kCLight * bz;
+    const float rho = drho_dk * s.k;
+    const float f1 = fmaf(rho, dx, f0);
+    if (!(fabsf(f0) < kMaxSnp) || !(fabsf(f1) < kMaxSnp)) return false;
+    const float r0 = sqrtf((1.0f - f0) * (1.0f + f0));
+    const float r1 = sqrtf((1.0f - f1) * (1.0f + f1));
+    const float rs = r0 + r1;
+    const float irs = 1.0f / rs;
+    const float fs = f0 + f1;
+    const float h = fs * irs;
+    const float q = sqrtf(fmaf(h, h, 1.0f));
+    const float chord = dx * q;
+    const float w = 0.5f * rho * chord;
+    float g, dg;
+    asin_over_series(w, &g, &dg);
+    const float arc = chord * g;
+
+    const float irs2 = irs * irs;
+    const float dh_df0 = (rs + fs * f0 / r0) * irs2;
+    const float dh_df1 = (rs + fs * f1 / r1) * irs2;
+    const float ds_df0 = dx * fs / (r0 * r1 * rs);
+    const float dchord_drho = dx * (h / q) * dh_df1 * dx;
+    const float ds_drho = dchord_drho * fmaf(w, dg, g) + 0.5f * chord * chord * dg;
+    const float a = dx * (dh_df0 + dh_df1);  // dy/dsnp
+    const float b = dx * dh_df1 * drho_dk * dx;  // dy/dk
+    const float c = s.t * ds_df0;            // dz/dsnp
+    const float d = arc;                     // dz/dtgl
+    const float e = s.t * ds_drho * drho_dk; // dz/dk
+    const float gg = drho_dk * dx;           // dsnp/dk
+
+    s.x = xk;
+    s.y = df_add_f(s.y, dx * h);
+    s.z = fmaf(s.t, arc, s.z);
+    s.f = f1;
+
+    // C <- J C J^T with J = I except rows y (a, b), z (c, d, e), snp (gg)
+    float *C = s.c;
+    const float C00 = C[0], C10 = C[1], C11 = C[2], C20 = C[3], C21 = C[4], C22 = C[5], C30 = C[6], C31 = C[7],
+                C32 = C[8], C33 = C[9], C40 = C[10], C41 = C[11], C42 = C[12], C43 = C[13], C44 = C[14];
+    // T = J C (rows 0..2)
+    const float T00 = C00 + a * C20 + b * C40, T02 = C20 + a * C22 + b * C42, T04 = C40 + a * C42 + b * C44;
+    const float T10 = C10 + c * C20 + d * C30 + e * C40;
+    const float T11 = C11 + c * C21 + d * C31 + e * C41;
+    const float T12 = C21 + c * C22 + d * C32 + e * C42;
+    const float T13 = C31 + c * C32 + d * C33 + e * C43;
+    const float T14 = C41 + c * C42 + d * C43 + e * C44;
+    const float T20 = C20 + gg * C40, T21 = C21 + gg * C41, T22 = C22 + gg * C42, T23 = C32 + gg * C43,
+                T24 = C42 + gg * C44;
+    C[0] = T00 + a * T02 + b * T04;
+    C[1] = T10 + a * T12 + b * T14;
+    C[2] = T11 + c * T12 + d * T13 + e * T14;
+    C[3] = T20 + a * T22 + b * T24;
+    C[4] = T21 + c * T22 + d * T23 + e * T24;
+    C[5] = T22 + gg * T24;
+    C[6] = C30 + a * C32 + b * C43;
+    C[7] = C31 + c * C32 + d * C33 + e * C43;
+    C[8] = C32 + gg * C43;
+    // C[9] = C33 unchanged
+    C[10] = C40 + a * C42 + b * C44;
+    C[11] = C41 + c * C42 + d * C43 + e * C44;
+    C[12] = C42 + gg * C44;
+    // C[13] = C43, C[14] = C44 unchanged
+    return true;
+}
+
+// ---- rotation into another sector frame ------------------------------------
+// Exact rotation of the point (double-float), first-order transform of the
+// covariance onto the new plane x' = const (slide along the track):
+// dy'/dy = r/r', dz'/dy = -tgl sin(d)/r', dsnp'/dy = -rho sin(d), dsnp'/dsnp = r'/r.
+__device__ bool rotate(TrackState &s, df delta, int new_sector, float bz)
+{
+    df sn;
+    float omc;
+    if (fabsf(delta.hi) < 0.6f) {
+        sincos_small(delta, &sn, &omc);
+    } else {
+        // rare (seed frame far from its sector): halve the angle into the
+        // series' range, then apply sin 2a = 2 sin a cos a, 1 - cos 2a = 2 sin^2 a
+        int halvings = 0;
+        df h = delta;
+        while (fabsf(h.hi) >= 0.3f && halvings < 6) {
+            h = {0.5f * h.hi, 0.5f * h.lo};
+            ++halvings;
+        }
+        sincos_small(h, &sn, &omc);
+        for (int k = 0; k < halvings; ++k) {
+            const float sf = df_to_f(sn);
+            const float nomc = 2.0f * sf * sf;
+            sn = df_mul_f(sn, 2.0f * (1.0f - omc));
+            omc = nomc;
+        }
+    }
+    const float snf = df_to_f(sn);
+    const float f = s.f;
+    const float r = sqrtf((1.0f - f) * (1.0f + f));
+    const float fn = f - f * omc - r * snf;
+    const float rn = r - r * omc + f * snf;
+    if (!(fabsf(fn) < kMaxSnp) || !(rn > 0.0f)) return false;
+    const float rho = -kCLight * bz * s.k;
+    const float p = r / rn, qq = -s.t * snf / rn, u = -rho * snf, v = rn / r;
+
+    const df x = s.x, y = s.y;
+    // x' = x cos d + y sin d ; y' = -x sin d + y cos d   (cos d = 1 - omc)
+    s.x = df_add(df_add(x, df_neg(df_mul_f(x, omc))), df_mul(y, sn));
+    s.y = df_add(df_add(y, df_neg(df_mul_f(y, omc))), df_neg(df_mul(x, sn)));
+    s.f = fn;
+    s.sector = new_sector;
+
+    float *C = s.c;
+    const float C00 = C[0], C10 = C[1], C11 = C[2], C20 = C[3], C21 = C[4], C22 = C[5], C30 = C[6], C31 = C[7],
+                C32 = C[8], C40 = C[10], C41 = C[11], C42 = C[12];
+    const float T10 = qq * C00 + C10;
+    const float T20 = u * C00 + v * C20;
+    const float T21 = u * C10 + v * C21;
+    const float T22 = u * C20 + v * C22;
+    C[0] = p * p * C00;
+    C[1] = p * T10;
+    C[2] = qq * T10 + qq * C10 + C11;
+    C[3] = p * T20;
+    C[4] = qq * T20 + T21;
+    C[5] = u * T20 + v * T22;
+    C[6] = p * C30;
+    C[7] = qq * C30 + C31;
+    C[8] = u * C30 + v * C32;
+    C[10] = p * C40;
+    C[11] = qq * C40 + C41;
+    C[12] = u * C40 + v * C42;
+    return true;
+}
+
+// ---- material step (reading: Highland scattering + Bethe loss of a pion) ----
+__device__ bool material(TrackState &s)
+{
+    const float f = s.f, t = s.t, k = s.k;
+    if (k == 0.0f) return true;
+    const float r = sqrtf((1.0f - f) * (1.0f + f));
+    const float t2 = fmaf(t, t, 1.0f);
+    const float st2 = sqrtf(t2);
+    const float path = st2 / r;
+    const float xx0 = kX0Fraction * path;
+    const float p = st2 / fabsf(k);
+    const float m2 = kMassPion * kMassPion;
+    const float e = sqrtf(fmaf(p, p, m2));
+    const float beta = p / e;
+    const float t0 = 0.0136f / (beta * p);
+    const float lg = fmaf(0.038f, logf(xx0), 1.0f);
+    const float th2 = t0 * t0 * xx0 * lg * lg;
+    float *C = s.c;
+    C[5] += th2 * r * r * t2;
+    C[9] += th2 * t2 * t2;
+    C[13] += th2 * t * t2 * k;
+    C[14] += th2 * t * t * k * k;
+    const float bg = p / kMassPion;
+    const float bg2 = bg * bg;
+    const float b2 = bg2 / (1.0f + bg2);
+    const float dedx = kBetheKZA / b2 * (logf(kTwoMeOverI * bg2) - b2);  // GeV cm^2/g
+    const float de = dedx * kXRho * path;
+    const float e1 = e - de;
+    if (!(e1 > kMassPion)) return false;
+    const float p1 = sqrtf((e1 - kMassPion) * (e1 + kMassPion));
+    const float sc = p / p1;
+    s.k = k * sc;
+    C[10] *= sc;
+    C[11] *= sc;
+    C[12] *= sc;
+    C[13] *= sc;
+    C[14] *= sc * sc;
+    return true;
+}
+
+// Carry a hypothesis to the plane of layer l; returns false if it is lost.
+// chamber = -1 when z is outside the 5 stacks.
+__device__ bool to_layer(TrackState &s, int l, const Params &P, int &chamber)
+{
+    const df xl = layer_x_df(l);
+    if (!propagate(s, xl, P.bz)) return false;
+    const float lim = xl.hi * half_sector_tan();
+    if (fabsf(s.y.hi) > lim) {
+        const int dir = s.y.hi > 0.0f ? 1 : -1;
+        const int ns = (s.sector + dir + kSectors) % kSectors;
+        const df d = dir > 0 ? df{kSectorWidthHi, kSectorWidthLo} : df{-kSectorWidthHi, -kSectorWidthLo};
+        if (!rotate(s, d, ns, P.bz)) return false;
+        if (!propagate(s, xl, P.bz)) return false;
+    }
+    if (P.material && !material(s)) return false;
+    const float u = (s.z - kZMin) * (1.0f / kStackLength);
+    if (u >= 0.0f && u < static_cast<float>(kStacks)) {
+        const int stack = static_cast<int>(u);
+        chamber = s.sector * (kStacks * kLayers) + stack * kLayers + l;
+    } else {
+        chamber = -1;
+    }
+    return true;
+}
+
+// ---- Kalman update, Joseph form, symmetrised --------------------------------
+// Measurement (y_tl, z_tl) with pad tilt: h(p) = (y - tt (z - z_tl), z).
+__device__ void kalman_update(TrackState &s, float tt, float ytl, float ztl, float vyy, float vzz, float vyz)
+{
+    float *C = s.c;
+    const float r0 = (__fsub_rn(ytl, s.y.hi) - s.y.lo) + tt * (s.z - ztl);
+    const float r1 = ztl - s.z;
+    // C H^T (5x2): column 0 = C[:,0] - tt C[:,1], column 1 = C[:,1]
+    float Ci0[5], Ci1[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        Ci0[i] = C[cidx(i, 0)];
+        Ci1[i] = C[cidx(i, 1)];
+    }
+    float H0[5], H1[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        H0[i] = Ci0[i] - tt * Ci1[i];
+        H1[i] = Ci1[i];
+    }
+    const float S00 = H0[0] - tt * H0[1] + vyy;
+    const float S01 = H1[0] - tt * H1[1] + vyz;
+    const float S11 = H1[1] + vzz;
+    const float idet = 1.0f / (S00 * S11 - S01 * S01);
+    const float Si00 = S11 * idet, Si01 = -S01 * idet, Si11 = S00 * idet;
+    float K0[5], K1[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        K0[i] = H0[i] * Si00 + H1[i] * Si01;
+        K1[i] = H0[i] * Si01 + H1[i] * Si11;
+    }
+    s.y = df_add_f(s.y, K0[0] * r0 + K1[0] * r1);
+    s.z += K0[1] * r0 + K1[1] * r1;
+    s.f += K0[2] * r0 + K1[2] * r1;
+    s.t += K0[3] * r0 + K1[3] * r1;
+    s.k += K0[4] * r0 + K1[4] * r1;
+    // Joseph: (I - K H) C (I - K H)^T + K V K^T; I - K H differs from I in
+    // columns 0 and 1 only: A x = x - u x_0 - v x_1 with u = K0, v = K1 - tt K0.
+    float u[5], v[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        u[i] = K0[i];
+        v[i] = K1[i] - tt * K0[i];
+    }
+    float B[5][5];  // B = A C
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+#pragma unroll
+        for (int j = 0; j < 5; ++j) B[i][j] = C[cidx(i, j)] - u[i] * Ci0[j] - v[i] * Ci1[j];
+    float N[5][5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            const float kv0 = vyy * K0[j] + vyz * K1[j];
+            const float kv1 = vyz * K0[j] + vzz * K1[j];
+            N[i][j] = B[i][j] - B[i][0] * u[j] - B[i][1] * v[j] + K0[i] * kv0 + K1[i] * kv1;
+        }
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j) C[cidx(i, j)] = i == j ? N[i][i] : 0.5f * (N[i][j] + N[j][i]);
+}
+
+// ---- small sorted extension list (per lane) ---------------------------------
+template <int NH>
+struct ExtList {
+    float score[NH];
+    float chi2[NH];
+    int id[NH];
+    int pos[NH];
+    __device__ __forceinline__ void clear()
+    {
+#pragma unroll
+        for (int k = 0; k < NH; ++k) {
+            score[k] = INFINITY;
+            chi2[k] = 0.0f;
+            id[k] = kMissing;
+            pos[k] = -1;
+        }
+    }
+    __device__ __forceinline__ static bool less(float sa, int ia, float sb, int ib)
+    {
+        return sa < sb || (sa == sb && ia < ib);
+    }
+    __device__ __forceinline__ void insert(float sc, int tid, int p, float c2)
+    {
+        if (!less(sc, tid, score[NH - 1], id[NH - 1])) return;
+        // shift larger entries up, then place (unrolled, stays in registers)
+        bool placed = false;
+#pragma unroll
+        for (int k = NH - 1; k >= 0; --k) {
+            if (placed) continue;
+            const bool move = k > 0 && less(sc, tid, score[k - 1], id[k - 1]);
+            if (move) {
+                score[k] = score[k - 1];
+                chi2[k] = chi2[k - 1];
+                id[k] = id[k - 1];
+                pos[k] = pos[k - 1];
+            } else {
+                score[k] = sc;
+                chi2[k] = c2;
+                id[k] = tid;
+                pos[k] = p;
+                placed = true;
+            }
+        }
+    }
+    __device__ __forceinline__ void pop()
+    {
+#pragma unroll
+        for (int k = 0; k + 1 < NH; ++k) {
+            score[k] = score[k + 1];
+            chi2[k] = chi2[k + 1];
+            id[k] = id[k + 1];
+            pos[k] = pos[k + 1];
+        }
+        score[NH - 1] = INFINITY;
+        id[NH - 1] = kMissing;
+        pos[NH - 1] = -1;
+    }
+};
+
+// Road query + candidate tests for one hypothesis at layer l (Sec. 3).
+template <int NH>
+__device__ void scan_candidates(const TrackState &s, int l, int chamber, float score, const Params &P,
+                                const IndexView &ix, float vyy_max_in, float vzz_max, ExtList<NH> &L)
+{
+    const float tt = layer_tilt_tan(l);
+    const float f = s.f;
+    const float r = sqrtf((1.0f - f) * (1.0f + f));
+    const float uu = f / r - lorentz_tan(P.bz);
+    const float vyy_res = kSigY0 * kSigY0 + kSigY1 * kSigY1 * uu * uu;
+    const float vyy_max = P.resmode ? vyy_res : vyy_max_in;
+    const float c10 = s.c[1], c11 = s.c[2];
+    const float syy_trk = s.c[0] - 2.0f * tt * c10 + tt * tt * c11;
+    const float syz_trk = c10 - tt * c11;
+    const float n2 = P.road * P.road;
+    const float W = P.road * sqrtf(fmaxf(syy_trk + vyy_max, 0.0f)) * 1.0001f + 1e-4f;
+    const float Rz = P.road * sqrtf(fmaxf(c11 + vzz_max, 0.0f)) * 1.0001f + 1e-4f;
+    const float dy_pred = kDriftLength * uu;
+    const float gate = P.gate * sqrtf(kSigDy0 * kSigDy0 + kSigDy1 * kSigDy1 * uu * uu);
+    const float z = s.z;
+    const float yh = s.y.hi, yl = s.y.lo;
+    const float zlo = stack_z_lo(stack_of_chamber(chamber));
+    const int r_lo = row_of_z(z - Rz, zlo), r_hi = row_of_z(z + Rz, zlo);
+    const float pad = 1e-3f + 1e-6f * fabsf(yh);
+    for (int row = r_lo; row <= r_hi; ++row) {
+        const float za = row == 0 ? z - Rz : fmaxf(z - Rz, zlo + kRowLength * row);
+        const float zb = row == kRowsPerStack - 1 ? z + Rz : fminf(z + Rz, zlo + kRowLength * (row + 1));
+        const float t1 = tt * (za - z), t2 = tt * (zb - z);
+        const float ylo = yh + fminf(t1, t2) - W - pad, yhi = yh + fmaxf(t1, t2) + W + pad;
+        const int b_lo = ybin_of(ylo, ix.inv_w, ix.nb), b_hi = ybin_of(yhi, ix.inv_w, ix.nb);
+        const int b0 = (chamber * kRowsPerStack + row) * ix.nb;
+        const int beg = __ldg(&ix.offsets[b0 + b_lo]);
+        const int end = __ldg(&ix.offsets[b0 + b_hi + 1]);
+        for (int pos = beg; pos < end; ++pos) {
+            const float4 a = __ldg(&ix.rec0[pos]);
+            const float ry = (__fsub_rn(a.x, yh) - yl) + tt * (z - a.y);
+            const float rz = a.y - z;
+            if (fabsf(ry) > W || fabsf(rz) > Rz) continue;
+            const float4 v = __ldg(&ix.rec1[pos]);
+            const float vyy = P.resmode ? vyy_res : v.x;
+            const float S00 = syy_trk + vyy;
+            const float S01 = syz_trk + v.z;
+            const float S11 = c11 + v.y;
+            if (ry * ry > n2 * S00 || rz * rz > n2 * S11) continue;
+            if (fabsf(a.z - dy_pred) > gate) continue;
+            const float chi2 = (S11 * ry * ry - 2.0f * S01 * ry * rz + S00 * rz * rz) / (S00 * S11 - S01 * S01);
+            if (!(chi2 < P.cut)) continue;
+            L.insert(score + chi2, __float_as_int(a.w), pos, chi2);
+        }
+    }
+}
+
+struct Snapshot {  // pre-transport copy of lane 0's state, in shared memory
+    float v[24];
+};
+
+__device__ __forceinline__ void save_state(float *sm, int stride, const TrackState &s)
+{
+    sm[0 * stride] = s.x.hi;
+    sm[1 * stride] = s.x.lo;
+    sm[2 * stride] = s.y.hi;
+    sm[3 * stride] = s.y.lo;
+    sm[4 * stride] = s.z;
+    sm[5 * stride] = s.f;
+    sm[6 * stride] = s.t;
+    sm[7 * stride] = s.k;
+#pragma unroll
+    for (int k = 0; k < 15; ++k) sm[(8 + k) * stride] = s.c[k];
+    sm[23 * stride] = __int_as_float(s.sector);
+}
+
+__device__ __forceinline__ void load_state(const float *sm, int stride, TrackState &s)
+{
+    s.x = {sm[0 * stride], sm[1 * stride]};
+    s.y = {sm[2 * stride], sm[3 * stride]};
+    s.z = sm[4 * stride];
+    s.f = sm[5 * stride];
+    s.t = sm[6 * stride];
+    s.k = sm[7 * stride];
+#pragma unroll
+    for (int k = 0; k < 15; ++k) s.c[k] = sm[(8 + k) * stride];
+    s.sector = __float_as_int(sm[23 * stride]);
+}
+
+__device__ __forceinline__ bool cov_pd(const float *c)
+{
+    // Cholesky of the 5x5 (seed validity)
+    float L[15];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        float d = c[cidx(j, j)];
+#pragma unroll
+        for (int k = 0; k < j; ++k) d -= L[cidx(j, k)] * L[cidx(j, k)];
+        if (!(d > 0.0f)) return false;
+        const float ljj = sqrtf(d);
+        L[cidx(j, j)] = ljj;
+#pragma unroll
+        for (int i = j + 1; i < 5; ++i) {
+            float x = c[cidx(i, j)];
+#pragma unroll
+            for (int k = 0; k < j; ++k) x -= L[cidx(i, k)] * L[cidx(j, k)];
+            L[cidx(i, j)] = x / ljj;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void write_result(const ResultsView &o, int n, int i, const TrackState &s, float chi2,
+                                             int ntrk, int nmiss, int status, const int (&ids)[kLayers])
+{
+    o.alpha[i] = sector_alpha_df(s.sector).hi;
+    o.x[i] = df_to_f(s.x);
+    o.par[0 * n + i] = df_to_f(s.y);
+    o.par[1 * n + i] = s.z;
+    o.par[2 * n + i] = s.f;
+    o.par[3 * n + i] = s.t;
+    o.par[4 * n + i] = s.k;
+#pragma unroll
+    for (int k = 0; k < 15; ++k) o.cov[k * n + i] = s.c[k];
+    o.chi2[i] = chi2;
+    o.ntrk[i] = ntrk;
+    o.nmiss[i] = nmiss;
+    o.status[i] = status;
+#pragma unroll
+    for (int l = 0; l < kLayers; ++l) o.ids[l * n + i] = ids[l];
+}
+
+__device__ __forceinline__ void write_seed_result(const ResultsView &o, const SeedsView &sv, int n, int i,
+                                                  int status)
+{
+    o.alpha[i] = sv.alpha[i];
+    o.x[i] = sv.x[i];
+    o.par[0 * n + i] = sv.y[i];
+    o.par[1 * n + i] = sv.z[i];
+    o.par[2 * n + i] = sv.snp[i];
+    o.par[3 * n + i] = sv.tgl[i];
+    o.par[4 * n + i] = sv.q2pt[i];
+#pragma unroll
+    for (int k = 0; k < 15; ++k) o.cov[k * n + i] = sv.cov[k * n + i];
+    o.chi2[i] = 0.0f;
+    o.ntrk[i] = 0;
+    o.nmiss[i] = 0;
+    o.status[i] = status;
+#pragma unroll
+    for (int l = 0; l < kLayers; ++l) o.ids[l * n + i] = -1;
+}
+
+template <int G>
+__device__ __forceinline__ float gshfl(unsigned mask, float v, int src)
+{
+    return G == 1 ? v : __shfl_sync(mask, v, src, G);
+}
+template <int G>
+__device__ __forceinline__ int gshfl(unsigned mask, int v, int src)
+{
+    return G == 1 ? v : __shfl_sync(mask, v, src, G);
+}
+
+// Follow seed i with a group of G lanes keeping up to NH hypotheses.
+// sm: this group's snapshot column (stride = groups per block).
+template <int G, int NH>
+__device__ void follow_track(int i, const SeedsView &sv, const IndexView &ix, const Params &P,
+                             const ResultsView &o, float *sm, int stride)
+{
+    const int n = sv.n;
+    const int q = G == 1 ? 0 : (threadIdx.x & (G - 1));
+    const unsigned gmask =
+        G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
+
+    // seed (every lane reads the same addresses)
+    TrackState s;
+    const float alpha = sv.alpha[i];
+    const float sx = sv.x[i], sy = sv.y[i];
+    s.x = {sx, 0.0f};
+    s.y = {sy, 0.0f};
+    s.z = sv.z[i];
+    s.f = sv.snp[i];
+    s.t = sv.tgl[i];
+    s.k = sv.q2pt[i];
+#pragma unroll
+    for (int k = 0; k < 15; ++k) s.c[k] = sv.cov[k * n + i];
+    if (!(fabsf(s.f) < kMaxSnp) || !cov_pd(s.c)) {
+        if (q == 0) write_seed_result(o, sv, n, i, TRD_ST_SEED_INVALID);
+        return;
+    }
+    // rotate into the sector of the seed's position
+    {
+        const float phi = alpha + atan2f(sy, sx);
+        constexpr float two_pi = kTwoPiHi;
+        float u = phi - two_pi * floorf(phi * (1.0f / two_pi));
+        int sec = static_cast<int>(u * (1.0f / kSectorWidthHi));
+        sec = min(max(sec, 0), kSectors - 1);
+        const df target = sector_alpha_df(sec);
+        df d = df_add_f(target, -alpha);
+        if (d.hi > 3.14159265f) d = df_add(d, df{-kTwoPiHi, -kTwoPiLo});
+        if (d.hi < -3.14159265f) d = df_add(d, df{kTwoPiHi, kTwoPiLo});
+        s.sector = sec;
+        if (!rotate(s, d, sec, P.bz)) {
+            if (q == 0) write_seed_result(o, sv, n, i, TRD_ST_PROP_FAIL);
+            return;
+        }
+    }
+
+    bool alive = q == 0;
+    float score = 0.0f, chisum = 0.0f;
+    int ntrk = 0, nmiss = 0;
+    int ids[kLayers];
+#pragma unroll
+    for (int l = 0; l < kLayers; ++l) ids[l] = -1;
+    const float vyy_max = __uint_as_float(__ldg(&ix.stats[0]));
+    const float vzz_max = __uint_as_float(__ldg(&ix.stats[1]));
+
+    for (int l = 0; l < kLayers; ++l) {
+        if (q == 0) save_state(sm, stride, s);
+        int chamber = -1;
+        const bool live = alive && to_layer(s, l, P, chamber);
+        ExtList<NH> L;
+        L.clear();
+        if (live && chamber >= 0) scan_candidates<NH>(s, l, chamber, score, P, ix, vyy_max, vzz_max, L);
+        if (live && nmiss < P.maxmiss) L.insert(score + P.pmiss, kMissing, -1, 0.0f);
+
+        // merge the lanes' lists: the k-th best extension goes to lane k
+        int my_parent = q, my_id = kMissing, my_pos = -1;
+        float my_score = INFINITY, my_chi2 = 0.0f;
+        int kept = 0;
+        if (G == 1) {
+            if (L.score[0] < INFINITY) {
+                my_score = L.score[0];
+                my_id = L.id[0];
+                my_pos = L.pos[0];
+                my_chi2 = L.chi2[0];
+                kept = 1;
+            }
+        } else {
+            for (int rr = 0; rr < P.nhyp; ++rr) {
+                float bs = L.score[0];
+                int bq = q, bid = L.id[0];
+#pragma unroll
+                for (int off = G / 2; off > 0; off >>= 1) {
+                    const float os = __shfl_xor_sync(gmask, bs, off, G);
+                    const int oq = __shfl_xor_sync(gmask, bq, off, G);
+                    const int oid = __shfl_xor_sync(gmask, bid, off, G);
+                    const bool take = os < bs || (os == bs && (oq < bq || (oq == bq && oid < bid)));
+                    if (take) {
+                        bs = os;
+                        bq = oq;
+                        bid = oid;
+                    }
+                }
+                if (!(bs < INFINITY)) break;
+                const float wchi2 = __shfl_sync(gmask, L.chi2[0], bq, G);
+                const int wpos = __shfl_sync(gmask, L.pos[0], bq, G);
+                if (q == rr) {
+                    my_parent = bq;
+                    my_id = bid;
+                    my_pos = wpos;
+                    my_score = bs;
+                    my_chi2 = wchi2;
+                }
+                if (q == bq) L.pop();
+                kept = rr + 1;
+            }
+        }
+        if (kept == 0) {
+            // no extension for any hypothesis: the track ends with the best
+            // hypothesis as it was after the previous layer
+            const bool any_live = G == 1 ? live : (__any_sync(gmask, live) != 0);
+            if (q == 0) {
+                TrackState b;
+                load_state(sm, stride, b);
+                write_result(o, n, i, b, chisum, ntrk, nmiss, any_live ? TRD_ST_STOPPED : TRD_ST_PROP_FAIL, ids);
+            }
+            return;
+        }
+        // adopt the parent's transported state
+        if (G > 1) {
+            const int src = my_parent;
+            s.x.hi = gshfl<G>(gmask, s.x.hi, src);
+            s.x.lo = gshfl<G>(gmask, s.x.lo, src);
+            s.y.hi = gshfl<G>(gmask, s.y.hi, src);
+            s.y.lo = gshfl<G>(gmask, s.y.lo, src);
+            s.z = gshfl<G>(gmask, s.z, src);
+            s.f = gshfl<G>(gmask, s.f, src);
+            s.t = gshfl<G>(gmask, s.t, src);
+            s.k = gshfl<G>(gmask, s.k, src);
+#pragma unroll
+            for (int k = 0; k < 15; ++k) s.c[k] = gshfl<G>(gmask, s.c[k], src);
+            s.sector = gshfl<G>(gmask, s.sector, src);
+            chisum = gshfl<G>(gmask, chisum, src);
+            ntrk = gshfl<G>(gmask, ntrk, src);
+            nmiss = gshfl<G>(gmask, nmiss, src);
+#pragma unroll
+            for (int k = 0; k < kLayers; ++k) ids[k] = gshfl<G>(gmask, ids[k], src);
+        }
+        alive = q < kept;
+        if (alive) {
+            score = my_score;
+            int idl = -1;
+            if (my_id != kMissing) {
+                const float4 a = __ldg(&ix.rec0[my_pos]);
+                const float4 v = __ldg(&ix.rec1[my_pos]);
+                float vyy = v.x;
+                if (P.resmode) {
+                    const float r = sqrtf((1.0f - s.f) * (1.0f + s.f));
+                    const float uu = s.f / r - lorentz_tan(P.bz);
+                    vyy = kSigY0 * kSigY0 + kSigY1 * kSigY1 * uu * uu;
+                }
+                kalman_update(s, layer_tilt_tan(l), a.x, a.y, vyy, v.y, v.z);
+                idl = my_id;
+                ntrk += 1;
+                chisum += my_chi2;
+            } else {
+                nmiss += 1;
+            }
+#pragma unroll
+            for (int k = 0; k < kLayers; ++k) ids[k] = k == l ? idl : ids[k];
+        }
+    }
+    if (q == 0) write_result(o, n, i, s, chisum, ntrk, nmiss, TRD_ST_OK, ids);
+}
+
+template <int G, int NH>
+__global__ void __launch_bounds__(128) k_follow(SeedsView sv, IndexView ix, Params P, ResultsView o)
+{
+    extern __shared__ float smem[];
+    const int groups = blockDim.x / G;
+    const int g = threadIdx.x / G;
+    const int i = blockIdx.x * groups + g;
+    if (i >= sv.n) return;
+    follow_track<G, NH>(i, sv, ix, P, o, smem + g, groups);
+}
+
+}  // namespace trd
+
+namespace trd_host {
+
+using namespace trd;
+
+template <int G, int NH>
+static int launch(const SeedsView &sv, const IndexView &ix, const Params &P, const ResultsView &o,
+                  cudaStream_t s, int block)
+{
+    const int groups = block / G;
+    const int grid = (sv.n + groups - 1) / groups;
+    const size_t smem = sizeof(float) * 24 * groups;
+    if (grid == 0) return TRD_OK;
+    k_follow<G, NH><<<grid, block, smem, s>>>(sv, ix, P, o);
+    TRD_CUDA_TRY(cudaGetLastError());
+    return TRD_OK;
+}
+
+int follow_launch(const trd_ctx *ctx, const trd_seeds_t *seeds, const IndexView &iv, const trd_params_t *p,
+                  trd_results_t *out, cudaStream_t s, int lanes_per_track, int block_threads)
+{
+    (void)ctx;
+    SeedsView sv{seeds->alpha, seeds->x, seeds->y, seeds->z, seeds->snp, seeds->tgl, seeds->q2pt, seeds->cov,
+                 seeds->n};
+    Params P{p->bz, p->n_sigma_road, p->chi2_cut, p->p_miss, p->dy_gate_sigma, p->n_hyp, p->max_missing,
+             p->res_mode, p->material_on};
+    ResultsView o{out->alpha, out->x, out->par, out->cov, out->chi2, out->n_trk, out->n_miss, out->status,
+                  out->tracklet_id};
+    const int block = block_threads > 0 ? block_threads : 128;
+    int G = lanes_per_track;
+    if (G <= 0) G = p->n_hyp <= 1 ? 1 : (p->n_hyp <= 2 ? 2 : (p->n_hyp <= 4 ? 4 : 8));
+    if (G < p->n_hyp) return TRD_EINVAL;
+    switch (G) {
+    case 1: return p->n_hyp == 1 ? launch<1, 1>(sv, iv, P, o, s, block) : TRD_EINVAL;
+    case 2: return launch<2, 2>(sv, iv, P, o, s, block);
+    case 4: return launch<4, 4>(sv, iv, P, o, s, block);
+    case 8: return launch<8, 8>(sv, iv, P, o, s, block);
+    default: return TRD_EINVAL;
+    }
+}
+
+}  // namespace trd_host

@@ -1,0 +1,218 @@
+// index.cu -- the tracklet index (Sec. 3: "all tracklets inside a search road
+// based on the covariance matrices of the tracks are considered").
+//
+// Tracklets are bucketed by (chamber, pad row, y bin) with a counting sort:
+//   1. count: bucket of each tracklet; atomicAdd on the bucket's counter
+//      returns the tracklet's rank inside its bucket (no second atomic pass);
+//      block-reduced maxima of vyy and vzz bound the road width.
+//   2. exclusive scan of the bucket counters (reduce / scan partials / apply).
+//   3. scatter: record at offsets[bucket] + rank, as two float4 rows.
+// Buckets of one (chamber, pad row) are adjacent in y, so the follower reads
+// one contiguous range per pad row.  Order inside a bucket is not defined;
+// the follower's selection does not depend on it (ties break on tracklet id).
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <algorithm>
+
+#include "trd_device.cuh"
+#include "trd_internal.h"
+
+namespace {
+
+constexpr int kCountThreads = 256;
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__global__ void __launch_bounds__(kCountThreads)
+k_index_count(const int32_t *__restrict__ ch, const float *__restrict__ y, const float *__restrict__ z,
+              const float *__restrict__ dy, const float *__restrict__ vyy, const float *__restrict__ vzz,
+              const float *__restrict__ vyz, int n, float inv_w, int nb, int32_t *__restrict__ bucket,
+              int32_t *__restrict__ rank, int32_t *__restrict__ counts, uint32_t *__restrict__ stats)
+{
+    float myy = 0.0f, mzz = 0.0f;
+    int rejected = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int c = ch[i];
+        const float yy = y[i], zz = z[i], dd = dy[i], a = vyy[i], b = vzz[i], cc = vyz[i];
+        const bool ok = c >= 0 && c < trd::kChambers && isfinite(yy) && isfinite(zz) && isfinite(dd) &&
+                        isfinite(a) && isfinite(b) && isfinite(cc) && a >= 0.0f && b >= 0.0f;
+        if (!ok) {
+            bucket[i] = -1;
+            rank[i] = 0;
+            ++rejected;
+            continue;
+        }
+        const int row = trd::row_of_z(zz, trd::stack_z_lo(trd::stack_of_chamber(c)));
+        const int yb = trd::ybin_of(yy, inv_w, nb);
+        const int bk = (c * trd::kRowsPerStack + row) * nb + yb;
+        bucket[i] = bk;
+        rank[i] = atomicAdd(&counts[bk], 1);
+        myy = fmaxf(myy, a);
+        mzz = fmaxf(mzz, b);
+    }
+    // block reduction of the maxima and the rejected count
+    for (int o = 16; o > 0; o >>= 1) {
+        myy = fmaxf(myy, __shfl_xor_sync(0xffffffffu, myy, o));
+        mzz = fmaxf(mzz, __shfl_xor_sync(0xffffffffu, mzz, o));
+        rejected += __shfl_xor_sync(0xffffffffu, rejected, o);
+    }
+    __shared__ float s_yy[kCountThreads / 32], s_zz[kCountThreads / 32];
+    __shared__ int s_rej[kCountThreads / 32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        s_yy[w] = myy;
+        s_zz[w] = mzz;
+        s_rej[w] = rejected;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float a = 0.0f, b = 0.0f;
+        int r = 0;
+        for (int k = 0; k < kCountThreads / 32; ++k) {
+            a = fmaxf(a, s_yy[k]);
+            b = fmaxf(b, s_zz[k]);
+            r += s_rej[k];
+        }
+        // non-negative floats order like their bit patterns
+        atomicMax(&stats[0], __float_as_uint(a));
+        atomicMax(&stats[1], __float_as_uint(b));
+        if (r) atomicAdd(&stats[2], static_cast<uint32_t>(r));
+    }
+}
+
+// Block-wide exclusive scan of one value per thread; returns the block total.
+__device__ __forceinline__ int block_exclusive_scan(int v, int *s_warp, int *total)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += t;
+    }
+    if (lane == 31) s_warp[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        const int nw = blockDim.x >> 5;
+        int s = lane < nw ? s_warp[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += t;
+        }
+        if (lane < nw) s_warp[lane] = s;
+    }
+    __syncthreads();
+    const int before = w ? s_warp[w - 1] : 0;
+    *total = s_warp[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int32_t *__restrict__ in, int n, int32_t *__restrict__ partials)
+{
+    const int base = blockIdx.x * kScanTile;
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const int i = base + k * kScanThreads + threadIdx.x;
+        if (i < n) s += in[i];
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ int s_w[kScanThreads / 32];
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int t = threadIdx.x < kScanThreads / 32 ? s_w[threadIdx.x] : 0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (threadIdx.x == 0) partials[blockIdx.x] = t;
+    }
+}
+
+// Single block: exclusive scan of the partial sums in place; partials[m] = total.
+__global__ void __launch_bounds__(kScanThreads) k_scan_partials(int32_t *partials, int m)
+{
+    __shared__ int s_w[kScanThreads / 32];
+    int carry = 0;
+    for (int base = 0; base < m; base += kScanThreads) {
+        const int i = base + threadIdx.x;
+        const int v = i < m ? partials[i] : 0;
+        int total;
+        const int ex = block_exclusive_scan(v, s_w, &total);
+        if (i < m) partials[i] = carry + ex;
+        carry += total;
+    }
+    if (threadIdx.x == 0) partials[m] = carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_apply(const int32_t *__restrict__ in, int n, const int32_t *__restrict__ partials, int32_t *__restrict__ out)
+{
+    __shared__ int s_w[kScanThreads / 32];
+    const int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    int v[kScanItems];
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = base + k < n ? in[base + k] : 0;
+        s += v[k];
+    }
+    int total;
+    int run = partials[blockIdx.x] + block_exclusive_scan(s, s_w, &total);
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < n) out[base + k] = run;
+        run += v[k];
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = partials[gridDim.x];
+}
+
+__global__ void __launch_bounds__(kCountThreads)
+k_index_scatter(const float *__restrict__ y, const float *__restrict__ z, const float *__restrict__ dy,
+                const float *__restrict__ vyy, const float *__restrict__ vzz, const float *__restrict__ vyz,
+                int n, const int32_t *__restrict__ bucket, const int32_t *__restrict__ rank,
+                const int32_t *__restrict__ offsets, float4 *__restrict__ rec0, float4 *__restrict__ rec1)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int b = bucket[i];
+        if (b < 0) continue;
+        const int pos = offsets[b] + rank[i];
+        rec0[pos] = make_float4(y[i], z[i], dy[i], __int_as_float(i));
+        rec1[pos] = make_float4(vyy[i], vzz[i], vyz[i], 0.0f);
+    }
+}
+
+}  // namespace
+
+namespace trd_host {
+
+int scan_blocks_for(int n) { return (n + kScanTile - 1) / kScanTile; }
+
+int index_rebuild_launch(trd_index *idx, const trd_tracklets_t *t, cudaStream_t s)
+{
+    const int n = t->n;
+    TRD_CUDA_TRY(cudaMemsetAsync(idx->counts, 0, sizeof(int32_t) * idx->n_buckets, s));
+    TRD_CUDA_TRY(cudaMemsetAsync(idx->stats, 0, sizeof(uint32_t) * 4, s));
+    const int grid_n = n > 0 ? std::min((n + kCountThreads - 1) / kCountThreads, idx->ctx->sm_count * 8) : 0;
+    if (n > 0) {
+        k_index_count<<<grid_n, kCountThreads, 0, s>>>(t->chamber, t->y, t->z, t->dy, t->vyy, t->vzz, t->vyz, n,
+                                                       idx->inv_w, idx->nb, idx->bucket, idx->rank, idx->counts,
+                                                       idx->stats);
+        TRD_CUDA_TRY(cudaGetLastError());
+    }
+    const int m = scan_blocks_for(idx->n_buckets);
+    k_scan_reduce<<<m, kScanThreads, 0, s>>>(idx->counts, idx->n_buckets, idx->partials);
+    TRD_CUDA_TRY(cudaGetLastError());
+    k_scan_partials<<<1, kScanThreads, 0, s>>>(idx->partials, m);
+    TRD_CUDA_TRY(cudaGetLastError());
+    k_scan_apply<<<m, kScanThreads, 0, s>>>(idx->counts, idx->n_buckets, idx->partials, idx->offsets);
+    TRD_CUDA_TRY(cudaGetLastError());
+    if (n > 0) {
+        k_index_scatter<<<grid_n, kCountThreads, 0, s>>>(t->y, t->z, t->dy, t->vyy, t->vzz, t->vyz, n, idx->bucket,
+                                                         idx->rank, idx->offsets, idx->rec0, idx->rec1);
+        TRD_CUDA_TRY(cudaGetLastError());
+    }
+    return TRD_OK;
+}
+
+}  // namespace trd_host

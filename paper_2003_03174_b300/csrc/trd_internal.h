@@ -1,0 +1,65 @@
+// trd_internal.h -- host-side definitions shared by the library's sources.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/trd_abi.h"
+
+struct trd_ctx {
+    int device;
+    int sm_count;
+    int max_threads_per_sm;
+    size_t l2_bytes;
+};
+
+// Device-resident tracklet index (built by trd_index_build / rebuild).
+struct trd_index {
+    trd_ctx *ctx;
+    int device;
+    int32_t capacity;   // tracklets the buffers can hold
+    int32_t n_input;    // tracklets given to the last build
+    float y_bin_width;  // cm
+    float inv_w;
+    int32_t nb;         // y bins per (chamber, pad row)
+    int32_t n_buckets;  // 540 * 18 * nb
+    // index proper
+    int32_t *offsets;   // [n_buckets + 1] exclusive prefix of bucket sizes
+    float4 *rec0;       // [capacity] {y, z, dy, id (bits)} in bucket order
+    float4 *rec1;       // [capacity] {vyy, vzz, vyz, 0}
+    uint32_t *stats;    // [4]: max vyy bits, max vzz bits, rejected count, spare
+    // build scratch
+    int32_t *bucket;    // [capacity] bucket of each input tracklet (-1: rejected)
+    int32_t *rank;      // [capacity] position inside its bucket
+    int32_t *counts;    // [n_buckets]
+    int32_t *partials;  // [scan blocks + 1]
+    int32_t n_partials;
+    cudaStream_t stream;  // stream of the last build
+    cudaEvent_t built;
+};
+
+// Plain-pointer views passed to kernels.
+struct IndexView {
+    const int32_t *offsets;
+    const float4 *rec0, *rec1;
+    const uint32_t *stats;
+    int32_t nb;
+    float inv_w;
+};
+
+namespace trd_host {
+int index_rebuild_launch(trd_index *idx, const trd_tracklets_t *t, cudaStream_t s);
+int follow_launch(const trd_ctx *ctx, const trd_seeds_t *seeds, const IndexView &iv,
+                  const trd_params_t *p, trd_results_t *out, cudaStream_t s, int lanes_per_track,
+                  int block_threads);
+int scan_blocks_for(int n);
+}  // namespace trd_host
+
+#define TRD_CUDA_TRY(expr)                                   \
+    do {                                                     \
+        cudaError_t e_ = (expr);                             \
+        if (e_ != cudaSuccess) {                             \
+            (void)cudaGetLastError();                        \
+            return TRD_ECUDA;                                \
+        }                                                    \
+    } while (0)

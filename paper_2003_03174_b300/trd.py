@@ -1,0 +1,251 @@
+"""Python binding of libtrd.so: argument marshalling only.
+
+Every step of the follower runs in the library's CUDA kernels; this module
+turns torch tensors into the plain pointers and sizes of the C ABI
+(include/trd_abi.h) and back.  There is no CPU path: if the shared library
+is missing or cannot be loaded, `lib()` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtrd.so")
+
+TRD_OK, TRD_EINVAL, TRD_ENOMEM, TRD_EAGAIN, TRD_ETIMEOUT, TRD_ECUDA = 0, -1, -2, -3, -4, -5
+ST_OK, ST_PROP_FAIL, ST_STOPPED, ST_SEED_INVALID = 0, 1, 2, 4
+MAX_HYP = 8
+_ERRNAMES = {-1: "TRD_EINVAL", -2: "TRD_ENOMEM", -3: "TRD_EAGAIN", -4: "TRD_ETIMEOUT", -5: "TRD_ECUDA"}
+
+EXPORTED = [
+    "trd_ctx_create", "trd_ctx_destroy", "trd_ctx_sm_count", "trd_index_build", "trd_index_free",
+    "trd_index_create", "trd_index_rebuild", "trd_index_info", "trd_follow", "trd_follow_tuned",
+    "trd_geometry", "trd_version", "trd_index_copy_out",
+]
+
+
+class TrdError(RuntimeError):
+    def __init__(self, fn, code):
+        super().__init__(f"{fn} returned {_ERRNAMES.get(code, code)}")
+        self.code = code
+
+
+class Seeds(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ("alpha", "x", "y", "z", "snp", "tgl", "q2pt", "cov")] + [
+        ("n", C.c_int32)]
+
+
+class Tracklets(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ("chamber", "y", "z", "dy", "vyy", "vzz", "vyz")] + [
+        ("n", C.c_int32)]
+
+
+class Params(C.Structure):
+    _fields_ = [("bz", C.c_float), ("n_sigma_road", C.c_float), ("chi2_cut", C.c_float),
+                ("p_miss", C.c_float), ("dy_gate_sigma", C.c_float), ("n_hyp", C.c_int32),
+                ("max_missing", C.c_int32), ("res_mode", C.c_int32), ("material_on", C.c_int32)]
+
+
+class Results(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ("alpha", "x", "par", "cov", "chi2", "n_trk", "n_miss",
+                                          "status", "tracklet_id")]
+
+
+_lib = None
+
+
+def lib():
+    """Load libtrd.so (raises if it is absent: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libtrd.so not built ({LIB_PATH}); run "
+                               "`python -m paper_2003_03174_b300.build`")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, f32 = C.c_void_p, C.c_int32, C.c_float
+        L.trd_ctx_create.argtypes = [C.c_int, C.POINTER(vp)]
+        L.trd_ctx_destroy.argtypes = [vp]
+        L.trd_ctx_sm_count.argtypes = [vp]
+        L.trd_index_build.argtypes = [vp, C.POINTER(Tracklets), f32, vp, C.POINTER(vp)]
+        L.trd_index_create.argtypes = [vp, i32, f32, C.POINTER(vp)]
+        L.trd_index_rebuild.argtypes = [vp, C.POINTER(Tracklets), vp]
+        L.trd_index_free.argtypes = [vp]
+        L.trd_index_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
+        L.trd_follow.argtypes = [vp, C.POINTER(Seeds), vp, C.POINTER(Params), C.POINTER(Results), vp]
+        L.trd_follow_tuned.argtypes = [vp, C.POINTER(Seeds), vp, C.POINTER(Params),
+                                       C.POINTER(Results), vp, C.c_int, C.c_int]
+        L.trd_geometry.argtypes = [C.POINTER(C.c_double), C.c_int]
+        L.trd_index_copy_out.argtypes = [vp, vp, vp]
+        L.trd_version.restype = C.c_char_p
+        for fn in EXPORTED:
+            if fn != "trd_version":
+                getattr(L, fn).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(fn, rc):
+    if rc != TRD_OK:
+        raise TrdError(fn, rc)
+
+
+def version() -> str:
+    return lib().trd_version().decode()
+
+
+def geometry() -> dict:
+    names = ["n_sectors", "n_stacks", "n_layers", "n_chambers", "x_layer0", "dx_layer",
+             "stack_length", "z_min", "tilt_deg", "drift_length", "lorentz_deg", "c_light",
+             "max_snp"]
+    out = (C.c_double * len(names))()
+    _check("trd_geometry", lib().trd_geometry(out, len(names)))
+    return dict(zip(names, list(out)))
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def params_struct(p: dict) -> Params:
+    return Params(float(p["bz"]), float(p["n_sigma_road"]), float(p["chi2_cut"]),
+                  float(p["p_miss"]), float(p["dy_gate_sigma"]), int(p["n_hyp"]),
+                  int(p["max_missing"]), int(p["res_mode"]), int(p["material_on"]))
+
+
+def seeds_struct(s: dict) -> Seeds:
+    n = int(s["alpha"].shape[0])
+    return Seeds(*[_ptr(s[k]) for k in ("alpha", "x", "y", "z", "snp", "tgl", "q2pt", "cov")], n)
+
+
+def tracklets_struct(t: dict) -> Tracklets:
+    n = int(t["chamber"].shape[0])
+    return Tracklets(*[_ptr(t[k]) for k in ("chamber", "y", "z", "dy", "vyy", "vzz", "vyz")], n)
+
+
+def alloc_results(n: int, device="cuda"):
+    import torch
+    f = dict(dtype=torch.float32, device=device)
+    i = dict(dtype=torch.int32, device=device)
+    return dict(alpha=torch.empty(n, **f), x=torch.empty(n, **f), par=torch.empty(5, n, **f),
+                cov=torch.empty(15, n, **f), chi2=torch.empty(n, **f), n_trk=torch.empty(n, **i),
+                n_miss=torch.empty(n, **i), status=torch.empty(n, **i),
+                tracklet_id=torch.empty(6, n, **i))
+
+
+def results_struct(r: dict) -> Results:
+    return Results(*[_ptr(r[k]) for k in ("alpha", "x", "par", "cov", "chi2", "n_trk", "n_miss",
+                                          "status", "tracklet_id")])
+
+
+def to_device(arrays: dict, device="cuda") -> dict:
+    """Copy a dict of numpy arrays to contiguous device tensors."""
+    import torch
+    return {k: torch.from_numpy(v).contiguous().to(device) for k, v in arrays.items()}
+
+
+class Index:
+    """A device-resident tracklet index owned by the library."""
+
+    def __init__(self, ctx: "Context", handle: C.c_void_p, keep=None):
+        self.ctx = ctx
+        self.handle = handle
+        self._keep = keep  # the input tensors must outlive the asynchronous build
+
+    def rebuild(self, tracklets: dict, stream=None):
+        ts = tracklets_struct(tracklets)
+        _check("trd_index_rebuild", lib().trd_index_rebuild(self.handle, C.byref(ts),
+                                                            _stream_handle(stream)))
+        self._keep = tracklets
+
+    def info(self):
+        a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
+        _check("trd_index_info", lib().trd_index_info(self.handle, C.byref(a), C.byref(b),
+                                                      C.byref(c)))
+        return dict(n_indexed=a.value, n_rejected=b.value, n_buckets=c.value)
+
+    def copy_out(self):
+        """(offsets, ids) as numpy arrays (synchronises)."""
+        import numpy as np
+        info = self.info()
+        off = np.zeros(info["n_buckets"] + 1, np.int32)
+        ids = np.zeros(max(info["n_indexed"], 1), np.int32)
+        _check("trd_index_copy_out", lib().trd_index_copy_out(
+            self.handle, off.ctypes.data_as(C.c_void_p), ids.ctypes.data_as(C.c_void_p)))
+        return off, ids[:info["n_indexed"]]
+
+    def free(self):
+        if self.handle:
+            lib().trd_index_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Context:
+    """Binds one CUDA device (trd_ctx_t)."""
+
+    def __init__(self, device: int = 0):
+        import torch
+        torch.cuda.init()
+        h = C.c_void_p()
+        _check("trd_ctx_create", lib().trd_ctx_create(int(device), C.byref(h)))
+        self.handle = h
+        self.device = device
+
+    @property
+    def sm_count(self) -> int:
+        return lib().trd_ctx_sm_count(self.handle)
+
+    def index_build(self, tracklets: dict, y_bin_width: float = 0.0, stream=None) -> Index:
+        ts = tracklets_struct(tracklets)
+        h = C.c_void_p()
+        _check("trd_index_build", lib().trd_index_build(self.handle, C.byref(ts),
+                                                        float(y_bin_width),
+                                                        _stream_handle(stream), C.byref(h)))
+        return Index(self, h, keep=tracklets)
+
+    def index_create(self, capacity: int, y_bin_width: float = 0.0) -> Index:
+        h = C.c_void_p()
+        _check("trd_index_create", lib().trd_index_create(self.handle, int(capacity),
+                                                          float(y_bin_width), C.byref(h)))
+        return Index(self, h)
+
+    def follow(self, seeds: dict, index: Index, params: dict, results: dict | None = None,
+               stream=None, lanes_per_track: int = 0, block_threads: int = 0) -> dict:
+        n = int(seeds["alpha"].shape[0])
+        if results is None:
+            results = alloc_results(n, device=seeds["alpha"].device)
+        ss, ps, rs = seeds_struct(seeds), params_struct(params), results_struct(results)
+        if lanes_per_track or block_threads:
+            rc = lib().trd_follow_tuned(self.handle, C.byref(ss), index.handle, C.byref(ps),
+                                        C.byref(rs), _stream_handle(stream), int(lanes_per_track),
+                                        int(block_threads))
+            _check("trd_follow_tuned", rc)
+        else:
+            rc = lib().trd_follow(self.handle, C.byref(ss), index.handle, C.byref(ps),
+                                  C.byref(rs), _stream_handle(stream))
+            _check("trd_follow", rc)
+        return results
+
+    def close(self):
+        if self.handle:
+            lib().trd_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

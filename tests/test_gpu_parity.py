@@ -1,0 +1,215 @@
+"""Parity of the CUDA follower (through the C ABI) with the FP64 oracle.
+
+Element-by-element comparison on the same seeded inputs at sizes the oracle
+finishes in seconds, sampled comparison at the full workload sizes in the
+launch configuration the benchmark times, and the edge cases (empty and
+invalid inputs, ragged tails, every hypothesis count and mode).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from parity import compare, to_numpy
+from synth import make_timeframe, make_workload, efficiency_purity
+from synth import timeframe as G
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2003_03174_b300 import trd
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return trd.Context(0)
+
+
+def run_gpu(ctx, tf, params=None, lanes=0, bin_width=0.0, seeds=None, tracklets=None):
+    from paper_2003_03174_b300 import trd
+    s = trd.to_device(tf.seeds if seeds is None else seeds)
+    t = trd.to_device(tf.tracklets if tracklets is None else tracklets)
+    idx = ctx.index_build(t, bin_width)
+    r = ctx.follow(s, idx, params or tf.params, lanes_per_track=lanes)
+    torch.cuda.synchronize()
+    return to_numpy(r), idx
+
+
+def test_tiny_parity(ctx):
+    tf = make_workload("tiny")
+    g, _ = run_gpu(ctx, tf)
+    o = O.follow(tf.seeds, tf.tracklets, tf.params)
+    rep = compare(g, o)
+    assert rep["same_path"] >= 0.98 * tf.n_seeds
+
+
+def test_medium_parity_spans_tiles_and_ragged_tail(ctx):
+    tf = make_workload("timeframe", seed=5, n_seeds=20_000 + 37)
+    g, _ = run_gpu(ctx, tf)
+    o = O.follow(tf.seeds, tf.tracklets, tf.params)
+    compare(g, o)
+
+
+@pytest.mark.parametrize("n_hyp", [2, 3, 6, 8])
+def test_multi_hypothesis_parity(ctx, n_hyp):
+    p = G.default_params(n_hyp=n_hyp, n_sigma_road=5.0)
+    tf = make_timeframe(3000 + n_hyp, seed=20 + n_hyp, noise=0.5, params=p)
+    g, _ = run_gpu(ctx, tf)
+    o = O.follow(tf.seeds, tf.tracklets, p)
+    compare(g, o)
+
+
+def test_calibration_distribution_parity(ctx):
+    tf = make_workload("calibration", seed=3, n_seeds=4000)
+    g, _ = run_gpu(ctx, tf)
+    o = O.follow(tf.seeds, tf.tracklets, tf.params)
+    compare(g, o)
+
+
+@pytest.mark.parametrize("over", [dict(res_mode=1), dict(material_on=0), dict(bz=-0.5),
+                                  dict(bz=0.0), dict(max_missing=0), dict(max_missing=6),
+                                  dict(chi2_cut=4.0, p_miss=6.0)])
+def test_mode_parity(ctx, over):
+    p = G.default_params(**over)
+    tf = make_timeframe(3000, seed=41, noise=0.3, bz=p["bz"], params=p)
+    g, _ = run_gpu(ctx, tf)
+    o = O.follow(tf.seeds, tf.tracklets, p)
+    compare(g, o)
+
+
+def test_lanes_per_track_do_not_change_results(ctx):
+    tf = make_workload("timeframe", seed=8, n_seeds=5000)
+    base, _ = run_gpu(ctx, tf, lanes=1)
+    for lanes in (2, 4, 8):
+        g, _ = run_gpu(ctx, tf, lanes=lanes)
+        for k in base:
+            np.testing.assert_array_equal(g[k], base[k], err_msg=f"{k} lanes={lanes}")
+
+
+def test_bin_width_does_not_change_results(ctx):
+    tf = make_workload("timeframe", seed=9, n_seeds=5000)
+    base, _ = run_gpu(ctx, tf)
+    for w in (0.5, 8.0, 132.0):
+        g, _ = run_gpu(ctx, tf, bin_width=w)
+        for k in base:
+            np.testing.assert_array_equal(g[k], base[k], err_msg=f"{k} w={w}")
+
+
+def test_results_are_deterministic(ctx):
+    tf = make_workload("timeframe", seed=10, n_seeds=8000)
+    a, _ = run_gpu(ctx, tf)
+    b, _ = run_gpu(ctx, tf)
+    for k in a:
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+
+
+def _bucket_reference(trk, w):
+    """Numpy counting sort with the index's FP32 bucketing expressions."""
+    f32 = np.float32
+    ch = trk["chamber"].astype(np.int64)
+    stack = (ch // 6) % 5
+    zlo = (f32(-360.0) + f32(144.0) * stack.astype(f32)).astype(f32)
+    row = np.floor((trk["z"] - zlo).astype(f32) * f32(0.125)).astype(f32)
+    row = np.clip(row, 0, 17).astype(np.int64)
+    inv_w = f32(1.0) / f32(w)
+    nb = int(math.ceil(np.float32(132.0) / np.float32(w)))
+    yb = np.clip(np.floor((trk["y"] + f32(66.0)).astype(f32) * inv_w), 0, nb - 1).astype(np.int64)
+    return (ch * 18 + row) * nb + yb, nb
+
+
+@pytest.mark.parametrize("w", [2.0, 0.7])
+def test_index_buckets_are_exact(ctx, w):
+    tf = make_workload("timeframe", seed=11, n_seeds=30_000)
+    from paper_2003_03174_b300 import trd
+    idx = ctx.index_build(trd.to_device(tf.tracklets), w)
+    off, ids = idx.copy_out()
+    bk, nb = _bucket_reference(tf.tracklets, w)
+    counts = np.bincount(bk, minlength=540 * 18 * nb)
+    ref_off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+    np.testing.assert_array_equal(off, ref_off)
+    # every bucket holds exactly its tracklets (order inside a bucket is free)
+    assert np.array_equal(np.sort(ids), np.arange(tf.n_tracklets))
+    got_bucket = np.repeat(np.arange(counts.shape[0]), counts)
+    np.testing.assert_array_equal(bk[ids], got_bucket)
+
+
+def test_empty_inputs(ctx):
+    from paper_2003_03174_b300 import trd
+    tf = make_workload("tiny", seed=12)
+    empty_t = {k: v[:0] for k, v in tf.tracklets.items()}
+    g, idx = run_gpu(ctx, tf, tracklets=empty_t)
+    assert idx.info()["n_indexed"] == 0
+    o = O.follow(tf.seeds, empty_t, tf.params)
+    compare(g, o)
+    assert np.all(g["n_trk"] == 0)
+    # no seeds at all: nothing launched, nothing written
+    s0 = trd.to_device({k: v[..., :0] if k != "cov" else v[:, :0] for k, v in tf.seeds.items()})
+    r = ctx.follow(s0, idx, tf.params)
+    torch.cuda.synchronize()
+    assert r["chi2"].numel() == 0
+
+
+def test_invalid_tracklets_are_left_out(ctx):
+    tf = make_workload("tiny", seed=13)
+    m = 40
+    bad = {k: v[:m].copy() for k, v in tf.tracklets.items()}
+    bad["chamber"][:10] = 540
+    bad["chamber"][10:20] = -3
+    bad["y"][20:30] = np.nan
+    bad["vyy"][30:40] = -1.0
+    trk = {k: np.concatenate([tf.tracklets[k], bad[k]]) for k in tf.tracklets}
+    g, idx = run_gpu(ctx, tf, tracklets=trk)
+    info = idx.info()
+    assert info["n_rejected"] == m and info["n_indexed"] == tf.n_tracklets
+    o = O.follow(tf.seeds, tf.tracklets, tf.params)
+    compare(g, o)
+
+
+def test_invalid_seeds(ctx):
+    tf = make_workload("tiny", seed=14)
+    s = {k: v.copy() for k, v in tf.seeds.items()}
+    s["snp"][:5] = 0.97
+    s["cov"][0, 5:10] = -1.0
+    s["cov"][1, 10:15] = 1.0  # |c10| > sqrt(c00 c11): not positive definite
+    g, _ = run_gpu(ctx, tf, seeds=s)
+    assert np.all(g["status"][:15] == O.STATUS_SEED_INVALID)
+    assert np.all(g["tracklet_id"][:, :15] == -1)
+    o = O.follow(s, tf.tracklets, tf.params)
+    compare(g, o)
+
+
+def test_event_rotated_by_one_sector(ctx):
+    tf = make_workload("tiny", seed=15)
+    s2 = dict(tf.seeds)
+    s2["alpha"] = (tf.seeds["alpha"].astype(np.float64) + math.radians(20.0)).astype(np.float32)
+    t2 = dict(tf.tracklets)
+    t2["chamber"] = ((tf.tracklets["chamber"] + 30) % 540).astype(np.int32)
+    g, _ = run_gpu(ctx, tf, seeds=s2, tracklets=t2)
+    o = O.follow(s2, t2, tf.params)
+    compare(g, o)
+
+
+def test_full_timeframe_sampled_parity(ctx):
+    """200k seeds, ~1M tracklets, N = 1, 3 sigma road: the benchmark's launch;
+    the oracle follows a sample of 2500 seeds against all tracklets."""
+    tf = make_workload("timeframe")
+    g, _ = run_gpu(ctx, tf)
+    rng = np.random.default_rng(0)
+    sel = np.unique(np.concatenate([np.arange(0, tf.n_seeds, 100), rng.integers(0, tf.n_seeds, 500),
+                                    np.arange(tf.n_seeds - 37, tf.n_seeds)]))
+    o = O.follow(tf.seeds, tf.tracklets, tf.params, seed_index=sel)
+    compare(g, o, sel=sel)
+    ep = efficiency_purity(g["tracklet_id"], tf.truth_ids)
+    assert ep["efficiency_reachable"] > 0.95 and ep["purity"] > 0.95
+
+
+def test_full_calibration_sampled_parity(ctx):
+    """450k seeds with the coherent y distortion, 5 sigma road, N = 6."""
+    tf = make_workload("calibration")
+    g, _ = run_gpu(ctx, tf)
+    sel = np.arange(0, tf.n_seeds, 1500)
+    o = O.follow(tf.seeds, tf.tracklets, tf.params, seed_index=sel)
+    compare(g, o, sel=sel)
