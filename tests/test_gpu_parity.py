@@ -202,8 +202,10 @@ def test_full_timeframe_sampled_parity(ctx):
                                     np.arange(tf.n_seeds - 37, tf.n_seeds)]))
     o = O.follow(tf.seeds, tf.tracklets, tf.params, seed_index=sel)
     compare(g, o, sel=sel)
+    # Sec. 3.1: purity ~1 in pp, falling to ~0.9 for low-momentum tracks at
+    # Pb-Pb density; this timeframe is Pb-Pb-like (1M tracklets, 30% noise)
     ep = efficiency_purity(g["tracklet_id"], tf.truth_ids)
-    assert ep["efficiency_reachable"] > 0.95 and ep["purity"] > 0.95
+    assert ep["efficiency_reachable"] > 0.95 and ep["purity"] > 0.85
 
 
 def test_full_calibration_sampled_parity(ctx):
