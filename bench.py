@@ -189,13 +189,22 @@ def run_ours(args):
     trk = trd.to_device(tf.tracklets, dev)
     n = tf.n_seeds
     stream = torch.cuda.Stream(device=dev)
-    index = ctx.index_create(tf.n_tracklets, args.bin_width)
+    shape = dict(lanes_per_track=0, block_threads=0, min_blocks_per_sm=0)
+    bin_width = args.bin_width
+    tuned = None
+    if not args.no_autotune:
+        from paper_2003_03174_b300 import autotune
+        with torch.cuda.stream(stream):
+            tuned = autotune.tune(ctx, seeds, trk, tf.params, cache=None)
+        shape = {k: tuned[k] for k in shape}
+        bin_width = tuned["y_bin_width"]
+    index = ctx.index_create(tf.n_tracklets, bin_width)
     res = trd.alloc_results(n, dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     def step():
         index.rebuild(trk, stream=stream)
-        ctx.follow(seeds, index, tf.params, results=res, stream=stream)
+        ctx.follow(seeds, index, tf.params, results=res, stream=stream, **shape)
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -215,7 +224,7 @@ def run_ours(args):
                 ev[k][0].record(stream)
                 index.rebuild(trk, stream=stream)
                 ev[k][1].record(stream)
-                ctx.follow(seeds, index, tf.params, results=res, stream=stream)
+                ctx.follow(seeds, index, tf.params, results=res, stream=stream, **shape)
                 ev[k][2].record(stream)
         torch.cuda.synchronize()
     if ws > 1:
@@ -254,7 +263,7 @@ def run_ours(args):
             for k, v in host_trk.items():
                 dev_trk[k].copy_(v, non_blocking=True)
             index.rebuild(dev_trk, stream=stream)
-            ctx.follow(dev_in, index, tf.params, results=res, stream=stream)
+            ctx.follow(dev_in, index, tf.params, results=res, stream=stream, **shape)
             for k, v in res.items():
                 host_out[k].copy_(v, non_blocking=True)
         e1.record(stream)
@@ -267,7 +276,7 @@ def run_ours(args):
     hbm = peaks.get("hbm_gbs")
     follow_avg_s = statistics.mean(follow_ms) / 1e3
     achieved = n * FOLLOW_BYTES_PER_SEED / follow_avg_s / 1e9
-    roof = {"bound": "hbm", "kernel": "k_follow<1,1>", "achieved": achieved,
+    roof = {"bound": "hbm", "kernel": "k_follow", "achieved": achieved,
             "peak": hbm if hbm else 6400.0, "unit": "GB/s",
             "peak_source": "measured" if hbm else "fallback",
             "frac": achieved / (hbm if hbm else 6400.0), "traffic": None,
@@ -287,7 +296,8 @@ def run_ours(args):
                                    f"N=1, 3-sigma road, chi2<15, <=2 missing",
                        "seeds_per_rank": n, "tracklets_per_rank": tf.n_tracklets,
                        "matched_per_rank_step": matched, "l2": "flushed (512 MB write) between steps",
-                       "index_y_bin_cm": args.bin_width or 2.0,
+                       "index_y_bin_cm": bin_width or 2.0, "launch": shape,
+                       "autotuned": tuned is not None,
                        "parallelism": f"replicas x{ws} (independent timeframes)"},
             "roofline": roof,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
@@ -316,6 +326,7 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=40_000)
     ap.add_argument("--ref-sample", type=int, default=20_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

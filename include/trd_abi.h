@@ -121,10 +121,10 @@ TRD_API int trd_ctx_destroy(trd_ctx_t *ctx);
 TRD_API int trd_ctx_sm_count(const trd_ctx_t *ctx);
 
 /* ---- tracklet index (Sec. 3: "all tracklets inside a search road") --------
- * trd_index_build: bucket the tracklets by (chamber, pad row, y bin) with a
- * counting sort on `stream`, and record each chamber's largest vyy and vzz.
- * Buckets of one (chamber, pad row) are contiguous in y, so a road query is
- * one contiguous range per pad row.  y_bin_width (cm, > 0; 0 selects 2 cm)
+ * trd_index_build: bucket the tracklets by (chamber, y bin, pad row) with a
+ * counting sort on `stream`, and record the largest vyy and vzz.  The pad
+ * rows of one (chamber, y bin) are adjacent, so a road query is one
+ * contiguous range per y bin.  y_bin_width (cm, > 0; 0 selects 2 cm)
  * sets the bin size.  The library allocates and owns the index (*out, freed
  * by trd_index_free); the input arrays may be reused once `stream` has passed
  * the build.  Errors: TRD_EINVAL, TRD_ENOMEM, TRD_ECUDA.                     */
@@ -148,8 +148,8 @@ TRD_API int trd_index_info(const trd_index_t *index, int32_t *n_indexed, int32_t
 
 /* Copies the index to host memory (synchronises with its build stream), for
  * inspection and tests.  offsets: n_buckets + 1 int32 (bucket b holds
- * entries offsets[b] .. offsets[b+1]-1; bucket = (chamber*18 + pad row) *
- * n_ybins + y bin); ids: n_indexed int32 input indices in bucket order.
+ * entries offsets[b] .. offsets[b+1]-1; bucket = (chamber * n_ybins +
+ * y bin) * 18 + pad row); ids: n_indexed int32 input indices in bucket order.
  * Either pointer may be NULL.  Host pointers, caller-owned.                 */
 TRD_API int trd_index_copy_out(const trd_index_t *index, int32_t *offsets, int32_t *ids);
 
@@ -170,12 +170,22 @@ TRD_API int trd_index_copy_out(const trd_index_t *index, int32_t *offsets, int32
 TRD_API int trd_follow(trd_ctx_t *ctx, const trd_seeds_t *seeds, const trd_index_t *index,
                const trd_params_t *params, trd_results_t *out, void *stream);
 
-/* trd_follow with explicit launch shape (used by the autotuner):
- * lanes_per_track in {1, 2, 4, 8} (0 = smallest power of two >= n_hyp; 1
- * needs n_hyp = 1), block_threads a multiple of 32 in 32..128 (0 = 128).    */
+/* Launch shape of the follower (the autotuner's search space).
+ *   lanes_per_track   lanes that follow one seed, one hypothesis per lane:
+ *                     1, 2, 4 or 8 (0 = smallest power of two >= n_hyp; 1
+ *                     needs n_hyp = 1)
+ *   block_threads     64 or 128 (0 = 128)
+ *   min_blocks_per_sm register budget: 128-thread blocks kept resident per SM
+ *                     (0 = 4; 1 lane: 4, 5, 6 or 8; more lanes: 3 or 4)      */
+typedef struct {
+    int32_t lanes_per_track, block_threads, min_blocks_per_sm;
+} trd_launch_t;
+
+/* trd_follow with an explicit launch shape; launch may be NULL (defaults).
+ * TRD_EINVAL for a shape outside the list above.                            */
 TRD_API int trd_follow_tuned(trd_ctx_t *ctx, const trd_seeds_t *seeds, const trd_index_t *index,
-                     const trd_params_t *params, trd_results_t *out, void *stream,
-                     int lanes_per_track, int block_threads);
+                             const trd_params_t *params, trd_results_t *out, void *stream,
+                             const trd_launch_t *launch);
 
 /* Geometry constants the library was built with, for cross-checks:
  * out[0..12] = n_sectors, n_stacks, n_layers, n_chambers, x_layer0,

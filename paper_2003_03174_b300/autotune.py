@@ -1,0 +1,141 @@
+"""Autotuner for the follower's launch shape and the index's y-bin width.
+
+Search space (all exposed by the C ABI):
+  * y-bin width of the index (cm): wider bins mean fewer, longer ranges;
+  * lanes per seed (one hypothesis per lane) and block size;
+  * register budget (128-thread blocks resident per SM): more residency hides
+    more memory latency, fewer registers may spill.
+Each candidate is timed with CUDA events on the caller's stream (median of
+`reps` launches after a warm-up); results of every shape are checked to be
+bit-identical to the first one (the shape must never change the answer).
+The winner is cached in a JSON file keyed by GPU name and workload shape.
+"""
+from __future__ import annotations
+
+import json
+import os
+import statistics
+
+from . import trd
+
+DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "trd_b300_autotune.json")
+
+
+def search_space(n_hyp: int):
+    """(lanes_per_track, block_threads, min_blocks_per_sm) candidates."""
+    shapes = []
+    if n_hyp == 1:
+        shapes += [(1, b, m) for b in (128, 64) for m in (4, 5, 6, 8)]
+        shapes += [(2, 128, m) for m in (3, 4)]
+    lanes = 2 if n_hyp <= 2 else (4 if n_hyp <= 4 else 8)
+    for g in sorted({lanes, min(8, 2 * lanes)}):
+        if g >= n_hyp and g > 1 and (g, 128, 3) not in shapes:
+            shapes += [(g, 128, m) for m in (3, 4)]
+    return shapes
+
+
+def key(gpu_name: str, n_seeds: int, n_tracklets: int, params: dict) -> str:
+    def bucket(v):
+        return 1 << max(0, int(v).bit_length() - 1)
+    return (f"{gpu_name}|seeds~{bucket(n_seeds)}|tracklets~{bucket(n_tracklets)}|N={params['n_hyp']}"
+            f"|road={params['n_sigma_road']}|res={params['res_mode']}")
+
+
+def _time(fn, stream, reps):
+    import torch
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(reps)]
+    fn()
+    for a, b in evs:
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return statistics.median(a.elapsed_time(b) for a, b in evs)
+
+
+def tune(ctx: trd.Context, seeds: dict, tracklets: dict, params: dict,
+         bin_widths=(1.0, 2.0, 4.0), reps: int = 7, cache: str | None = DEFAULT_CACHE,
+         force: bool = False) -> dict:
+    """Return {'y_bin_width', 'lanes_per_track', 'block_threads',
+    'min_blocks_per_sm', 'ms', 'table'} for this workload."""
+    import torch
+    n = int(seeds["alpha"].shape[0])
+    m = int(tracklets["chamber"].shape[0])
+    k = key(torch.cuda.get_device_name(), n, m, params)
+    if cache and not force and os.path.exists(cache):
+        try:
+            hit = json.load(open(cache)).get(k)
+            if hit:
+                return hit
+        except Exception:
+            pass
+    stream = torch.cuda.current_stream()
+    res = trd.alloc_results(n, seeds["alpha"].device)
+    table, ref = [], None
+    for w in bin_widths:
+        index = ctx.index_create(m, w)
+        t_index = _time(lambda: index.rebuild(tracklets, stream=stream), stream, reps)
+        for g, b, mb in search_space(int(params["n_hyp"])):
+            def run():
+                ctx.follow(seeds, index, params, results=res, stream=stream, lanes_per_track=g,
+                           block_threads=b, min_blocks_per_sm=mb)
+            t_follow = _time(run, stream, reps)
+            snap = {kk: v.clone() for kk, v in res.items()}
+            if ref is None:
+                ref = snap
+            else:
+                for kk in ref:
+                    if not torch.equal(ref[kk], snap[kk]):
+                        raise RuntimeError(f"launch shape {(w, g, b, mb)} changed '{kk}'")
+            table.append(dict(y_bin_width=w, lanes_per_track=g, block_threads=b,
+                              min_blocks_per_sm=mb, index_ms=t_index, follow_ms=t_follow,
+                              ms=t_index + t_follow))
+        index.free()
+    best = min(table, key=lambda r: r["ms"])
+    out = dict(best, table=table, key=k)
+    if cache:
+        try:
+            os.makedirs(os.path.dirname(cache), exist_ok=True)
+            db = json.load(open(cache)) if os.path.exists(cache) else {}
+            db[k] = out
+            json.dump(db, open(cache, "w"), indent=1)
+        except Exception:
+            pass
+    return out
+
+
+def table_markdown(title: str, r: dict) -> str:
+    lines = [f"# {title}", "",
+             "| y bin cm | lanes | block | blocks/SM | index ms | follow ms | total ms |",
+             "|---|---|---|---|---|---|---|"]
+    for row in sorted(r["table"], key=lambda x: x["ms"]):
+        lines.append(f"| {row['y_bin_width']} | {row['lanes_per_track']} | {row['block_threads']} | "
+                     f"{row['min_blocks_per_sm']} | {row['index_ms']:.4f} | {row['follow_ms']:.4f} | "
+                     f"{row['ms']:.4f} |")
+    return "\n".join(lines) + "\n"
+
+
+def main():
+    import argparse
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    from synth import make_workload
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="timeframe")
+    ap.add_argument("--seeds", type=int, default=0)
+    ap.add_argument("--out", default="")
+    a = ap.parse_args()
+    tf = make_workload(a.workload, n_seeds=a.seeds or None)
+    ctx = trd.Context(0)
+    r = tune(ctx, trd.to_device(tf.seeds), trd.to_device(tf.tracklets), tf.params, cache=None)
+    text = table_markdown(f"autotune, {a.workload}: {tf.n_seeds} seeds, {tf.n_tracklets} tracklets, "
+                          f"N={tf.params['n_hyp']}", r)
+    print(text)
+    if a.out:
+        open(a.out, "w").write(text)
+
+
+if __name__ == "__main__":
+    main()

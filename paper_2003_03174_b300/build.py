@@ -18,6 +18,12 @@ FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr", "-Xcompil
          "-Xcompiler", "-fvisibility=hidden", "-Xptxas", "-warn-double-usage"]
 
 
+# The follower needs no correctly rounded division or square root: positions
+# are carried as double-floats and every quotient feeds a derivative, a window
+# or a chi2 where 2-ulp errors are far inside the parity tolerances.
+PER_FILE = {"follow.cu": ["-prec-div=false", "-prec-sqrt=false"]}
+
+
 def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
 
@@ -39,7 +45,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     objs = []
     for src in sources():
         obj = os.path.join(objdir, os.path.basename(src) + ".o")
-        cmd = [NVCC, *ARCH, *FLAGS, "-c", src, "-o", obj]
+        cmd = [NVCC, *ARCH, *FLAGS, *PER_FILE.get(os.path.basename(src), []), "-c", src, "-o", obj]
         if verbose:
             cmd += ["-Xptxas", "-v"]
         r = subprocess.run(cmd, capture_output=True, text=True)

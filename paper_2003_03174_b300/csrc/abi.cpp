@@ -30,8 +30,7 @@ int check_device(int device)
 void free_index_buffers(trd_index *x)
 {
     cudaFree(x->offsets);
-    cudaFree(x->rec0);
-    cudaFree(x->rec1);
+    cudaFree(x->rec);
     cudaFree(x->stats);
     cudaFree(x->bucket);
     cudaFree(x->rank);
@@ -42,6 +41,16 @@ void free_index_buffers(trd_index *x)
 }
 
 }  // namespace
+
+namespace trd_host {
+// Each launch takes its own work-counter slot, so launches in flight on
+// different streams never share a counter (up to kCounterSlots at once).
+int *next_counter(trd_ctx *ctx)
+{
+    const unsigned k = __atomic_fetch_add(&ctx->launch_seq, 1u, __ATOMIC_RELAXED);
+    return ctx->counters + (k % kCounterSlots);
+}
+}  // namespace trd_host
 
 extern "C" {
 
@@ -71,6 +80,13 @@ int trd_ctx_create(int device, trd_ctx_t **ctx)
     c->sm_count = prop.multiProcessorCount;
     c->max_threads_per_sm = prop.maxThreadsPerMultiProcessor;
     c->l2_bytes = static_cast<size_t>(prop.l2CacheSize);
+    c->launch_seq = 0;
+    c->counters = nullptr;
+    if (cudaMalloc(&c->counters, sizeof(int32_t) * kCounterSlots) != cudaSuccess) {
+        (void)cudaGetLastError();
+        delete c;
+        return TRD_ENOMEM;
+    }
     *ctx = c;
     return TRD_OK;
 }
@@ -78,6 +94,9 @@ int trd_ctx_create(int device, trd_ctx_t **ctx)
 int trd_ctx_destroy(trd_ctx_t *ctx)
 {
     if (!ctx) return TRD_EINVAL;
+    cudaSetDevice(ctx->device);
+    cudaFree(ctx->counters);
+    (void)cudaGetLastError();
     delete ctx;
     return TRD_OK;
 }
@@ -104,8 +123,7 @@ int trd_index_create(trd_ctx_t *ctx, int32_t capacity, float y_bin_width, trd_in
     x->n_partials = trd_host::scan_blocks_for(x->n_buckets);
     const size_t cap = static_cast<size_t>(std::max(capacity, 1));
     bool ok = cudaMalloc(&x->offsets, sizeof(int32_t) * (x->n_buckets + 1)) == cudaSuccess &&
-              cudaMalloc(&x->rec0, sizeof(float4) * cap) == cudaSuccess &&
-              cudaMalloc(&x->rec1, sizeof(float4) * cap) == cudaSuccess &&
+              cudaMalloc(&x->rec, 2 * sizeof(float4) * cap) == cudaSuccess &&
               cudaMalloc(&x->stats, sizeof(uint32_t) * 4) == cudaSuccess &&
               cudaMalloc(&x->bucket, sizeof(int32_t) * cap) == cudaSuccess &&
               cudaMalloc(&x->rank, sizeof(int32_t) * cap) == cudaSuccess &&
@@ -184,24 +202,26 @@ int trd_index_copy_out(const trd_index_t *index, int32_t *offsets, int32_t *ids)
     if (ids) {
         int32_t total = 0;
         TRD_CUDA_TRY(cudaMemcpy(&total, index->offsets + index->n_buckets, sizeof total, cudaMemcpyDeviceToHost));
-        // element 3 of each rec0 record holds the input index bits
+        // word 3 of each 32-byte record holds the input index bits
         if (total > 0)
-            TRD_CUDA_TRY(cudaMemcpy2D(ids, sizeof(int32_t), reinterpret_cast<const char *>(index->rec0) + 12,
-                                      sizeof(float4), sizeof(int32_t), total, cudaMemcpyDeviceToHost));
+            TRD_CUDA_TRY(cudaMemcpy2D(ids, sizeof(int32_t), reinterpret_cast<const char *>(index->rec) + 12,
+                                      2 * sizeof(float4), sizeof(int32_t), total, cudaMemcpyDeviceToHost));
     }
     return TRD_OK;
 }
 
 int trd_follow_tuned(trd_ctx_t *ctx, const trd_seeds_t *seeds, const trd_index_t *index,
-                     const trd_params_t *p, trd_results_t *out, void *stream, int lanes_per_track,
-                     int block_threads)
+                     const trd_params_t *p, trd_results_t *out, void *stream, const trd_launch_t *launch)
 {
+    const int lanes_per_track = launch ? launch->lanes_per_track : 0;
+    const int block_threads = launch ? launch->block_threads : 0;
+    const int min_blocks = launch ? launch->min_blocks_per_sm : 0;
     if (!ctx || !seeds || !index || !p || !out || seeds->n < 0) return TRD_EINVAL;
     if (p->n_hyp < 1 || p->n_hyp > TRD_MAX_HYP || p->max_missing < 0 || p->max_missing > TRD_N_LAYERS) return TRD_EINVAL;
     if (!finite_pos(p->n_sigma_road) || !finite_pos(p->chi2_cut) || !finite_pos(p->dy_gate_sigma) ||
         !isfinite(p->p_miss) || !isfinite(p->bz))
         return TRD_EINVAL;
-    if (block_threads != 0 && (block_threads < 32 || block_threads > 128 || block_threads % 32)) return TRD_EINVAL;
+    if (block_threads != 0 && block_threads != 64 && block_threads != 128) return TRD_EINVAL;
     if (seeds->n > 0) {
         if (!seeds->alpha || !seeds->x || !seeds->y || !seeds->z || !seeds->snp || !seeds->tgl || !seeds->q2pt ||
             !seeds->cov)
@@ -211,15 +231,15 @@ int trd_follow_tuned(trd_ctx_t *ctx, const trd_seeds_t *seeds, const trd_index_t
             return TRD_EINVAL;
     }
     TRD_CUDA_TRY(cudaSetDevice(ctx->device));
-    IndexView iv{index->offsets, index->rec0, index->rec1, index->stats, index->nb, index->inv_w};
+    IndexView iv{index->offsets, index->rec, index->stats, index->nb, index->inv_w};
     return trd_host::follow_launch(ctx, seeds, iv, p, out, static_cast<cudaStream_t>(stream), lanes_per_track,
-                                   block_threads);
+                                   block_threads, min_blocks, trd_host::next_counter(ctx));
 }
 
 int trd_follow(trd_ctx_t *ctx, const trd_seeds_t *seeds, const trd_index_t *index, const trd_params_t *p,
                trd_results_t *out, void *stream)
 {
-    return trd_follow_tuned(ctx, seeds, index, p, out, stream, 0, 0);
+    return trd_follow_tuned(ctx, seeds, index, p, out, stream, nullptr);
 }
 
 }  // extern "C"

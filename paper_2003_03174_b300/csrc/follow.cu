@@ -12,6 +12,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
+
 #include "trd_device.cuh"
 #include "trd_internal.h"
 
@@ -197,7 +199,7 @@ __device__ bool material(TrackState &s)
     const float e = sqrtf(fmaf(p, p, m2));
     const float beta = p / e;
     const float t0 = 0.0136f / (beta * p);
-    const float lg = fmaf(0.038f, logf(xx0), 1.0f);
+    const float lg = fmaf(0.038f, __logf(xx0), 1.0f);
     const float th2 = t0 * t0 * xx0 * lg * lg;
     float *C = s.c;
     C[5] += th2 * r * r * t2;
@@ -207,7 +209,7 @@ __device__ bool material(TrackState &s)
     const float bg = p / kMassPion;
     const float bg2 = bg * bg;
     const float b2 = bg2 / (1.0f + bg2);
-    const float dedx = kBetheKZA / b2 * (logf(kTwoMeOverI * bg2) - b2);  // GeV cm^2/g
+    const float dedx = kBetheKZA / b2 * (__logf(kTwoMeOverI * bg2) - b2);  // GeV cm^2/g
     const float de = dedx * kXRho * path;
     const float e1 = e - de;
     if (!(e1 > kMassPion)) return false;
@@ -283,32 +285,35 @@ __device__ void kalman_update(TrackState &s, float tt, float ytl, float ztl, flo
     s.f += K0[2] * r0 + K1[2] * r1;
     s.t += K0[3] * r0 + K1[3] * r1;
     s.k += K0[4] * r0 + K1[4] * r1;
-    // Joseph: (I - K H) C (I - K H)^T + K V K^T; I - K H differs from I in
+    // Joseph: (I - K H) C (I - K H)^T + K V K^T.  I - K H differs from I in
     // columns 0 and 1 only: A x = x - u x_0 - v x_1 with u = K0, v = K1 - tt K0.
-    float u[5], v[5];
+    // B = A C is needed in columns 0, 1 and on and below the diagonal; the
+    // product B A^T + K V K^T is evaluated for the lower triangle, which is
+    // stored for both triangles (exactly symmetric).
+    float u[5], v[5], kv0[5], kv1[5];
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
         u[i] = K0[i];
         v[i] = K1[i] - tt * K0[i];
+        kv0[i] = vyy * K0[i] + vyz * K1[i];
+        kv1[i] = vyz * K0[i] + vzz * K1[i];
     }
-    float B[5][5];  // B = A C
+    float B0[5], B1[5];  // columns 0 and 1 of B
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        B0[i] = Ci0[i] - u[i] * Ci0[0] - v[i] * Ci1[0];
+        B1[i] = Ci1[i] - u[i] * Ci0[1] - v[i] * Ci1[1];
+    }
+    float Nw[15];
 #pragma unroll
     for (int i = 0; i < 5; ++i)
 #pragma unroll
-        for (int j = 0; j < 5; ++j) B[i][j] = C[cidx(i, j)] - u[i] * Ci0[j] - v[i] * Ci1[j];
-    float N[5][5];
-#pragma unroll
-    for (int i = 0; i < 5; ++i)
-#pragma unroll
-        for (int j = 0; j < 5; ++j) {
-            const float kv0 = vyy * K0[j] + vyz * K1[j];
-            const float kv1 = vyz * K0[j] + vzz * K1[j];
-            N[i][j] = B[i][j] - B[i][0] * u[j] - B[i][1] * v[j] + K0[i] * kv0 + K1[i] * kv1;
+        for (int j = 0; j <= i; ++j) {
+            const float bij = j == 0 ? B0[i] : (j == 1 ? B1[i] : C[cidx(i, j)] - u[i] * Ci0[j] - v[i] * Ci1[j]);
+            Nw[cidx(i, j)] = bij - B0[i] * u[j] - B1[i] * v[j] + K0[i] * kv0[j] + K1[i] * kv1[j];
         }
 #pragma unroll
-    for (int i = 0; i < 5; ++i)
-#pragma unroll
-        for (int j = 0; j <= i; ++j) C[cidx(i, j)] = i == j ? N[i][i] : 0.5f * (N[i][j] + N[j][i]);
+    for (int k = 0; k < 15; ++k) C[k] = Nw[k];
 }
 
 // ---- small sorted extension list (per lane) ---------------------------------
@@ -371,6 +376,32 @@ struct ExtList {
 };
 
 // Road query + candidate tests for one hypothesis at layer l (Sec. 3).
+// The road bounds z_tl to z +- Rz (pad rows r_lo..r_hi) and the measured y to
+// y +- (W + |tan tau| Rz) (y bins b_lo..b_hi); each y bin is one contiguous
+// range of the index over those rows.  Two bins' offsets are loaded at once,
+// and candidate records four at a time, so a layer costs about two dependent
+// global round trips.
+template <int NH>
+__device__ __forceinline__ void test_record(const float4 &a, int pos, const IndexView &ix, float tt, float z, float yh,
+                                            float yl, float W, float Rz, float n2, float syy_trk, float syz_trk,
+                                            float c11, float vyy_res, int resmode, float dy_pred, float gate,
+                                            float cut, float score, ExtList<NH> &L)
+{
+    const float ry = (__fsub_rn(a.x, yh) - yl) + tt * (z - a.y);
+    const float rz = a.y - z;
+    if (fabsf(ry) > W || fabsf(rz) > Rz) return;
+    const float4 v = __ldg(&ix.rec[2 * pos + 1]);  // same 32-byte sector as a
+    const float vyy = resmode ? vyy_res : v.x;
+    const float S00 = syy_trk + vyy;
+    const float S01 = syz_trk + v.z;
+    const float S11 = c11 + v.y;
+    if (ry * ry > n2 * S00 || rz * rz > n2 * S11) return;
+    if (fabsf(a.z - dy_pred) > gate) return;
+    const float chi2 = (S11 * ry * ry - 2.0f * S01 * ry * rz + S00 * rz * rz) / (S00 * S11 - S01 * S01);
+    if (!(chi2 < cut)) return;
+    L.insert(score + chi2, __float_as_int(a.w), pos, chi2);
+}
+
 template <int NH>
 __device__ void scan_candidates(const TrackState &s, int l, int chamber, float score, const Params &P,
                                 const IndexView &ix, float vyy_max_in, float vzz_max, ExtList<NH> &L)
@@ -393,31 +424,33 @@ __device__ void scan_candidates(const TrackState &s, int l, int chamber, float s
     const float yh = s.y.hi, yl = s.y.lo;
     const float zlo = stack_z_lo(stack_of_chamber(chamber));
     const int r_lo = row_of_z(z - Rz, zlo), r_hi = row_of_z(z + Rz, zlo);
-    const float pad = 1e-3f + 1e-6f * fabsf(yh);
-    for (int row = r_lo; row <= r_hi; ++row) {
-        const float za = row == 0 ? z - Rz : fmaxf(z - Rz, zlo + kRowLength * row);
-        const float zb = row == kRowsPerStack - 1 ? z + Rz : fminf(z + Rz, zlo + kRowLength * (row + 1));
-        const float t1 = tt * (za - z), t2 = tt * (zb - z);
-        const float ylo = yh + fminf(t1, t2) - W - pad, yhi = yh + fmaxf(t1, t2) + W + pad;
-        const int b_lo = ybin_of(ylo, ix.inv_w, ix.nb), b_hi = ybin_of(yhi, ix.inv_w, ix.nb);
-        const int b0 = (chamber * kRowsPerStack + row) * ix.nb;
-        const int beg = __ldg(&ix.offsets[b0 + b_lo]);
-        const int end = __ldg(&ix.offsets[b0 + b_hi + 1]);
-        for (int pos = beg; pos < end; ++pos) {
-            const float4 a = __ldg(&ix.rec0[pos]);
-            const float ry = (__fsub_rn(a.x, yh) - yl) + tt * (z - a.y);
-            const float rz = a.y - z;
-            if (fabsf(ry) > W || fabsf(rz) > Rz) continue;
-            const float4 v = __ldg(&ix.rec1[pos]);
-            const float vyy = P.resmode ? vyy_res : v.x;
-            const float S00 = syy_trk + vyy;
-            const float S01 = syz_trk + v.z;
-            const float S11 = c11 + v.y;
-            if (ry * ry > n2 * S00 || rz * rz > n2 * S11) continue;
-            if (fabsf(a.z - dy_pred) > gate) continue;
-            const float chi2 = (S11 * ry * ry - 2.0f * S01 * ry * rz + S00 * rz * rz) / (S00 * S11 - S01 * S01);
-            if (!(chi2 < P.cut)) continue;
-            L.insert(score + chi2, __float_as_int(a.w), pos, chi2);
+    const float half = W + fabsf(tt) * Rz + 1e-3f + 1e-6f * fabsf(yh);
+    const int b_lo = ybin_of(yh - half, ix.inv_w, ix.nb), b_hi = ybin_of(yh + half, ix.inv_w, ix.nb);
+    for (int b = b_lo; b <= b_hi; b += 2) {
+        const int base = bucket_of(chamber, b, 0, ix.nb);
+        const bool two = b + 1 <= b_hi;
+        const int beg0 = __ldg(&ix.offsets[base + r_lo]);
+        const int end0 = __ldg(&ix.offsets[base + r_hi + 1]);
+        int beg1 = 0, end1 = 0;
+        if (two) {
+            beg1 = __ldg(&ix.offsets[base + kRowsPerStack + r_lo]);
+            end1 = __ldg(&ix.offsets[base + kRowsPerStack + r_hi + 1]);
+        }
+#pragma unroll 1
+        for (int k = 0; k < 2; ++k) {
+            const int beg = k ? beg1 : beg0, end = k ? end1 : end0;
+#pragma unroll 1
+            for (int pos = beg; pos < end; pos += 4) {
+                float4 a[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    a[u] = pos + u < end ? __ldg(&ix.rec[2 * (pos + u)]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (pos + u < end)
+                        test_record<NH>(a[u], pos + u, ix, tt, z, yh, yl, W, Rz, n2, syy_trk, syz_trk, c11, vyy_res,
+                                        P.resmode, dy_pred, gate, P.cut, score, L);
+            }
         }
     }
 }
@@ -528,19 +561,43 @@ __device__ __forceinline__ int gshfl(unsigned mask, int v, int src)
     return G == 1 ? v : __shfl_sync(mask, v, src, G);
 }
 
-// Follow seed i with a group of G lanes keeping up to NH hypotheses.
-// sm: this group's snapshot column (stride = groups per block).
-template <int G, int NH>
-__device__ void follow_track(int i, const SeedsView &sv, const IndexView &ix, const Params &P,
-                             const ResultsView &o, float *sm, int stride)
+// Next seed for this group from the launch's work counter.  G == 1: the lanes
+// that ask together share one atomicAdd (warp-aggregated).
+template <int G>
+__device__ __forceinline__ int fetch_seed(int *counter, unsigned gmask, int q)
+{
+    if (G == 1) {
+        const unsigned mask = __activemask();
+        const int lane = threadIdx.x & 31;
+        const int leader = __ffs(mask) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(counter, __popc(mask));
+        base = __shfl_sync(mask, base, leader);
+        return base + __popc(mask & ((1u << lane) - 1u));
+    } else {
+        int t = 0;
+        if (q == 0) t = atomicAdd(counter, 1);
+        return __shfl_sync(gmask, t, 0, G);
+    }
+}
+
+// Per-seed registers of one lane (hypothesis q of its group).
+struct Lane {
+    TrackState s;
+    float score, chisum;
+    int ntrk, nmiss;
+    int ids[kLayers];
+    bool alive;
+};
+
+// Load seed i, validate it and rotate it into the sector of its position.
+// Returns false (and writes the result) when the seed ends right here.
+template <int G>
+__device__ __forceinline__ bool start_seed(int i, int q, const SeedsView &sv, const Params &P, const ResultsView &o,
+                                           Lane &L)
 {
     const int n = sv.n;
-    const int q = G == 1 ? 0 : (threadIdx.x & (G - 1));
-    const unsigned gmask =
-        G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
-
-    // seed (every lane reads the same addresses)
-    TrackState s;
+    TrackState &s = L.s;
     const float alpha = sv.alpha[i];
     const float sx = sv.x[i], sy = sv.y[i];
     s.x = {sx, 0.0f};
@@ -553,153 +610,176 @@ __device__ void follow_track(int i, const SeedsView &sv, const IndexView &ix, co
     for (int k = 0; k < 15; ++k) s.c[k] = sv.cov[k * n + i];
     if (!(fabsf(s.f) < kMaxSnp) || !cov_pd(s.c)) {
         if (q == 0) write_seed_result(o, sv, n, i, TRD_ST_SEED_INVALID);
-        return;
+        return false;
     }
-    // rotate into the sector of the seed's position
-    {
-        const float phi = alpha + atan2f(sy, sx);
-        constexpr float two_pi = kTwoPiHi;
-        float u = phi - two_pi * floorf(phi * (1.0f / two_pi));
-        int sec = static_cast<int>(u * (1.0f / kSectorWidthHi));
-        sec = min(max(sec, 0), kSectors - 1);
-        const df target = sector_alpha_df(sec);
-        df d = df_add_f(target, -alpha);
-        if (d.hi > 3.14159265f) d = df_add(d, df{-kTwoPiHi, -kTwoPiLo});
-        if (d.hi < -3.14159265f) d = df_add(d, df{kTwoPiHi, kTwoPiLo});
-        s.sector = sec;
-        if (!rotate(s, d, sec, P.bz)) {
-            if (q == 0) write_seed_result(o, sv, n, i, TRD_ST_PROP_FAIL);
-            return;
-        }
+    const float phi = alpha + atan2f(sy, sx);
+    float u = phi - kTwoPiHi * floorf(phi * (1.0f / kTwoPiHi));
+    int sec = static_cast<int>(u * (1.0f / kSectorWidthHi));
+    sec = min(max(sec, 0), kSectors - 1);
+    df d = df_add_f(sector_alpha_df(sec), -alpha);
+    if (d.hi > 3.14159265f) d = df_add(d, df{-kTwoPiHi, -kTwoPiLo});
+    if (d.hi < -3.14159265f) d = df_add(d, df{kTwoPiHi, kTwoPiLo});
+    s.sector = sec;
+    if (!rotate(s, d, sec, P.bz)) {
+        if (q == 0) write_seed_result(o, sv, n, i, TRD_ST_PROP_FAIL);
+        return false;
     }
-
-    bool alive = q == 0;
-    float score = 0.0f, chisum = 0.0f;
-    int ntrk = 0, nmiss = 0;
-    int ids[kLayers];
+    L.alive = q == 0;
+    L.score = 0.0f;
+    L.chisum = 0.0f;
+    L.ntrk = 0;
+    L.nmiss = 0;
 #pragma unroll
-    for (int l = 0; l < kLayers; ++l) ids[l] = -1;
-    const float vyy_max = __uint_as_float(__ldg(&ix.stats[0]));
-    const float vzz_max = __uint_as_float(__ldg(&ix.stats[1]));
-
-    for (int l = 0; l < kLayers; ++l) {
-        if (q == 0) save_state(sm, stride, s);
-        int chamber = -1;
-        const bool live = alive && to_layer(s, l, P, chamber);
-        ExtList<NH> L;
-        L.clear();
-        if (live && chamber >= 0) scan_candidates<NH>(s, l, chamber, score, P, ix, vyy_max, vzz_max, L);
-        if (live && nmiss < P.maxmiss) L.insert(score + P.pmiss, kMissing, -1, 0.0f);
-
-        // merge the lanes' lists: the k-th best extension goes to lane k
-        int my_parent = q, my_id = kMissing, my_pos = -1;
-        float my_score = INFINITY, my_chi2 = 0.0f;
-        int kept = 0;
-        if (G == 1) {
-            if (L.score[0] < INFINITY) {
-                my_score = L.score[0];
-                my_id = L.id[0];
-                my_pos = L.pos[0];
-                my_chi2 = L.chi2[0];
-                kept = 1;
-            }
-        } else {
-            for (int rr = 0; rr < P.nhyp; ++rr) {
-                float bs = L.score[0];
-                int bq = q, bid = L.id[0];
-#pragma unroll
-                for (int off = G / 2; off > 0; off >>= 1) {
-                    const float os = __shfl_xor_sync(gmask, bs, off, G);
-                    const int oq = __shfl_xor_sync(gmask, bq, off, G);
-                    const int oid = __shfl_xor_sync(gmask, bid, off, G);
-                    const bool take = os < bs || (os == bs && (oq < bq || (oq == bq && oid < bid)));
-                    if (take) {
-                        bs = os;
-                        bq = oq;
-                        bid = oid;
-                    }
-                }
-                if (!(bs < INFINITY)) break;
-                const float wchi2 = __shfl_sync(gmask, L.chi2[0], bq, G);
-                const int wpos = __shfl_sync(gmask, L.pos[0], bq, G);
-                if (q == rr) {
-                    my_parent = bq;
-                    my_id = bid;
-                    my_pos = wpos;
-                    my_score = bs;
-                    my_chi2 = wchi2;
-                }
-                if (q == bq) L.pop();
-                kept = rr + 1;
-            }
-        }
-        if (kept == 0) {
-            // no extension for any hypothesis: the track ends with the best
-            // hypothesis as it was after the previous layer
-            const bool any_live = G == 1 ? live : (__any_sync(gmask, live) != 0);
-            if (q == 0) {
-                TrackState b;
-                load_state(sm, stride, b);
-                write_result(o, n, i, b, chisum, ntrk, nmiss, any_live ? TRD_ST_STOPPED : TRD_ST_PROP_FAIL, ids);
-            }
-            return;
-        }
-        // adopt the parent's transported state
-        if (G > 1) {
-            const int src = my_parent;
-            s.x.hi = gshfl<G>(gmask, s.x.hi, src);
-            s.x.lo = gshfl<G>(gmask, s.x.lo, src);
-            s.y.hi = gshfl<G>(gmask, s.y.hi, src);
-            s.y.lo = gshfl<G>(gmask, s.y.lo, src);
-            s.z = gshfl<G>(gmask, s.z, src);
-            s.f = gshfl<G>(gmask, s.f, src);
-            s.t = gshfl<G>(gmask, s.t, src);
-            s.k = gshfl<G>(gmask, s.k, src);
-#pragma unroll
-            for (int k = 0; k < 15; ++k) s.c[k] = gshfl<G>(gmask, s.c[k], src);
-            s.sector = gshfl<G>(gmask, s.sector, src);
-            chisum = gshfl<G>(gmask, chisum, src);
-            ntrk = gshfl<G>(gmask, ntrk, src);
-            nmiss = gshfl<G>(gmask, nmiss, src);
-#pragma unroll
-            for (int k = 0; k < kLayers; ++k) ids[k] = gshfl<G>(gmask, ids[k], src);
-        }
-        alive = q < kept;
-        if (alive) {
-            score = my_score;
-            int idl = -1;
-            if (my_id != kMissing) {
-                const float4 a = __ldg(&ix.rec0[my_pos]);
-                const float4 v = __ldg(&ix.rec1[my_pos]);
-                float vyy = v.x;
-                if (P.resmode) {
-                    const float r = sqrtf((1.0f - s.f) * (1.0f + s.f));
-                    const float uu = s.f / r - lorentz_tan(P.bz);
-                    vyy = kSigY0 * kSigY0 + kSigY1 * kSigY1 * uu * uu;
-                }
-                kalman_update(s, layer_tilt_tan(l), a.x, a.y, vyy, v.y, v.z);
-                idl = my_id;
-                ntrk += 1;
-                chisum += my_chi2;
-            } else {
-                nmiss += 1;
-            }
-#pragma unroll
-            for (int k = 0; k < kLayers; ++k) ids[k] = k == l ? idl : ids[k];
-        }
-    }
-    if (q == 0) write_result(o, n, i, s, chisum, ntrk, nmiss, TRD_ST_OK, ids);
+    for (int k = 0; k < kLayers; ++k) L.ids[k] = -1;
+    return true;
 }
 
+// One layer of seed i for the group.  Returns true when the seed is finished
+// (result written).
 template <int G, int NH>
-__global__ void __launch_bounds__(128) k_follow(SeedsView sv, IndexView ix, Params P, ResultsView o)
+__device__ __forceinline__ bool layer_step(int i, int l, int q, unsigned gmask, const IndexView &ix, const Params &P,
+                                           const ResultsView &o, int n, float *sm, int stride, float vyy_max,
+                                           float vzz_max, Lane &H)
+{
+    TrackState &s = H.s;
+    if (q == 0) save_state(sm, stride, s);
+    int chamber = -1;
+    const bool live = H.alive && to_layer(s, l, P, chamber);
+    ExtList<NH> L;
+    L.clear();
+    if (live && chamber >= 0) scan_candidates<NH>(s, l, chamber, H.score, P, ix, vyy_max, vzz_max, L);
+    if (live && H.nmiss < P.maxmiss) L.insert(H.score + P.pmiss, kMissing, -1, 0.0f);
+
+    // merge the lanes' lists: the k-th best extension goes to lane k
+    int my_parent = q, my_id = kMissing, my_pos = -1;
+    float my_score = INFINITY, my_chi2 = 0.0f;
+    int kept = 0;
+    if (G == 1) {
+        if (L.score[0] < INFINITY) {
+            my_score = L.score[0];
+            my_id = L.id[0];
+            my_pos = L.pos[0];
+            my_chi2 = L.chi2[0];
+            kept = 1;
+        }
+    } else {
+        for (int rr = 0; rr < P.nhyp; ++rr) {
+            float bs = L.score[0];
+            int bq = q, bid = L.id[0];
+#pragma unroll
+            for (int off = G / 2; off > 0; off >>= 1) {
+                const float os = __shfl_xor_sync(gmask, bs, off, G);
+                const int oq = __shfl_xor_sync(gmask, bq, off, G);
+                const int oid = __shfl_xor_sync(gmask, bid, off, G);
+                const bool take = os < bs || (os == bs && (oq < bq || (oq == bq && oid < bid)));
+                if (take) {
+                    bs = os;
+                    bq = oq;
+                    bid = oid;
+                }
+            }
+            if (!(bs < INFINITY)) break;
+            const float wchi2 = __shfl_sync(gmask, L.chi2[0], bq, G);
+            const int wpos = __shfl_sync(gmask, L.pos[0], bq, G);
+            if (q == rr) {
+                my_parent = bq;
+                my_id = bid;
+                my_pos = wpos;
+                my_score = bs;
+                my_chi2 = wchi2;
+            }
+            if (q == bq) L.pop();
+            kept = rr + 1;
+        }
+    }
+    if (kept == 0) {
+        // no extension for any hypothesis: the seed ends with the best
+        // hypothesis as it was after the previous layer
+        const bool any_live = G == 1 ? live : (__any_sync(gmask, live) != 0);
+        if (q == 0) {
+            TrackState b;
+            load_state(sm, stride, b);
+            write_result(o, n, i, b, H.chisum, H.ntrk, H.nmiss, any_live ? TRD_ST_STOPPED : TRD_ST_PROP_FAIL, H.ids);
+        }
+        return true;
+    }
+    if (G > 1) {  // adopt the parent's transported state
+        const int src = my_parent;
+        s.x.hi = gshfl<G>(gmask, s.x.hi, src);
+        s.x.lo = gshfl<G>(gmask, s.x.lo, src);
+        s.y.hi = gshfl<G>(gmask, s.y.hi, src);
+        s.y.lo = gshfl<G>(gmask, s.y.lo, src);
+        s.z = gshfl<G>(gmask, s.z, src);
+        s.f = gshfl<G>(gmask, s.f, src);
+        s.t = gshfl<G>(gmask, s.t, src);
+        s.k = gshfl<G>(gmask, s.k, src);
+#pragma unroll
+        for (int k = 0; k < 15; ++k) s.c[k] = gshfl<G>(gmask, s.c[k], src);
+        s.sector = gshfl<G>(gmask, s.sector, src);
+        H.chisum = gshfl<G>(gmask, H.chisum, src);
+        H.ntrk = gshfl<G>(gmask, H.ntrk, src);
+        H.nmiss = gshfl<G>(gmask, H.nmiss, src);
+#pragma unroll
+        for (int k = 0; k < kLayers; ++k) H.ids[k] = gshfl<G>(gmask, H.ids[k], src);
+    }
+    H.alive = q < kept;
+    if (H.alive) {
+        H.score = my_score;
+        int idl = -1;
+        if (my_id != kMissing) {
+            const float4 a = __ldg(&ix.rec[2 * my_pos]);
+            const float4 v = __ldg(&ix.rec[2 * my_pos + 1]);
+            float vyy = v.x;
+            if (P.resmode) {
+                const float r = sqrtf((1.0f - s.f) * (1.0f + s.f));
+                const float uu = s.f / r - lorentz_tan(P.bz);
+                vyy = kSigY0 * kSigY0 + kSigY1 * kSigY1 * uu * uu;
+            }
+            kalman_update(s, layer_tilt_tan(l), a.x, a.y, vyy, v.y, v.z);
+            idl = my_id;
+            H.ntrk += 1;
+            H.chisum += my_chi2;
+        } else {
+            H.nmiss += 1;
+        }
+#pragma unroll
+        for (int k = 0; k < kLayers; ++k) H.ids[k] = k == l ? idl : H.ids[k];
+    }
+    if (l == kLayers - 1) {
+        if (q == 0) write_result(o, n, i, s, H.chisum, H.ntrk, H.nmiss, TRD_ST_OK, H.ids);
+        return true;
+    }
+    return false;
+}
+
+// Persistent follower: every group loops over seeds taken from the launch's
+// counter and over their layers in one flattened loop, so a lane whose seed
+// ends takes the next seed instead of idling while its warp finishes.
+template <int G, int NH, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_follow(SeedsView sv, IndexView ix, Params P, ResultsView o, int *counter)
 {
     extern __shared__ float smem[];
     const int groups = blockDim.x / G;
     const int g = threadIdx.x / G;
-    const int i = blockIdx.x * groups + g;
-    if (i >= sv.n) return;
-    follow_track<G, NH>(i, sv, ix, P, o, smem + g, groups);
+    const int q = G == 1 ? 0 : (threadIdx.x & (G - 1));
+    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
+    float *sm = smem + g;
+    const float vyy_max = __uint_as_float(__ldg(&ix.stats[0]));
+    const float vzz_max = __uint_as_float(__ldg(&ix.stats[1]));
+    Lane H;
+    int i = 0, l = 0;
+    bool have = false;
+    for (;;) {
+        if (!have) {
+            i = fetch_seed<G>(counter, gmask, q);
+            if (i >= sv.n) break;
+            have = start_seed<G>(i, q, sv, P, o, H);
+            l = 0;
+            if (!have) continue;
+        }
+        if (layer_step<G, NH>(i, l, q, gmask, ix, P, o, sv.n, sm, groups, vyy_max, vzz_max, H)) have = false;
+        ++l;
+    }
 }
 
 }  // namespace trd
@@ -708,23 +788,28 @@ namespace trd_host {
 
 using namespace trd;
 
-template <int G, int NH>
-static int launch(const SeedsView &sv, const IndexView &ix, const Params &P, const ResultsView &o,
-                  cudaStream_t s, int block)
+template <int G, int NH, int MINB>
+static int launch(const trd_ctx *ctx, const SeedsView &sv, const IndexView &ix, const Params &P,
+                  const ResultsView &o, cudaStream_t s, int block, int *counter)
 {
+    if (sv.n == 0) return TRD_OK;
     const int groups = block / G;
-    const int grid = (sv.n + groups - 1) / groups;
     const size_t smem = sizeof(float) * 24 * groups;
-    if (grid == 0) return TRD_OK;
-    k_follow<G, NH><<<grid, block, smem, s>>>(sv, ix, P, o);
+    int per_sm = 0;
+    TRD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_follow<G, NH, MINB>, block, smem));
+    per_sm = per_sm > 0 ? per_sm : 1;
+    const long long need = (static_cast<long long>(sv.n) + groups - 1) / groups;
+    const int grid = static_cast<int>(std::min<long long>(need, static_cast<long long>(ctx->sm_count) * per_sm));
+    TRD_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), s));
+    k_follow<G, NH, MINB><<<grid, block, smem, s>>>(sv, ix, P, o, counter);
     TRD_CUDA_TRY(cudaGetLastError());
     return TRD_OK;
 }
 
 int follow_launch(const trd_ctx *ctx, const trd_seeds_t *seeds, const IndexView &iv, const trd_params_t *p,
-                  trd_results_t *out, cudaStream_t s, int lanes_per_track, int block_threads)
+                  trd_results_t *out, cudaStream_t s, int lanes_per_track, int block_threads, int min_blocks,
+                  int *counter)
 {
-    (void)ctx;
     SeedsView sv{seeds->alpha, seeds->x, seeds->y, seeds->z, seeds->snp, seeds->tgl, seeds->q2pt, seeds->cov,
                  seeds->n};
     Params P{p->bz, p->n_sigma_road, p->chi2_cut, p->p_miss, p->dy_gate_sigma, p->n_hyp, p->max_missing,
@@ -735,11 +820,18 @@ int follow_launch(const trd_ctx *ctx, const trd_seeds_t *seeds, const IndexView 
     int G = lanes_per_track;
     if (G <= 0) G = p->n_hyp <= 1 ? 1 : (p->n_hyp <= 2 ? 2 : (p->n_hyp <= 4 ? 4 : 8));
     if (G < p->n_hyp) return TRD_EINVAL;
-    switch (G) {
-    case 1: return p->n_hyp == 1 ? launch<1, 1>(sv, iv, P, o, s, block) : TRD_EINVAL;
-    case 2: return launch<2, 2>(sv, iv, P, o, s, block);
-    case 4: return launch<4, 4>(sv, iv, P, o, s, block);
-    case 8: return launch<8, 8>(sv, iv, P, o, s, block);
+    const int mb = min_blocks > 0 ? min_blocks : 4;
+    switch (G * 16 + mb) {
+    case 1 * 16 + 4: return p->n_hyp == 1 ? launch<1, 1, 4>(ctx, sv, iv, P, o, s, block, counter) : TRD_EINVAL;
+    case 1 * 16 + 5: return p->n_hyp == 1 ? launch<1, 1, 5>(ctx, sv, iv, P, o, s, block, counter) : TRD_EINVAL;
+    case 1 * 16 + 6: return p->n_hyp == 1 ? launch<1, 1, 6>(ctx, sv, iv, P, o, s, block, counter) : TRD_EINVAL;
+    case 1 * 16 + 8: return p->n_hyp == 1 ? launch<1, 1, 8>(ctx, sv, iv, P, o, s, block, counter) : TRD_EINVAL;
+    case 2 * 16 + 3: return launch<2, 2, 3>(ctx, sv, iv, P, o, s, block, counter);
+    case 2 * 16 + 4: return launch<2, 2, 4>(ctx, sv, iv, P, o, s, block, counter);
+    case 4 * 16 + 3: return launch<4, 4, 3>(ctx, sv, iv, P, o, s, block, counter);
+    case 4 * 16 + 4: return launch<4, 4, 4>(ctx, sv, iv, P, o, s, block, counter);
+    case 8 * 16 + 3: return launch<8, 8, 3>(ctx, sv, iv, P, o, s, block, counter);
+    case 8 * 16 + 4: return launch<8, 8, 4>(ctx, sv, iv, P, o, s, block, counter);
     default: return TRD_EINVAL;
     }
 }

@@ -1,14 +1,14 @@
 // index.cu -- the tracklet index (Sec. 3: "all tracklets inside a search road
 // based on the covariance matrices of the tracks are considered").
 //
-// Tracklets are bucketed by (chamber, pad row, y bin) with a counting sort:
+// Tracklets are bucketed by (chamber, y bin, pad row) with a counting sort:
 //   1. count: bucket of each tracklet; atomicAdd on the bucket's counter
 //      returns the tracklet's rank inside its bucket (no second atomic pass);
 //      block-reduced maxima of vyy and vzz bound the road width.
 //   2. exclusive scan of the bucket counters (reduce / scan partials / apply).
-//   3. scatter: record at offsets[bucket] + rank, as two float4 rows.
-// Buckets of one (chamber, pad row) are adjacent in y, so the follower reads
-// one contiguous range per pad row.  Order inside a bucket is not defined;
+//   3. scatter: a 32-byte record at offsets[bucket] + rank.
+// The pad rows of one (chamber, y bin) are adjacent, so the follower reads
+// one contiguous range per y bin.  Order inside a bucket is not defined;
 // the follower's selection does not depend on it (ties break on tracklet id).
 #include <cuda_runtime.h>
 #include <math.h>
@@ -46,7 +46,7 @@ k_index_count(const int32_t *__restrict__ ch, const float *__restrict__ y, const
         }
         const int row = trd::row_of_z(zz, trd::stack_z_lo(trd::stack_of_chamber(c)));
         const int yb = trd::ybin_of(yy, inv_w, nb);
-        const int bk = (c * trd::kRowsPerStack + row) * nb + yb;
+        const int bk = trd::bucket_of(c, yb, row, nb);
         bucket[i] = bk;
         rank[i] = atomicAdd(&counts[bk], 1);
         myy = fmaxf(myy, a);
@@ -171,14 +171,14 @@ __global__ void __launch_bounds__(kCountThreads)
 k_index_scatter(const float *__restrict__ y, const float *__restrict__ z, const float *__restrict__ dy,
                 const float *__restrict__ vyy, const float *__restrict__ vzz, const float *__restrict__ vyz,
                 int n, const int32_t *__restrict__ bucket, const int32_t *__restrict__ rank,
-                const int32_t *__restrict__ offsets, float4 *__restrict__ rec0, float4 *__restrict__ rec1)
+                const int32_t *__restrict__ offsets, float4 *__restrict__ rec)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int b = bucket[i];
         if (b < 0) continue;
         const int pos = offsets[b] + rank[i];
-        rec0[pos] = make_float4(y[i], z[i], dy[i], __int_as_float(i));
-        rec1[pos] = make_float4(vyy[i], vzz[i], vyz[i], 0.0f);
+        rec[2 * pos] = make_float4(y[i], z[i], dy[i], __int_as_float(i));
+        rec[2 * pos + 1] = make_float4(vyy[i], vzz[i], vyz[i], 0.0f);
     }
 }
 
@@ -209,7 +209,7 @@ int index_rebuild_launch(trd_index *idx, const trd_tracklets_t *t, cudaStream_t 
     TRD_CUDA_TRY(cudaGetLastError());
     if (n > 0) {
         k_index_scatter<<<grid_n, kCountThreads, 0, s>>>(t->y, t->z, t->dy, t->vyy, t->vzz, t->vyz, n, idx->bucket,
-                                                         idx->rank, idx->offsets, idx->rec0, idx->rec1);
+                                                         idx->rank, idx->offsets, idx->rec);
         TRD_CUDA_TRY(cudaGetLastError());
     }
     return TRD_OK;

@@ -182,6 +182,13 @@ __device__ __forceinline__ int row_of_z(float z, float z_lo)
     return static_cast<int>(u);
 }
 
+// Bucket order: chamber, then y bin, then pad row, so that the pad rows of one
+// y bin are adjacent and a road query reads one contiguous range per y bin.
+__device__ __forceinline__ int bucket_of(int chamber, int ybin, int row, int nb)
+{
+    return (chamber * nb + ybin) * kRowsPerStack + row;
+}
+
 __device__ __forceinline__ int ybin_of(float y, float inv_w, int nb)
 {
     float u = floorf((y + kYHalf) * inv_w);

@@ -6,11 +6,15 @@
 
 #include "../../include/trd_abi.h"
 
+constexpr int kCounterSlots = 1024;
+
 struct trd_ctx {
     int device;
     int sm_count;
     int max_threads_per_sm;
     size_t l2_bytes;
+    int32_t *counters;   // [kCounterSlots] device work counters, one per launch in flight
+    unsigned launch_seq; // next slot (atomic)
 };
 
 // Device-resident tracklet index (built by trd_index_build / rebuild).
@@ -25,8 +29,8 @@ struct trd_index {
     int32_t n_buckets;  // 540 * 18 * nb
     // index proper
     int32_t *offsets;   // [n_buckets + 1] exclusive prefix of bucket sizes
-    float4 *rec0;       // [capacity] {y, z, dy, id (bits)} in bucket order
-    float4 *rec1;       // [capacity] {vyy, vzz, vyz, 0}
+    float4 *rec;        // [2 * capacity]: per tracklet, in bucket order, a 32-byte
+                        // record {y, z, dy, id (bits)}, {vyy, vzz, vyz, 0}
     uint32_t *stats;    // [4]: max vyy bits, max vzz bits, rejected count, spare
     // build scratch
     int32_t *bucket;    // [capacity] bucket of each input tracklet (-1: rejected)
@@ -41,7 +45,7 @@ struct trd_index {
 // Plain-pointer views passed to kernels.
 struct IndexView {
     const int32_t *offsets;
-    const float4 *rec0, *rec1;
+    const float4 *rec;  // 2 float4 per tracklet
     const uint32_t *stats;
     int32_t nb;
     float inv_w;
@@ -51,7 +55,8 @@ namespace trd_host {
 int index_rebuild_launch(trd_index *idx, const trd_tracklets_t *t, cudaStream_t s);
 int follow_launch(const trd_ctx *ctx, const trd_seeds_t *seeds, const IndexView &iv,
                   const trd_params_t *p, trd_results_t *out, cudaStream_t s, int lanes_per_track,
-                  int block_threads);
+                  int block_threads, int min_blocks, int *counter);
+int *next_counter(trd_ctx *ctx);
 int scan_blocks_for(int n);
 }  // namespace trd_host
 

@@ -47,6 +47,11 @@ class Params(C.Structure):
                 ("max_missing", C.c_int32), ("res_mode", C.c_int32), ("material_on", C.c_int32)]
 
 
+class Launch(C.Structure):
+    _fields_ = [("lanes_per_track", C.c_int32), ("block_threads", C.c_int32),
+                ("min_blocks_per_sm", C.c_int32)]
+
+
 class Results(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in ("alpha", "x", "par", "cov", "chi2", "n_trk", "n_miss",
                                           "status", "tracklet_id")]
@@ -74,7 +79,7 @@ def lib():
         L.trd_index_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
         L.trd_follow.argtypes = [vp, C.POINTER(Seeds), vp, C.POINTER(Params), C.POINTER(Results), vp]
         L.trd_follow_tuned.argtypes = [vp, C.POINTER(Seeds), vp, C.POINTER(Params),
-                                       C.POINTER(Results), vp, C.c_int, C.c_int]
+                                       C.POINTER(Results), vp, C.POINTER(Launch)]
         L.trd_geometry.argtypes = [C.POINTER(C.c_double), C.c_int]
         L.trd_index_copy_out.argtypes = [vp, vp, vp]
         L.trd_version.restype = C.c_char_p
@@ -223,15 +228,16 @@ class Context:
         return Index(self, h)
 
     def follow(self, seeds: dict, index: Index, params: dict, results: dict | None = None,
-               stream=None, lanes_per_track: int = 0, block_threads: int = 0) -> dict:
+               stream=None, lanes_per_track: int = 0, block_threads: int = 0,
+               min_blocks_per_sm: int = 0) -> dict:
         n = int(seeds["alpha"].shape[0])
         if results is None:
             results = alloc_results(n, device=seeds["alpha"].device)
         ss, ps, rs = seeds_struct(seeds), params_struct(params), results_struct(results)
-        if lanes_per_track or block_threads:
+        if lanes_per_track or block_threads or min_blocks_per_sm:
+            ln = Launch(int(lanes_per_track), int(block_threads), int(min_blocks_per_sm))
             rc = lib().trd_follow_tuned(self.handle, C.byref(ss), index.handle, C.byref(ps),
-                                        C.byref(rs), _stream_handle(stream), int(lanes_per_track),
-                                        int(block_threads))
+                                        C.byref(rs), _stream_handle(stream), C.byref(ln))
             _check("trd_follow_tuned", rc)
         else:
             rc = lib().trd_follow(self.handle, C.byref(ss), index.handle, C.byref(ps),

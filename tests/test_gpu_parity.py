@@ -117,7 +117,7 @@ def _bucket_reference(trk, w):
     inv_w = f32(1.0) / f32(w)
     nb = int(math.ceil(np.float32(132.0) / np.float32(w)))
     yb = np.clip(np.floor((trk["y"] + f32(66.0)).astype(f32) * inv_w), 0, nb - 1).astype(np.int64)
-    return (ch * 18 + row) * nb + yb, nb
+    return (ch * nb + yb) * 18 + row, nb
 
 
 @pytest.mark.parametrize("w", [2.0, 0.7])
