@@ -153,6 +153,32 @@ TRD_API int trd_index_info(const trd_index_t *index, int32_t *n_indexed, int32_t
  * Either pointer may be NULL.  Host pointers, caller-owned.                 */
 TRD_API int trd_index_copy_out(const trd_index_t *index, int32_t *offsets, int32_t *ids);
 
+/* Index build that allocates nothing (the paper has no counterpart: this is
+ * for callers that cannot allocate device memory where they build an index,
+ * such as code inside a framework whose pool owns every device allocation, or
+ * a real-time loop that must not call cudaMalloc because it can synchronise
+ * the device).  It runs the same kernels as trd_index_build on the current
+ * device and writes the index into the caller's device buffers:
+ *   offsets  n_buckets + 1 int32, n_buckets = 540 * 18 * ceil(132 / w)
+ *            (bucket = (chamber * n_ybins + y bin) * 18 + pad row)
+ *   records  8 floats per tracklet (16-byte aligned): {y, z, dy, input index
+ *            as int32 bits}, {vyy, vzz, vyz, 0}, in bucket order; the first
+ *            offsets[n_buckets] records are written
+ *   stats    4 uint32: largest vyy and vzz (float bits), rejected count, 0
+ * Its scratch is a fixed device array inside the library (about 13.5 MB on
+ * every GPU that loads it, kept until exit), so it accepts at most 1,048,576
+ * tracklets and y bins of at least 1 cm (w = 0 selects 2 cm); anything larger
+ * returns TRD_EINVAL.  All calls on a device share that scratch: calls that
+ * overlap on the GPU (other streams, other threads) race and must be ordered
+ * by the caller.  The first call on each device looks up the array's device
+ * address (no allocation); make that first call before any stream capture.
+ * Asynchronous on `stream`; the inputs must stay valid until it completes.
+ * Errors: TRD_EINVAL (NULL pointer, size or bin width beyond the limits,
+ * misaligned records), TRD_ECUDA.                                           */
+TRD_API int trd_index_build_noalloc(const trd_tracklets_t *tracklets, float y_bin_width,
+                                    int32_t *offsets, float *records, uint32_t *stats,
+                                    void *stream);
+
 /* ---- the follower (Sec. 3) -------------------------------------------------
  * trd_follow: for every seed, rotate it into the sector of its position,
  * then for layers 0..5: transport the helix and covariance to the layer plane

@@ -216,3 +216,112 @@ int index_rebuild_launch(trd_index *idx, const trd_tracklets_t *t, cudaStream_t 
 }
 
 }  // namespace trd_host
+
+// ---- index build into caller buffers, with no allocation --------------------
+// Some callers cannot allocate device memory at the point where they build an
+// index: code running inside a framework that owns every device allocation
+// through its own pool, or a real-time loop that must not call cudaMalloc
+// because it may synchronise the device.  For them the build's scratch (bucket
+// and rank of every tracklet, one counter per bucket, scan partials) lives in
+// the file-scope array below, sized for kNoAllocMaxTracklets tracklets and
+// y bins of at least kNoAllocMinBinWidth cm.  Every GPU that loads the library
+// holds it (about 13.5 MB) until the process exits, and all calls on a device
+// share it.
+namespace {
+
+constexpr int kNoAllocMaxTracklets = 1 << 20;
+constexpr float kNoAllocMinBinWidth = 1.0f;
+constexpr int kNoAllocMaxBins = 132;  // ceil(2 * 66 cm / 1 cm)
+constexpr int kNoAllocMaxBuckets = trd::kChambers * trd::kRowsPerStack * kNoAllocMaxBins;
+constexpr int kNoAllocMaxPartials = (kNoAllocMaxBuckets + kScanTile - 1) / kScanTile + 1;
+constexpr size_t kNoAllocWords =
+    2 * static_cast<size_t>(kNoAllocMaxTracklets) + kNoAllocMaxBuckets + kNoAllocMaxPartials;
+
+static __device__ __align__(256) int32_t g_noalloc_scratch[kNoAllocWords];
+
+constexpr int kNoAllocMaxDevices = 64;
+struct NoAllocDevice {
+    int32_t *scratch;  // device address of g_noalloc_scratch on this device
+    int sm_count;
+};
+NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
+int g_noalloc_ready[kNoAllocMaxDevices];  // guarded by __atomic builtins
+
+// Once per device, with that device current: the host-side name of the array
+// is not a device address, so fetch the address the kernels must be given.
+int noalloc_setup(int dev, NoAllocDevice *out)
+{
+    if (__atomic_load_n(&g_noalloc_ready[dev], __ATOMIC_ACQUIRE)) {
+        *out = g_noalloc_dev[dev];
+        return TRD_OK;
+    }
+    NoAllocDevice d{};
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+        (void)cudaGetLastError();
+        return TRD_ECUDA;
+    }
+    d.scratch = static_cast<int32_t *>(p);
+    if (cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return TRD_ECUDA;
+    }
+    g_noalloc_dev[dev] = d;  // the same values whichever thread writes first
+    __atomic_store_n(&g_noalloc_ready[dev], 1, __ATOMIC_RELEASE);
+    *out = d;
+    return TRD_OK;
+}
+
+}  // namespace
+
+extern "C" int trd_index_build_noalloc(const trd_tracklets_t *t, float y_bin_width, int32_t *offsets,
+                                       float *records, uint32_t *stats, void *stream)
+{
+    if (!t || !offsets || !records || !stats || t->n < 0) return TRD_EINVAL;
+    if (t->n > kNoAllocMaxTracklets) return TRD_EINVAL;  // larger than the static scratch
+    if (y_bin_width == 0.0f) y_bin_width = 2.0f;
+    if (!(y_bin_width >= kNoAllocMinBinWidth) || !isfinite(y_bin_width)) return TRD_EINVAL;
+    if (reinterpret_cast<uintptr_t>(records) % 16 != 0) return TRD_EINVAL;
+    if (t->n > 0 && (!t->chamber || !t->y || !t->z || !t->dy || !t->vyy || !t->vzz || !t->vyz)) return TRD_EINVAL;
+    int dev = 0;
+    TRD_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return TRD_ECUDA;
+    NoAllocDevice d;
+    const int rc = noalloc_setup(dev, &d);
+    if (rc) return rc;
+
+    const int n = t->n;
+    const int nb = static_cast<int>(ceilf(2.0f * trd::kYHalf / y_bin_width));
+    const float inv_w = 1.0f / y_bin_width;
+    const int n_buckets = trd::kChambers * trd::kRowsPerStack * nb;
+    const int m = (n_buckets + kScanTile - 1) / kScanTile;
+    int32_t *bucket = d.scratch;
+    int32_t *rank = bucket + kNoAllocMaxTracklets;
+    int32_t *counts = rank + kNoAllocMaxTracklets;
+    int32_t *partials = counts + kNoAllocMaxBuckets;
+    float4 *rec = reinterpret_cast<float4 *>(records);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+    // the counters and the caller's stats must start at zero; the rest of the
+    // scratch is fully written before it is read
+    TRD_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(int32_t) * n_buckets, s));
+    TRD_CUDA_TRY(cudaMemsetAsync(stats, 0, sizeof(uint32_t) * 4, s));
+    const int grid_n = n > 0 ? std::min((n + kCountThreads - 1) / kCountThreads, d.sm_count * 8) : 0;
+    if (n > 0) {
+        k_index_count<<<grid_n, kCountThreads, 0, s>>>(t->chamber, t->y, t->z, t->dy, t->vyy, t->vzz, t->vyz, n,
+                                                       inv_w, nb, bucket, rank, counts, stats);
+        TRD_CUDA_TRY(cudaGetLastError());
+    }
+    k_scan_reduce<<<m, kScanThreads, 0, s>>>(counts, n_buckets, partials);
+    TRD_CUDA_TRY(cudaGetLastError());
+    k_scan_partials<<<1, kScanThreads, 0, s>>>(partials, m);
+    TRD_CUDA_TRY(cudaGetLastError());
+    k_scan_apply<<<m, kScanThreads, 0, s>>>(counts, n_buckets, partials, offsets);
+    TRD_CUDA_TRY(cudaGetLastError());
+    if (n > 0) {
+        k_index_scatter<<<grid_n, kCountThreads, 0, s>>>(t->y, t->z, t->dy, t->vyy, t->vzz, t->vyz, n, bucket, rank,
+                                                         offsets, rec);
+        TRD_CUDA_TRY(cudaGetLastError());
+    }
+    return TRD_OK;
+}
