@@ -44,6 +44,17 @@ RECORD_BYTES = 32
 IN_ROAD_PER_SEED = 15.75
 FOLLOW_BYTES_PER_SEED = SEED_BYTES + RESULT_BYTES + RECORD_BYTES * IN_ROAD_PER_SEED
 L2_FLUSH_BYTES = 512 << 20
+# DRAM bytes (read + write) of one k_follow launch on this workload from one
+# ncu capture (profiles/kernels_timeframe.md), valid only for the kernel source
+# it was measured on: reported as null once follow.cu or trd_device.cuh change.
+FOLLOW_TRAFFIC = {"source_sha256_16": "432ed8e557f77c76", "bytes": 67.278336e6}
+
+
+def _follow_source_hash():
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2003_03174_b300", "csrc")
+    data = b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("follow.cu", "trd_device.cuh"))
+    return hashlib.sha256(data).hexdigest()[:16]
 
 
 def _dist():
@@ -189,7 +200,7 @@ def run_ours(args):
     trk = trd.to_device(tf.tracklets, dev)
     n = tf.n_seeds
     stream = torch.cuda.Stream(device=dev)
-    shape = dict(lanes_per_track=0, block_threads=0, min_blocks_per_sm=0)
+    shape = dict(lanes_per_track=args.lanes, block_threads=args.block, min_blocks_per_sm=args.min_blocks)
     bin_width = args.bin_width
     tuned = None
     if not args.no_autotune:
@@ -279,7 +290,10 @@ def run_ours(args):
     roof = {"bound": "hbm", "kernel": "k_follow", "achieved": achieved,
             "peak": hbm if hbm else 6400.0, "unit": "GB/s",
             "peak_source": "measured" if hbm else "fallback",
-            "frac": achieved / (hbm if hbm else 6400.0), "traffic": None,
+            "frac": achieved / (hbm if hbm else 6400.0),
+            "traffic": FOLLOW_TRAFFIC["bytes"] if _follow_source_hash() == FOLLOW_TRAFFIC["source_sha256_16"]
+            and tf.n_seeds == 200_000 else None,
+            "traffic_unit": "bytes per launch (ncu dram read+write)",
             "algorithmic_bytes_per_launch": n * FOLLOW_BYTES_PER_SEED,
             "follow_ms": statistics.mean(follow_ms), "index_ms": statistics.mean(index_ms)}
     launches_per_step = 6  # count, 3 scan kernels, scatter, follow
@@ -327,6 +341,9 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=20_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--lanes", type=int, default=0, help="lanes per seed (with --no-autotune)")
+    ap.add_argument("--block", type=int, default=0, help="block threads (with --no-autotune)")
+    ap.add_argument("--min-blocks", type=int, default=0, help="register budget (with --no-autotune)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
