@@ -62,6 +62,7 @@ extern "C" {
 
 typedef struct trd_ctx trd_ctx_t;
 typedef struct trd_index trd_index_t;
+typedef struct trd_batch trd_batch_t;
 
 /* Seeds: ITS-TPC tracks extrapolated towards the TRD (Sec. 3), in any frame
  * alpha.  Device pointers, each n floats; cov is [15][n].  Read only.      */
@@ -212,6 +213,35 @@ typedef struct {
 TRD_API int trd_follow_tuned(trd_ctx_t *ctx, const trd_seeds_t *seeds, const trd_index_t *index,
                              const trd_params_t *params, trd_results_t *out, void *stream,
                              const trd_launch_t *launch);
+
+/* ---- batches of timeframes (Sec. 3.1: Run 3 processes time frames of many
+ * collisions; here many time frames at once) ----------------------------------
+ * trd_batch_create: prepare one CUDA graph that, for n_tf timeframes stored
+ * back to back, builds a single index over all their tracklets and follows
+ * all their seeds in one persistent launch that pulls seeds of every
+ * timeframe from one work queue.
+ *   seed_offsets, tracklet_offsets  host arrays of n_tf + 1 int32: timeframe t
+ *       owns seeds [seed_offsets[t], seed_offsets[t+1]) of `seeds` and
+ *       tracklets [tracklet_offsets[t], ...) of `tracklets`; offsets[0] = 0,
+ *       non-decreasing, offsets[n_tf] = n (empty timeframes are allowed).
+ *   seeds, tracklets, results: device arrays of the concatenated timeframes,
+ *       caller-owned, bound to the graph (refill them in place between runs).
+ *       Result tracklet ids are local to each seed's timeframe.
+ *   params, y_bin_width, launch: as for trd_index_build / trd_follow_tuned.
+ * The library owns the batch (index, offsets, graph); free with
+ * trd_batch_free.  Each seed's arithmetic is the same as in trd_follow on
+ * its timeframe alone, so results are identical.
+ * trd_batch_run replays the graph on `stream` (asynchronous).  A batch must
+ * not be run concurrently with itself.
+ * Errors: TRD_EINVAL (bad offsets, parameters or shape), TRD_ENOMEM,
+ * TRD_ECUDA.                                                                */
+TRD_API int trd_batch_create(trd_ctx_t *ctx, int32_t n_tf, const int32_t *seed_offsets,
+                             const int32_t *tracklet_offsets, const trd_seeds_t *seeds,
+                             const trd_tracklets_t *tracklets, const trd_params_t *params,
+                             trd_results_t *results, float y_bin_width, const trd_launch_t *launch,
+                             trd_batch_t **out);
+TRD_API int trd_batch_run(trd_batch_t *batch, void *stream);
+TRD_API int trd_batch_free(trd_batch_t *batch);
 
 /* Geometry constants the library was built with, for cross-checks:
  * out[0..12] = n_sectors, n_stacks, n_layers, n_chambers, x_layer0,

@@ -36,6 +36,7 @@ void free_index_buffers(trd_index *x)
     cudaFree(x->rank);
     cudaFree(x->counts);
     cudaFree(x->partials);
+    cudaFree(x->toff);
     if (x->built) cudaEventDestroy(x->built);
     (void)cudaGetLastError();
 }
@@ -49,6 +50,55 @@ int *next_counter(trd_ctx *ctx)
 {
     const unsigned k = __atomic_fetch_add(&ctx->launch_seq, 1u, __ATOMIC_RELAXED);
     return ctx->counters + (k % kCounterSlots);
+}
+
+// Allocate an index for up to `capacity` tracklets of `n_tf` timeframes.
+int index_alloc(trd_ctx *ctx, int32_t capacity, float y_bin_width, int32_t n_tf, trd_index **out)
+{
+    if (!ctx || !out || capacity < 0 || n_tf < 1) return TRD_EINVAL;
+    *out = nullptr;
+    if (y_bin_width == 0.0f) y_bin_width = kDefaultBinWidth;
+    if (!finite_pos(y_bin_width) || y_bin_width < 0.05f) return TRD_EINVAL;
+    const int32_t nb = static_cast<int32_t>(ceilf(2.0f * kYHalf / y_bin_width));
+    const long long n_buckets = static_cast<long long>(n_tf) * TRD_N_CHAMBERS * kRowsPerStack * nb;
+    if (n_buckets >= (1LL << 31) - 1) return TRD_EINVAL;
+    TRD_CUDA_TRY(cudaSetDevice(ctx->device));
+    trd_index *x = new (std::nothrow) trd_index;
+    if (!x) return TRD_ENOMEM;
+    memset(x, 0, sizeof *x);
+    x->ctx = ctx;
+    x->device = ctx->device;
+    x->capacity = capacity;
+    x->y_bin_width = y_bin_width;
+    x->nb = nb;
+    x->inv_w = 1.0f / y_bin_width;
+    x->n_tf = n_tf;
+    x->n_buckets = static_cast<int32_t>(n_buckets);
+    x->n_partials = scan_blocks_for(x->n_buckets);
+    const size_t cap = static_cast<size_t>(std::max(capacity, 1));
+    bool ok = cudaMalloc(&x->offsets, sizeof(int32_t) * (x->n_buckets + 1)) == cudaSuccess &&
+              cudaMalloc(&x->rec, 2 * sizeof(float4) * cap) == cudaSuccess &&
+              cudaMalloc(&x->stats, sizeof(uint32_t) * 4) == cudaSuccess &&
+              cudaMalloc(&x->bucket, sizeof(int32_t) * cap) == cudaSuccess &&
+              cudaMalloc(&x->rank, sizeof(int32_t) * cap) == cudaSuccess &&
+              cudaMalloc(&x->counts, sizeof(int32_t) * x->n_buckets) == cudaSuccess &&
+              cudaMalloc(&x->partials, sizeof(int32_t) * (x->n_partials + 1)) == cudaSuccess &&
+              (n_tf == 1 || cudaMalloc(&x->toff, sizeof(int32_t) * (n_tf + 1)) == cudaSuccess) &&
+              cudaEventCreateWithFlags(&x->built, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        free_index_buffers(x);
+        delete x;
+        return TRD_ENOMEM;
+    }
+    *out = x;
+    return TRD_OK;
+}
+
+void index_release(trd_index *x)
+{
+    cudaSetDevice(x->device);
+    free_index_buffers(x);
+    delete x;
 }
 }  // namespace trd_host
 
@@ -105,38 +155,7 @@ int trd_ctx_sm_count(const trd_ctx_t *ctx) { return ctx ? ctx->sm_count : TRD_EI
 
 int trd_index_create(trd_ctx_t *ctx, int32_t capacity, float y_bin_width, trd_index_t **out)
 {
-    if (!ctx || !out || capacity < 0) return TRD_EINVAL;
-    *out = nullptr;
-    if (y_bin_width == 0.0f) y_bin_width = kDefaultBinWidth;
-    if (!finite_pos(y_bin_width) || y_bin_width < 0.05f) return TRD_EINVAL;
-    TRD_CUDA_TRY(cudaSetDevice(ctx->device));
-    trd_index *x = new (std::nothrow) trd_index;
-    if (!x) return TRD_ENOMEM;
-    memset(x, 0, sizeof *x);
-    x->ctx = ctx;
-    x->device = ctx->device;
-    x->capacity = capacity;
-    x->y_bin_width = y_bin_width;
-    x->nb = static_cast<int32_t>(ceilf(2.0f * kYHalf / y_bin_width));
-    x->inv_w = 1.0f / y_bin_width;
-    x->n_buckets = TRD_N_CHAMBERS * kRowsPerStack * x->nb;
-    x->n_partials = trd_host::scan_blocks_for(x->n_buckets);
-    const size_t cap = static_cast<size_t>(std::max(capacity, 1));
-    bool ok = cudaMalloc(&x->offsets, sizeof(int32_t) * (x->n_buckets + 1)) == cudaSuccess &&
-              cudaMalloc(&x->rec, 2 * sizeof(float4) * cap) == cudaSuccess &&
-              cudaMalloc(&x->stats, sizeof(uint32_t) * 4) == cudaSuccess &&
-              cudaMalloc(&x->bucket, sizeof(int32_t) * cap) == cudaSuccess &&
-              cudaMalloc(&x->rank, sizeof(int32_t) * cap) == cudaSuccess &&
-              cudaMalloc(&x->counts, sizeof(int32_t) * x->n_buckets) == cudaSuccess &&
-              cudaMalloc(&x->partials, sizeof(int32_t) * (x->n_partials + 1)) == cudaSuccess &&
-              cudaEventCreateWithFlags(&x->built, cudaEventDisableTiming) == cudaSuccess;
-    if (!ok) {
-        free_index_buffers(x);
-        delete x;
-        return TRD_ENOMEM;
-    }
-    *out = x;
-    return TRD_OK;
+    return trd_host::index_alloc(ctx, capacity, y_bin_width, 1, out);
 }
 
 int trd_index_rebuild(trd_index_t *index, const trd_tracklets_t *t, void *stream)

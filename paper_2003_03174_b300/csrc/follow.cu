@@ -27,6 +27,8 @@ struct Params {
 struct SeedsView {
     const float *alpha, *x, *y, *z, *snp, *tgl, *q2pt, *cov;
     int n;
+    const int32_t *soff;  // [n_tf + 1] seed offsets of a batch of timeframes, or null
+    int n_tf;
 };
 
 struct ResultsView {
@@ -403,7 +405,7 @@ __device__ __forceinline__ void test_record(const float4 &a, int pos, const Inde
 }
 
 template <int NH>
-__device__ void scan_candidates(const TrackState &s, int l, int chamber, float score, const Params &P,
+__device__ void scan_candidates(const TrackState &s, int l, int chamber, int cbase, float score, const Params &P,
                                 const IndexView &ix, float vyy_max_in, float vzz_max, ExtList<NH> &L)
 {
     const float tt = layer_tilt_tan(l);
@@ -427,7 +429,7 @@ __device__ void scan_candidates(const TrackState &s, int l, int chamber, float s
     const float half = W + fabsf(tt) * Rz + 1e-3f + 1e-6f * fabsf(yh);
     const int b_lo = ybin_of(yh - half, ix.inv_w, ix.nb), b_hi = ybin_of(yh + half, ix.inv_w, ix.nb);
     for (int b = b_lo; b <= b_hi; b += 2) {
-        const int base = bucket_of(chamber, b, 0, ix.nb);
+        const int base = bucket_of(cbase + chamber, b, 0, ix.nb);
         const bool two = b + 1 <= b_hi;
         const int beg0 = __ldg(&ix.offsets[base + r_lo]);
         const int end0 = __ldg(&ix.offsets[base + r_hi + 1]);
@@ -586,6 +588,7 @@ struct Lane {
     TrackState s;
     float score, chisum;
     int ntrk, nmiss;
+    int cbase;  // first chamber of the seed's timeframe in the index (timeframe * 540)
     int ids[kLayers];
     bool alive;
 };
@@ -624,6 +627,7 @@ __device__ __forceinline__ bool start_seed(int i, int q, const SeedsView &sv, co
         if (q == 0) write_seed_result(o, sv, n, i, TRD_ST_PROP_FAIL);
         return false;
     }
+    L.cbase = tf_of(i, sv.soff, sv.n_tf) * kChambers;
     L.alive = q == 0;
     L.score = 0.0f;
     L.chisum = 0.0f;
@@ -647,7 +651,7 @@ __device__ __forceinline__ bool layer_step(int i, int l, int q, unsigned gmask, 
     const bool live = H.alive && to_layer(s, l, P, chamber);
     ExtList<NH> L;
     L.clear();
-    if (live && chamber >= 0) scan_candidates<NH>(s, l, chamber, H.score, P, ix, vyy_max, vzz_max, L);
+    if (live && chamber >= 0) scan_candidates<NH>(s, l, chamber, H.cbase, H.score, P, ix, vyy_max, vzz_max, L);
     if (live && H.nmiss < P.maxmiss) L.insert(H.score + P.pmiss, kMissing, -1, 0.0f);
 
     // merge the lanes' lists: the k-th best extension goes to lane k
@@ -808,10 +812,10 @@ static int launch(const trd_ctx *ctx, const SeedsView &sv, const IndexView &ix, 
 
 int follow_launch(const trd_ctx *ctx, const trd_seeds_t *seeds, const IndexView &iv, const trd_params_t *p,
                   trd_results_t *out, cudaStream_t s, int lanes_per_track, int block_threads, int min_blocks,
-                  int *counter)
+                  int *counter, const int32_t *seed_offsets, int n_tf)
 {
     SeedsView sv{seeds->alpha, seeds->x, seeds->y, seeds->z, seeds->snp, seeds->tgl, seeds->q2pt, seeds->cov,
-                 seeds->n};
+                 seeds->n, seed_offsets, n_tf};
     Params P{p->bz, p->n_sigma_road, p->chi2_cut, p->p_miss, p->dy_gate_sigma, p->n_hyp, p->max_missing,
              p->res_mode, p->material_on};
     ResultsView o{out->alpha, out->x, out->par, out->cov, out->chi2, out->n_trk, out->n_miss, out->status,

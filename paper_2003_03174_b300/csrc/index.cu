@@ -29,7 +29,8 @@ __global__ void __launch_bounds__(kCountThreads)
 k_index_count(const int32_t *__restrict__ ch, const float *__restrict__ y, const float *__restrict__ z,
               const float *__restrict__ dy, const float *__restrict__ vyy, const float *__restrict__ vzz,
               const float *__restrict__ vyz, int n, float inv_w, int nb, int32_t *__restrict__ bucket,
-              int32_t *__restrict__ rank, int32_t *__restrict__ counts, uint32_t *__restrict__ stats)
+              int32_t *__restrict__ rank, int32_t *__restrict__ counts, uint32_t *__restrict__ stats,
+              const int32_t *__restrict__ toff, int n_tf)
 {
     float myy = 0.0f, mzz = 0.0f;
     int rejected = 0;
@@ -46,7 +47,7 @@ k_index_count(const int32_t *__restrict__ ch, const float *__restrict__ y, const
         }
         const int row = trd::row_of_z(zz, trd::stack_z_lo(trd::stack_of_chamber(c)));
         const int yb = trd::ybin_of(yy, inv_w, nb);
-        const int bk = trd::bucket_of(c, yb, row, nb);
+        const int bk = trd::bucket_of(trd::tf_of(i, toff, n_tf) * trd::kChambers + c, yb, row, nb);
         bucket[i] = bk;
         rank[i] = atomicAdd(&counts[bk], 1);
         myy = fmaxf(myy, a);
@@ -171,13 +172,16 @@ __global__ void __launch_bounds__(kCountThreads)
 k_index_scatter(const float *__restrict__ y, const float *__restrict__ z, const float *__restrict__ dy,
                 const float *__restrict__ vyy, const float *__restrict__ vzz, const float *__restrict__ vyz,
                 int n, const int32_t *__restrict__ bucket, const int32_t *__restrict__ rank,
-                const int32_t *__restrict__ offsets, float4 *__restrict__ rec)
+                const int32_t *__restrict__ offsets, float4 *__restrict__ rec, const int32_t *__restrict__ toff,
+                int n_tf)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int b = bucket[i];
         if (b < 0) continue;
         const int pos = offsets[b] + rank[i];
-        rec[2 * pos] = make_float4(y[i], z[i], dy[i], __int_as_float(i));
+        // ids are local to the tracklet's timeframe
+        const int local = toff ? i - __ldg(&toff[trd::tf_of(i, toff, n_tf)]) : i;
+        rec[2 * pos] = make_float4(y[i], z[i], dy[i], __int_as_float(local));
         rec[2 * pos + 1] = make_float4(vyy[i], vzz[i], vyz[i], 0.0f);
     }
 }
@@ -197,7 +201,7 @@ int index_rebuild_launch(trd_index *idx, const trd_tracklets_t *t, cudaStream_t 
     if (n > 0) {
         k_index_count<<<grid_n, kCountThreads, 0, s>>>(t->chamber, t->y, t->z, t->dy, t->vyy, t->vzz, t->vyz, n,
                                                        idx->inv_w, idx->nb, idx->bucket, idx->rank, idx->counts,
-                                                       idx->stats);
+                                                       idx->stats, idx->toff, idx->n_tf);
         TRD_CUDA_TRY(cudaGetLastError());
     }
     const int m = scan_blocks_for(idx->n_buckets);
@@ -209,7 +213,7 @@ int index_rebuild_launch(trd_index *idx, const trd_tracklets_t *t, cudaStream_t 
     TRD_CUDA_TRY(cudaGetLastError());
     if (n > 0) {
         k_index_scatter<<<grid_n, kCountThreads, 0, s>>>(t->y, t->z, t->dy, t->vyy, t->vzz, t->vyz, n, idx->bucket,
-                                                         idx->rank, idx->offsets, idx->rec);
+                                                         idx->rank, idx->offsets, idx->rec, idx->toff, idx->n_tf);
         TRD_CUDA_TRY(cudaGetLastError());
     }
     return TRD_OK;
@@ -309,7 +313,7 @@ extern "C" int trd_index_build_noalloc(const trd_tracklets_t *t, float y_bin_wid
     const int grid_n = n > 0 ? std::min((n + kCountThreads - 1) / kCountThreads, d.sm_count * 8) : 0;
     if (n > 0) {
         k_index_count<<<grid_n, kCountThreads, 0, s>>>(t->chamber, t->y, t->z, t->dy, t->vyy, t->vzz, t->vyz, n,
-                                                       inv_w, nb, bucket, rank, counts, stats);
+                                                       inv_w, nb, bucket, rank, counts, stats, nullptr, 1);
         TRD_CUDA_TRY(cudaGetLastError());
     }
     k_scan_reduce<<<m, kScanThreads, 0, s>>>(counts, n_buckets, partials);
@@ -320,7 +324,7 @@ extern "C" int trd_index_build_noalloc(const trd_tracklets_t *t, float y_bin_wid
     TRD_CUDA_TRY(cudaGetLastError());
     if (n > 0) {
         k_index_scatter<<<grid_n, kCountThreads, 0, s>>>(t->y, t->z, t->dy, t->vyy, t->vzz, t->vyz, n, bucket, rank,
-                                                         offsets, rec);
+                                                         offsets, rec, nullptr, 1);
         TRD_CUDA_TRY(cudaGetLastError());
     }
     return TRD_OK;

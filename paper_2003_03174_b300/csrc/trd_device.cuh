@@ -189,6 +189,23 @@ __device__ __forceinline__ int bucket_of(int chamber, int ybin, int row, int nb)
     return (chamber * nb + ybin) * kRowsPerStack + row;
 }
 
+// Timeframe of element i in a batch laid out by offsets off[0..n_tf]
+// (off[0] = 0, non-decreasing): the last t with off[t] <= i.  A single
+// timeframe passes off = nullptr.
+__device__ __forceinline__ int tf_of(int i, const int32_t *__restrict__ off, int n_tf)
+{
+    if (!off) return 0;
+    int lo = 0, hi = n_tf - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&off[mid]) <= i)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
 __device__ __forceinline__ int ybin_of(float y, float inv_w, int nb)
 {
     float u = floorf((y + kYHalf) * inv_w);

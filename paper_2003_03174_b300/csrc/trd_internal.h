@@ -26,7 +26,9 @@ struct trd_index {
     float y_bin_width;  // cm
     float inv_w;
     int32_t nb;         // y bins per (chamber, pad row)
-    int32_t n_buckets;  // 540 * 18 * nb
+    int32_t n_tf;       // timeframes indexed together (1 for a plain index)
+    int32_t *toff;      // [n_tf + 1] tracklet offsets per timeframe (device), null when n_tf = 1
+    int32_t n_buckets;  // n_tf * 540 * 18 * nb
     // index proper
     int32_t *offsets;   // [n_buckets + 1] exclusive prefix of bucket sizes
     float4 *rec;        // [2 * capacity]: per tracklet, in bucket order, a 32-byte
@@ -55,8 +57,11 @@ namespace trd_host {
 int index_rebuild_launch(trd_index *idx, const trd_tracklets_t *t, cudaStream_t s);
 int follow_launch(const trd_ctx *ctx, const trd_seeds_t *seeds, const IndexView &iv,
                   const trd_params_t *p, trd_results_t *out, cudaStream_t s, int lanes_per_track,
-                  int block_threads, int min_blocks, int *counter);
+                  int block_threads, int min_blocks, int *counter, const int32_t *seed_offsets = nullptr,
+                  int n_tf = 1);
 int *next_counter(trd_ctx *ctx);
+int index_alloc(trd_ctx *ctx, int32_t capacity, float y_bin_width, int32_t n_tf, trd_index **out);
+void index_release(trd_index *x);
 int scan_blocks_for(int n);
 }  // namespace trd_host
 

@@ -21,7 +21,8 @@ _ERRNAMES = {-1: "TRD_EINVAL", -2: "TRD_ENOMEM", -3: "TRD_EAGAIN", -4: "TRD_ETIM
 EXPORTED = [
     "trd_ctx_create", "trd_ctx_destroy", "trd_ctx_sm_count", "trd_index_build", "trd_index_free",
     "trd_index_create", "trd_index_rebuild", "trd_index_info", "trd_follow", "trd_follow_tuned",
-    "trd_geometry", "trd_version", "trd_index_copy_out",
+    "trd_geometry", "trd_version", "trd_index_copy_out", "trd_batch_create", "trd_batch_run",
+    "trd_batch_free",
 ]
 
 
@@ -82,6 +83,11 @@ def lib():
                                        C.POINTER(Results), vp, C.POINTER(Launch)]
         L.trd_geometry.argtypes = [C.POINTER(C.c_double), C.c_int]
         L.trd_index_copy_out.argtypes = [vp, vp, vp]
+        L.trd_batch_create.argtypes = [vp, i32, vp, vp, C.POINTER(Seeds), C.POINTER(Tracklets),
+                                       C.POINTER(Params), C.POINTER(Results), f32, C.POINTER(Launch),
+                                       C.POINTER(vp)]
+        L.trd_batch_run.argtypes = [vp, vp]
+        L.trd_batch_free.argtypes = [vp]
         L.trd_version.restype = C.c_char_p
         for fn in EXPORTED:
             if fn != "trd_version":
@@ -198,6 +204,28 @@ class Index:
             pass
 
 
+class Batch:
+    """Many timeframes followed by one CUDA-graph replay (trd_batch_t)."""
+
+    def __init__(self, handle, keep):
+        self.handle = handle
+        self._keep = keep  # bound device buffers must outlive the graph
+
+    def run(self, stream=None):
+        _check("trd_batch_run", lib().trd_batch_run(self.handle, _stream_handle(stream)))
+
+    def free(self):
+        if self.handle:
+            lib().trd_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
 class Context:
     """Binds one CUDA device (trd_ctx_t)."""
 
@@ -244,6 +272,24 @@ class Context:
                                   C.byref(rs), _stream_handle(stream))
             _check("trd_follow", rc)
         return results
+
+    def batch_create(self, seeds: dict, tracklets: dict, seed_offsets, tracklet_offsets,
+                     params: dict, results: dict, y_bin_width: float = 0.0,
+                     lanes_per_track: int = 0, block_threads: int = 0,
+                     min_blocks_per_sm: int = 0) -> Batch:
+        import numpy as np
+        so = np.ascontiguousarray(np.asarray(seed_offsets, dtype=np.int32))
+        to = np.ascontiguousarray(np.asarray(tracklet_offsets, dtype=np.int32))
+        n_tf = int(so.shape[0]) - 1
+        ss, ts = seeds_struct(seeds), tracklets_struct(tracklets)
+        ps, rs = params_struct(params), results_struct(results)
+        ln = Launch(int(lanes_per_track), int(block_threads), int(min_blocks_per_sm))
+        h = C.c_void_p()
+        _check("trd_batch_create", lib().trd_batch_create(
+            self.handle, n_tf, so.ctypes.data_as(C.c_void_p), to.ctypes.data_as(C.c_void_p),
+            C.byref(ss), C.byref(ts), C.byref(ps), C.byref(rs), float(y_bin_width), C.byref(ln),
+            C.byref(h)))
+        return Batch(h, keep=(seeds, tracklets, results))
 
     def close(self):
         if self.handle:

@@ -358,3 +358,38 @@ def efficiency_purity(tracklet_id: np.ndarray, truth_ids: np.ndarray) -> dict:
     purity = float((n_cor[two] == n_att[two]).mean()) if two.any() else 0.0
     return dict(efficiency=eff_all, efficiency_reachable=eff_reach, purity=purity,
                 matched=int(two.sum()))
+
+
+BATCH_PARAMS = dict(n_hyp=3, road=3.0, chi2_cut=15.0, max_missing=2, noise=0.30)
+
+
+def _batch_member(args):
+    n, seed = args
+    p = default_params(0.5, n_sigma_road=BATCH_PARAMS["road"], chi2_cut=BATCH_PARAMS["chi2_cut"],
+                       n_hyp=BATCH_PARAMS["n_hyp"], max_missing=BATCH_PARAMS["max_missing"])
+    return make_timeframe(int(n), seed=seed, noise=BATCH_PARAMS["noise"], name=f"tf{seed}", params=p)
+
+
+def make_batch(counts, seed: int = 0, workers: int = 0):
+    """Timeframes with the given seed counts (timeframe t drawn with seed
+    1000 * seed + t), N = 3, 3-sigma road, 30 % noise.  workers > 1 draws
+    them in a process pool started with 'spawn'."""
+    jobs = [(int(n), 1000 * seed + t) for t, n in enumerate(counts)]
+    if workers and workers > 1 and len(jobs) > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(workers) as pool:
+            return pool.map(_batch_member, jobs, chunksize=1)
+    return [_batch_member(j) for j in jobs]
+
+
+def concat(tfs):
+    """Concatenate timeframes: (seeds, tracklets, seed_offsets, tracklet_offsets)."""
+    so = np.zeros(len(tfs) + 1, np.int32)
+    to = np.zeros(len(tfs) + 1, np.int32)
+    so[1:] = np.cumsum([t.n_seeds for t in tfs])
+    to[1:] = np.cumsum([t.n_tracklets for t in tfs])
+    seeds = {k: (np.concatenate([t.seeds[k] for t in tfs], axis=-1) if k == "cov" else
+                 np.concatenate([t.seeds[k] for t in tfs])) for k in tfs[0].seeds}
+    seeds["cov"] = np.ascontiguousarray(seeds["cov"])
+    trk = {k: np.concatenate([t.tracklets[k] for t in tfs]) for k in tfs[0].tracklets}
+    return seeds, trk, so, to
