@@ -330,6 +330,87 @@ def run_ours(args):
     return 0
 
 
+def run_batched(args):
+    """64 timeframes (seed counts log-uniform in 5k-400k, N = 3): one graph
+    replay of the batch against 64 plain launches (index rebuild + follow per
+    timeframe, each with its own resident index), same launch shape."""
+    from synth.timeframe import batched_seed_counts, concat, make_batch
+    counts = batched_seed_counts(args.n_tf)
+    tfs = make_batch(counts, seed=0, workers=os.cpu_count())  # spawn pool before any CUDA call
+    import torch
+    from paper_2003_03174_b300 import autotune, trd
+    dev = torch.device("cuda", 0)
+    ctx = trd.Context(0)
+    params = tfs[0].params
+    seeds, trk, so, to = concat(tfs)
+    s_all, t_all = trd.to_device(seeds, dev), trd.to_device(trk, dev)
+    res_all = trd.alloc_results(int(so[-1]), dev)
+    stream = torch.cuda.Stream(device=dev)
+    big = int(np.argmax(counts))
+    with torch.cuda.stream(stream):
+        tuned = autotune.tune(ctx, trd.to_device(tfs[big].seeds, dev), trd.to_device(tfs[big].tracklets, dev),
+                              params, cache=None, reps=5)
+    shape = {k: tuned[k] for k in ("lanes_per_track", "block_threads", "min_blocks_per_sm")}
+    w = tuned["y_bin_width"]
+
+    # plain: one resident index and one launch pair per timeframe
+    plain = []
+    for k, tf in enumerate(tfs):
+        sv = {kk: (v[:, so[k]:so[k + 1]] if kk == "cov" else v[so[k]:so[k + 1]]).contiguous()
+              for kk, v in s_all.items()}
+        tv = {kk: v[to[k]:to[k + 1]] for kk, v in t_all.items()}
+        plain.append((sv, tv, ctx.index_create(max(tf.n_tracklets, 1), w), trd.alloc_results(tf.n_seeds, dev)))
+
+    def plain_step():
+        for sv, tv, idx, rv in plain:
+            idx.rebuild(tv, stream=stream)
+            ctx.follow(sv, idx, params, results=rv, stream=stream, **shape)
+
+    batch = ctx.batch_create(s_all, t_all, so, to, params, res_all, y_bin_width=w, **shape)
+
+    def timed(fn):
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                fn()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / args.steps
+
+    with ClockSampler(0) as clk:
+        t_plain = timed(plain_step)
+        t_batch = timed(lambda: batch.run(stream))
+    matched_b = int((res_all["n_trk"] >= 2).sum().item())
+    matched_p = sum(int((rv["n_trk"] >= 2).sum().item()) for _, _, _, rv in plain)
+    same = all(torch.equal(rv[key], res_all[key][..., so[k]:so[k + 1]])
+               for k, (_, _, _, rv) in enumerate(plain) for key in rv)
+    line = {
+        "metric": METRIC, "workload": "batched", "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batched: {len(tfs)} timeframes, {int(so[-1])} seeds, {int(to[-1])} tracklets, "
+                               f"seed counts log-uniform 5k-400k, N=3, 3-sigma road",
+                   "launch": shape, "index_y_bin_cm": w, "l2": "inputs (~1.5 GB) larger than L2"},
+        "batched": {"value": matched_b / t_batch, "ms_per_step": 1e3 * t_batch,
+                    "path": "trd_batch_run: one CUDA graph (index build over all timeframes + one persistent follow)"},
+        "plain": {"value": matched_p / t_plain, "ms_per_step": 1e3 * t_plain,
+                  "path": f"{len(tfs)} x (trd_index_rebuild + trd_follow) on one stream"},
+        "speedup_batched_vs_plain": t_plain / t_batch,
+        "results_identical": bool(same),
+        "gpu_launches_per_step": {"batched": 6, "plain": 6 * len(tfs)},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_served(args):
+    raise SystemExit("served workload: see the server")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -341,13 +422,21 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=20_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--workload", choices=["timeframe", "batched", "served"], default="timeframe")
+    ap.add_argument("--n-tf", type=int, default=64)
     ap.add_argument("--lanes", type=int, default=0, help="lanes per seed (with --no-autotune)")
     ap.add_argument("--block", type=int, default=0, help="block threads (with --no-autotune)")
     ap.add_argument("--min-blocks", type=int, default=0, help="register budget (with --no-autotune)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    return run_reference(args) if args.impl == "reference" else run_ours(args)
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "served":
+        return run_served(args)
+    return run_ours(args)
 
 
 if __name__ == "__main__":

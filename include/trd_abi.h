@@ -63,6 +63,7 @@ extern "C" {
 typedef struct trd_ctx trd_ctx_t;
 typedef struct trd_index trd_index_t;
 typedef struct trd_batch trd_batch_t;
+typedef struct trd_server trd_server_t;
 
 /* Seeds: ITS-TPC tracks extrapolated towards the TRD (Sec. 3), in any frame
  * alpha.  Device pointers, each n floats; cov is [15][n].  Read only.      */
@@ -242,6 +243,62 @@ TRD_API int trd_batch_create(trd_ctx_t *ctx, int32_t n_tf, const int32_t *seed_o
                              trd_batch_t **out);
 TRD_API int trd_batch_run(trd_batch_t *batch, void *stream);
 TRD_API int trd_batch_free(trd_batch_t *batch);
+
+/* ---- serving (Sec. 3.1: timeframes arrive continuously and are tracked
+ * synchronously with data taking) -------------------------------------------
+ * A server owns a scheduler thread, max_slots CUDA streams and one resident
+ * index per stream.  Requests are admitted in arrival order as soon as a
+ * stream is free and the request's device bytes fit mem_budget_bytes
+ * (inputs + results + the stream's index); admitted requests run
+ * concurrently on their streams, so the copies of one overlap the kernels of
+ * another, and a request that arrives while others are on the GPU starts as
+ * soon as a stream and memory free up.  Each request's arithmetic is that of
+ * trd_follow on its timeframe alone.                                        */
+typedef struct {
+    uint64_t mem_budget_bytes; /* device bytes for requests and indices (0 = 60 GiB) */
+    int32_t max_slots;         /* requests on the GPU at once, 1..64 (0 = 4) */
+    int32_t max_queue;         /* requests waiting for admission (0 = 1024) */
+    float y_bin_width;         /* index bin width in cm (0 = 2) */
+    trd_params_t params;       /* follower parameters of every request */
+    trd_launch_t launch;       /* follower launch shape (zeros = defaults) */
+} trd_server_cfg_t;
+
+/* Host-clock seconds (steady clock) of one request, and its GPU time. */
+typedef struct {
+    double submit_s, admit_s, done_s; /* done_s: stream callback after the results landed */
+    float gpu_ms;                     /* first input copy to last result copy, CUDA events */
+    int32_t slot;
+} trd_timing_t;
+
+/* trd_server_create: errors TRD_EINVAL (bad config or parameters),
+ * TRD_ENOMEM, TRD_ECUDA.  The server is owned by the caller; destroy it with
+ * trd_server_destroy, which finishes queued and running requests first.    */
+TRD_API int trd_server_create(trd_ctx_t *ctx, const trd_server_cfg_t *cfg, trd_server_t **out);
+
+/* trd_server_submit: queue one timeframe.  seeds, tracklets and results are
+ * HOST pointers (layouts as for trd_follow) that must stay valid until the
+ * request completes; page-locked host memory lets the copies overlap other
+ * requests' kernels.  *ticket identifies the request.  Errors: TRD_EINVAL,
+ * TRD_ENOMEM (the request alone exceeds the budget), TRD_EAGAIN (queue
+ * full: retry later).                                                       */
+TRD_API int trd_server_submit(trd_server_t *server, const trd_seeds_t *seeds,
+                              const trd_tracklets_t *tracklets, trd_results_t *results,
+                              uint64_t *ticket);
+
+/* trd_server_poll: non-blocking.  TRD_OK: the results are in the caller's
+ * host buffers and the ticket is released (timing filled if not NULL);
+ * TRD_EAGAIN: not finished; TRD_EINVAL: unknown or already released ticket;
+ * another negative code: the request failed (ticket released).
+ * trd_server_wait: the same, waiting at most timeout_ms on the host
+ * (TRD_ETIMEOUT when it runs out).                                          */
+TRD_API int trd_server_poll(trd_server_t *server, uint64_t ticket, trd_timing_t *timing);
+TRD_API int trd_server_wait(trd_server_t *server, uint64_t ticket, int32_t timeout_ms,
+                            trd_timing_t *timing);
+
+/* Requests waiting, requests on the GPU, device bytes held (I/O + indices). */
+TRD_API int trd_server_stats(trd_server_t *server, int32_t *queued, int32_t *in_flight,
+                             uint64_t *device_bytes);
+TRD_API int trd_server_destroy(trd_server_t *server);
 
 /* Geometry constants the library was built with, for cross-checks:
  * out[0..12] = n_sectors, n_stacks, n_layers, n_chambers, x_layer0,

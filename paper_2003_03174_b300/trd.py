@@ -22,7 +22,8 @@ EXPORTED = [
     "trd_ctx_create", "trd_ctx_destroy", "trd_ctx_sm_count", "trd_index_build", "trd_index_free",
     "trd_index_create", "trd_index_rebuild", "trd_index_info", "trd_follow", "trd_follow_tuned",
     "trd_geometry", "trd_version", "trd_index_copy_out", "trd_batch_create", "trd_batch_run",
-    "trd_batch_free",
+    "trd_batch_free", "trd_server_create", "trd_server_submit", "trd_server_poll", "trd_server_wait",
+    "trd_server_stats", "trd_server_destroy", "trd_index_build_noalloc",
 ]
 
 
@@ -58,6 +59,16 @@ class Results(C.Structure):
                                           "status", "tracklet_id")]
 
 
+class ServerCfg(C.Structure):
+    _fields_ = [("mem_budget_bytes", C.c_uint64), ("max_slots", C.c_int32), ("max_queue", C.c_int32),
+                ("y_bin_width", C.c_float), ("params", Params), ("launch", Launch)]
+
+
+class Timing(C.Structure):
+    _fields_ = [("submit_s", C.c_double), ("admit_s", C.c_double), ("done_s", C.c_double),
+                ("gpu_ms", C.c_float), ("slot", C.c_int32)]
+
+
 _lib = None
 
 
@@ -88,6 +99,14 @@ def lib():
                                        C.POINTER(vp)]
         L.trd_batch_run.argtypes = [vp, vp]
         L.trd_batch_free.argtypes = [vp]
+        L.trd_server_create.argtypes = [vp, C.POINTER(ServerCfg), C.POINTER(vp)]
+        L.trd_server_submit.argtypes = [vp, C.POINTER(Seeds), C.POINTER(Tracklets),
+                                        C.POINTER(Results), C.POINTER(C.c_uint64)]
+        L.trd_server_poll.argtypes = [vp, C.c_uint64, C.POINTER(Timing)]
+        L.trd_server_wait.argtypes = [vp, C.c_uint64, C.c_int32, C.POINTER(Timing)]
+        L.trd_server_stats.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(C.c_uint64)]
+        L.trd_server_destroy.argtypes = [vp]
+        L.trd_index_build_noalloc.argtypes = [C.POINTER(Tracklets), f32, vp, vp, vp, vp]
         L.trd_version.restype = C.c_char_p
         for fn in EXPORTED:
             if fn != "trd_version":
@@ -200,6 +219,96 @@ class Index:
     def __del__(self):
         try:
             self.free()
+        except Exception:
+            pass
+
+
+def _hptr(a):
+    """Host pointer of a numpy array or a CPU (possibly pinned) torch tensor."""
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return C.c_void_p(a.ctypes.data)
+
+
+def host_results(n: int, pinned: bool = False):
+    """Host result arrays (numpy, or pinned torch CPU tensors)."""
+    if pinned:
+        import torch
+        f = dict(dtype=torch.float32, pin_memory=True)
+        i = dict(dtype=torch.int32, pin_memory=True)
+        return dict(alpha=torch.empty(n, **f), x=torch.empty(n, **f), par=torch.empty(5, n, **f),
+                    cov=torch.empty(15, n, **f), chi2=torch.empty(n, **f), n_trk=torch.empty(n, **i),
+                    n_miss=torch.empty(n, **i), status=torch.empty(n, **i),
+                    tracklet_id=torch.empty(6, n, **i))
+    import numpy as np
+    f, i = np.float32, np.int32
+    return dict(alpha=np.empty(n, f), x=np.empty(n, f), par=np.empty((5, n), f), cov=np.empty((15, n), f),
+                chi2=np.empty(n, f), n_trk=np.empty(n, i), n_miss=np.empty(n, i), status=np.empty(n, i),
+                tracklet_id=np.empty((6, n), i))
+
+
+class Server:
+    """Serving loop (trd_server_t): submit host timeframes, poll tickets."""
+
+    def __init__(self, ctx: "Context", params: dict, mem_budget_bytes: int = 0, max_slots: int = 0,
+                 max_queue: int = 0, y_bin_width: float = 0.0, lanes_per_track: int = 0,
+                 block_threads: int = 0, min_blocks_per_sm: int = 0):
+        cfg = ServerCfg(int(mem_budget_bytes), int(max_slots), int(max_queue), float(y_bin_width),
+                        params_struct(params),
+                        Launch(int(lanes_per_track), int(block_threads), int(min_blocks_per_sm)))
+        h = C.c_void_p()
+        _check("trd_server_create", lib().trd_server_create(ctx.handle, C.byref(cfg), C.byref(h)))
+        self.handle = h
+        self.ctx = ctx
+        self._live = {}
+
+    def submit(self, seeds: dict, tracklets: dict, results: dict) -> int:
+        n = int(seeds["alpha"].shape[0])
+        m = int(tracklets["chamber"].shape[0])
+        ss = Seeds(*[_hptr(seeds[k]) for k in ("alpha", "x", "y", "z", "snp", "tgl", "q2pt", "cov")], n)
+        ts = Tracklets(*[_hptr(tracklets[k]) for k in ("chamber", "y", "z", "dy", "vyy", "vzz", "vyz")], m)
+        rs = Results(*[_hptr(results[k]) for k in ("alpha", "x", "par", "cov", "chi2", "n_trk",
+                                                   "n_miss", "status", "tracklet_id")])
+        t = C.c_uint64()
+        _check("trd_server_submit", lib().trd_server_submit(self.handle, C.byref(ss), C.byref(ts),
+                                                            C.byref(rs), C.byref(t)))
+        self._live[t.value] = (seeds, tracklets, results)
+        return t.value
+
+    def _done(self, fn, ticket, rc, tm):
+        if rc == TRD_EAGAIN or rc == TRD_ETIMEOUT:
+            return None
+        self._live.pop(ticket, None)
+        _check(fn, rc)
+        return dict(submit_s=tm.submit_s, admit_s=tm.admit_s, done_s=tm.done_s, gpu_ms=tm.gpu_ms,
+                    slot=tm.slot)
+
+    def poll(self, ticket: int):
+        """Timing dict when finished, None while pending (raises on failure)."""
+        tm = Timing()
+        rc = lib().trd_server_poll(self.handle, C.c_uint64(ticket), C.byref(tm))
+        return self._done("trd_server_poll", ticket, rc, tm)
+
+    def wait(self, ticket: int, timeout_ms: int = 60_000):
+        """Timing dict, or None if the bounded host wait ran out."""
+        tm = Timing()
+        rc = lib().trd_server_wait(self.handle, C.c_uint64(ticket), int(timeout_ms), C.byref(tm))
+        return self._done("trd_server_wait", ticket, rc, tm)
+
+    def stats(self):
+        q, f, b = C.c_int32(), C.c_int32(), C.c_uint64()
+        _check("trd_server_stats", lib().trd_server_stats(self.handle, C.byref(q), C.byref(f), C.byref(b)))
+        return dict(queued=q.value, in_flight=f.value, device_bytes=b.value)
+
+    def close(self):
+        if self.handle:
+            lib().trd_server_destroy(self.handle)
+            self.handle = None
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
         except Exception:
             pass
 
