@@ -169,21 +169,22 @@ int start_request(trd_server *S, Slot &slot, Request *r)
     return TRD_OK;
 }
 
-// make the slot's resident index large enough (scheduler thread, lock held,
-// slot idle); returns the index bytes added
-int ensure_index(trd_server *S, Slot &slot, int n_trk)
+// make the slot's resident index large enough (scheduler thread, lock NOT
+// held, slot reserved and idle); *added = index bytes added (may be negative)
+int ensure_index(trd_server *S, Slot &slot, int n_trk, long long *added)
 {
+    *added = 0;
     if (slot.index && slot.index->capacity >= n_trk) return TRD_OK;
     const int cap = std::max(n_trk, slot.index ? 2 * slot.index->capacity : n_trk);
     if (slot.index) {
-        S->index_used -= index_bytes(slot.index->capacity, S->cfg.y_bin_width);
+        *added -= static_cast<long long>(index_bytes(slot.index->capacity, S->cfg.y_bin_width));
         cudaStreamSynchronize(slot.stream);
         trd_host::index_release(slot.index);
         slot.index = nullptr;
     }
     int rc = trd_host::index_alloc(S->ctx, cap, S->cfg.y_bin_width, 1, &slot.index);
     if (rc) return rc;
-    S->index_used += index_bytes(cap, S->cfg.y_bin_width);
+    *added += static_cast<long long>(index_bytes(cap, S->cfg.y_bin_width));
     return TRD_OK;
 }
 
@@ -222,34 +223,39 @@ void worker_loop(trd_server *S)
                                                   S->cfg.y_bin_width)
                                     : 0;
             if (S->used + S->index_used + r->bytes + grow > S->cfg.mem_budget_bytes && !S->inflight.empty()) break;
+            // reserve the slot and the budget, then enqueue without the lock so
+            // that submit and poll never wait for copies or allocations
             S->queue.pop_front();
-            int rc = ensure_index(S, slot, r->trk.n);
-            if (!rc) {
-                r->slot = free_slot;
-                r->t_admit = now_s();
-                r->state.store(1);
-                slot.busy = r;
-                S->used += r->bytes;
-                S->inflight.push_back(r);
-                rc = start_request(S, slot, r);
+            r->slot = free_slot;
+            r->t_admit = now_s();
+            r->state.store(1);
+            slot.busy = r;
+            S->used += r->bytes;
+            S->index_used += grow;
+            S->inflight.push_back(r);
+            lk.unlock();
+            long long added = 0;
+            int rc = ensure_index(S, slot, r->trk.n, &added);
+            if (!rc) rc = start_request(S, slot, r);
+            if (rc) {
+                cudaStreamSynchronize(slot.stream);
+                if (r->dbuf) cudaFree(r->dbuf);
+                r->dbuf = nullptr;
+                (void)cudaGetLastError();
             }
+            lk.lock();
+            S->index_used += static_cast<size_t>(static_cast<long long>(added) - static_cast<long long>(grow));
             if (rc) {  // the request fails on its own; the server keeps going
                 r->error = rc;
                 r->t_done.store(now_s());
-                if (r->slot >= 0) {
-                    cudaStreamSynchronize(slot.stream);
-                    if (r->dbuf) cudaFree(r->dbuf);
-                    r->dbuf = nullptr;
-                    (void)cudaGetLastError();
-                    S->used -= r->bytes;
-                    slot.busy = nullptr;
-                    for (size_t k = 0; k < S->inflight.size(); ++k)
-                        if (S->inflight[k] == r) {
-                            S->inflight[k] = S->inflight.back();
-                            S->inflight.pop_back();
-                            break;
-                        }
-                }
+                S->used -= r->bytes;
+                slot.busy = nullptr;
+                for (size_t k = 0; k < S->inflight.size(); ++k)
+                    if (S->inflight[k] == r) {
+                        S->inflight[k] = S->inflight.back();
+                        S->inflight.pop_back();
+                        break;
+                    }
                 r->state.store(3);
                 S->cv.notify_all();
             }
