@@ -64,6 +64,26 @@ def _dist():
     return ws, rank, local
 
 
+def reduce_over_ranks(total_s: float, matched: int, device=None):
+    """Whole-job numbers: the slowest rank's timed total (max) and the matched
+    tracks of all ranks (sum).  Each rank follows its own timeframe, so this
+    is the only collective: on timing scalars, never on the data path."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(total_s), float(matched)
+    t = torch.tensor([float(total_s)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    m = torch.tensor([float(matched)], dtype=torch.float64, device=device)
+    dist.all_reduce(m)
+    return float(t.item()), float(m.item())
+
+
+def rank_workload_seed(rank: int) -> int:
+    """Seed of the timeframe a rank follows (weak scaling: one timeframe each)."""
+    return rank
+
+
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -195,7 +215,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     ctx = trd.Context(local)
 
-    tf = make_workload(WORKLOAD, seed=rank)  # each rank: its own timeframe
+    tf = make_workload(WORKLOAD, seed=rank_workload_seed(rank))  # each rank: its own timeframe
     seeds = trd.to_device(tf.seeds, dev)
     trk = trd.to_device(tf.tracklets, dev)
     n = tf.n_seeds
@@ -243,16 +263,7 @@ def run_ours(args):
     step_ms = [a.elapsed_time(c) for a, _, c in ev]
     follow_ms = [b.elapsed_time(c) for _, b, c in ev]
     index_ms = [a.elapsed_time(b) for a, b, _ in ev]
-    total_s = sum(step_ms) / 1e3
-    if ws > 1:
-        t = torch.tensor([total_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
-        m = torch.tensor([matched], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(m)
-        matched_all = float(m.item())
-    else:
-        matched_all = float(matched)
+    total_s, matched_all = reduce_over_ranks(sum(step_ms) / 1e3, matched, dev)
     value = matched_all * args.steps / total_s
 
     # end to end: pinned host inputs -> device, index + follow, results -> host
