@@ -307,7 +307,7 @@ def run_ours(args):
             "traffic_unit": "bytes per launch (ncu dram read+write)",
             "algorithmic_bytes_per_launch": n * FOLLOW_BYTES_PER_SEED,
             "follow_ms": statistics.mean(follow_ms), "index_ms": statistics.mean(index_ms)}
-    launches_per_step = 6  # count, 3 scan kernels, scatter, follow
+    launches_per_step = 7  # count, 3 scan kernels, scatter, seed prepare, follow
     clocks = clk.summary()
 
     if rank == 0:

@@ -491,25 +491,27 @@ __device__ __forceinline__ void load_state(const float *sm, int stride, TrackSta
 
 __device__ __forceinline__ bool cov_pd(const float *c)
 {
-    // Cholesky of the 5x5 (seed validity)
+    // Cholesky of the 5x5 (seed validity), without early exits: every pivot
+    // is computed and the matrix is positive definite when all are > 0.
     float L[15];
+    bool pd = true;
 #pragma unroll
     for (int j = 0; j < 5; ++j) {
         float d = c[cidx(j, j)];
 #pragma unroll
         for (int k = 0; k < j; ++k) d -= L[cidx(j, k)] * L[cidx(j, k)];
-        if (!(d > 0.0f)) return false;
-        const float ljj = sqrtf(d);
-        L[cidx(j, j)] = ljj;
+        pd = pd && d > 0.0f;
+        const float inv = rsqrtf(fmaxf(d, 1e-30f));
+        L[cidx(j, j)] = d * inv;
 #pragma unroll
         for (int i = j + 1; i < 5; ++i) {
             float x = c[cidx(i, j)];
 #pragma unroll
             for (int k = 0; k < j; ++k) x -= L[cidx(i, k)] * L[cidx(j, k)];
-            L[cidx(i, j)] = x / ljj;
+            L[cidx(i, j)] = x * inv;
         }
     }
-    return true;
+    return pd;
 }
 
 __device__ __forceinline__ void write_result(const ResultsView &o, int n, int i, const TrackState &s, float chi2,
@@ -593,14 +595,19 @@ struct Lane {
     bool alive;
 };
 
-// Load seed i, validate it and rotate it into the sector of its position.
-// Returns false (and writes the result) when the seed ends right here.
-template <int G>
-__device__ __forceinline__ bool start_seed(int i, int q, const SeedsView &sv, const Params &P, const ResultsView &o,
-                                           Lane &L)
+// Seed preparation, one thread per seed (all seeds take the same path, so
+// this runs without divergence): load the seed, validate it, rotate it into
+// the sector of its position.  A seed that ends here gets its final result;
+// a live seed's rotated state is parked in its own result slots (which the
+// follower overwrites at the end) with status -1:
+//   alpha <- sector, x <- x.hi, chi2 <- x.lo, par <- (y.hi, z, snp, tgl, q2pt),
+//   cov <- cov, n_miss <- bits of y.lo.
+__global__ void __launch_bounds__(256) k_seed_prepare(SeedsView sv, Params P, ResultsView o)
 {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = sv.n;
-    TrackState &s = L.s;
+    if (i >= n) return;
+    TrackState s;
     const float alpha = sv.alpha[i];
     const float sx = sv.x[i], sy = sv.y[i];
     s.x = {sx, 0.0f};
@@ -612,8 +619,8 @@ __device__ __forceinline__ bool start_seed(int i, int q, const SeedsView &sv, co
 #pragma unroll
     for (int k = 0; k < 15; ++k) s.c[k] = sv.cov[k * n + i];
     if (!(fabsf(s.f) < kMaxSnp) || !cov_pd(s.c)) {
-        if (q == 0) write_seed_result(o, sv, n, i, TRD_ST_SEED_INVALID);
-        return false;
+        write_seed_result(o, sv, n, i, TRD_ST_SEED_INVALID);
+        return;
     }
     const float phi = alpha + atan2f(sy, sx);
     float u = phi - kTwoPiHi * floorf(phi * (1.0f / kTwoPiHi));
@@ -624,9 +631,40 @@ __device__ __forceinline__ bool start_seed(int i, int q, const SeedsView &sv, co
     if (d.hi < -3.14159265f) d = df_add(d, df{kTwoPiHi, kTwoPiLo});
     s.sector = sec;
     if (!rotate(s, d, sec, P.bz)) {
-        if (q == 0) write_seed_result(o, sv, n, i, TRD_ST_PROP_FAIL);
-        return false;
+        write_seed_result(o, sv, n, i, TRD_ST_PROP_FAIL);
+        return;
     }
+    o.alpha[i] = static_cast<float>(sec);
+    o.x[i] = s.x.hi;
+    o.chi2[i] = s.x.lo;
+    o.par[0 * n + i] = s.y.hi;
+    o.par[1 * n + i] = s.z;
+    o.par[2 * n + i] = s.f;
+    o.par[3 * n + i] = s.t;
+    o.par[4 * n + i] = s.k;
+#pragma unroll
+    for (int k = 0; k < 15; ++k) o.cov[k * n + i] = s.c[k];
+    o.nmiss[i] = __float_as_int(s.y.lo);
+    o.status[i] = -1;
+}
+
+// Pick up seed i as prepared by k_seed_prepare.  Returns false when the seed
+// already has its final result.
+template <int G>
+__device__ __forceinline__ bool start_seed(int i, int q, const SeedsView &sv, const ResultsView &o, Lane &L)
+{
+    const int n = sv.n;
+    if (o.status[i] != -1) return false;
+    TrackState &s = L.s;
+    s.sector = static_cast<int>(o.alpha[i]);
+    s.x = {o.x[i], o.chi2[i]};
+    s.y = {o.par[0 * n + i], __int_as_float(o.nmiss[i])};
+    s.z = o.par[1 * n + i];
+    s.f = o.par[2 * n + i];
+    s.t = o.par[3 * n + i];
+    s.k = o.par[4 * n + i];
+#pragma unroll
+    for (int k = 0; k < 15; ++k) s.c[k] = o.cov[k * n + i];
     L.cbase = tf_of(i, sv.soff, sv.n_tf) * kChambers;
     L.alive = q == 0;
     L.score = 0.0f;
@@ -777,7 +815,7 @@ __global__ void __launch_bounds__(128, MINB) k_follow(SeedsView sv, IndexView ix
         if (!have) {
             i = fetch_seed<G>(counter, gmask, q);
             if (i >= sv.n) break;
-            have = start_seed<G>(i, q, sv, P, o, H);
+            have = start_seed<G>(i, q, sv, o, H);
             l = 0;
             if (!have) continue;
         }
@@ -805,6 +843,8 @@ static int launch(const trd_ctx *ctx, const SeedsView &sv, const IndexView &ix, 
     const long long need = (static_cast<long long>(sv.n) + groups - 1) / groups;
     const int grid = static_cast<int>(std::min<long long>(need, static_cast<long long>(ctx->sm_count) * per_sm));
     TRD_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), s));
+    k_seed_prepare<<<(sv.n + 255) / 256, 256, 0, s>>>(sv, P, o);
+    TRD_CUDA_TRY(cudaGetLastError());
     k_follow<G, NH, MINB><<<grid, block, smem, s>>>(sv, ix, P, o, counter);
     TRD_CUDA_TRY(cudaGetLastError());
     return TRD_OK;
