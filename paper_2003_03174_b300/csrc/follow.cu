@@ -380,19 +380,22 @@ struct ExtList {
 // Road query + candidate tests for one hypothesis at layer l (Sec. 3).
 // The road bounds z_tl to z +- Rz (pad rows r_lo..r_hi) and the measured y to
 // y +- (W + |tan tau| Rz) (y bins b_lo..b_hi); each y bin is one contiguous
-// range of the index over those rows.  Two bins' offsets are loaded at once,
-// and candidate records four at a time, so a layer costs about two dependent
-// global round trips.
+// range of the index over those rows.  The candidates of the first two bins
+// form one list: their {y, z} are read eight at a time (one dependent L2
+// round trip, which also brings each 32-byte record into L1), a bit mask
+// keeps those inside the road's y/z bounds, and only those get the full test
+// (record read again from L1).  More than two bins (very wide roads) are
+// handled the same way, two at a time.
 template <int NH>
-__device__ __forceinline__ void test_record(const float4 &a, int pos, const IndexView &ix, float tt, float z, float yh,
-                                            float yl, float W, float Rz, float n2, float syy_trk, float syz_trk,
-                                            float c11, float vyy_res, int resmode, float dy_pred, float gate,
-                                            float cut, float score, ExtList<NH> &L)
+__device__ __forceinline__ void full_test(int pos, const IndexView &ix, float tt, float z, float yh, float yl,
+                                          float n2, float syy_trk, float syz_trk, float c11, float vyy_res,
+                                          int resmode, float dy_pred, float gate, float cut, float score,
+                                          ExtList<NH> &L)
 {
+    const float4 a = __ldg(&ix.rec[2 * pos]);
+    const float4 v = __ldg(&ix.rec[2 * pos + 1]);
     const float ry = (__fsub_rn(a.x, yh) - yl) + tt * (z - a.y);
     const float rz = a.y - z;
-    if (fabsf(ry) > W || fabsf(rz) > Rz) return;
-    const float4 v = __ldg(&ix.rec[2 * pos + 1]);  // same 32-byte sector as a
     const float vyy = resmode ? vyy_res : v.x;
     const float S00 = syy_trk + vyy;
     const float S01 = syz_trk + v.z;
@@ -428,6 +431,7 @@ __device__ void scan_candidates(const TrackState &s, int l, int chamber, int cba
     const int r_lo = row_of_z(z - Rz, zlo), r_hi = row_of_z(z + Rz, zlo);
     const float half = W + fabsf(tt) * Rz + 1e-3f + 1e-6f * fabsf(yh);
     const int b_lo = ybin_of(yh - half, ix.inv_w, ix.nb), b_hi = ybin_of(yh + half, ix.inv_w, ix.nb);
+    const float2 *yz = reinterpret_cast<const float2 *>(ix.rec);  // {y, z} of record p at yz[4 p]
     for (int b = b_lo; b <= b_hi; b += 2) {
         const int base = bucket_of(cbase + chamber, b, 0, ix.nb);
         const bool two = b + 1 <= b_hi;
@@ -438,20 +442,31 @@ __device__ void scan_candidates(const TrackState &s, int l, int chamber, int cba
             beg1 = __ldg(&ix.offsets[base + kRowsPerStack + r_lo]);
             end1 = __ldg(&ix.offsets[base + kRowsPerStack + r_hi + 1]);
         }
+        const int n0 = end0 - beg0;
+        const int n = n0 + (end1 - beg1);
 #pragma unroll 1
-        for (int k = 0; k < 2; ++k) {
-            const int beg = k ? beg1 : beg0, end = k ? end1 : end0;
-#pragma unroll 1
-            for (int pos = beg; pos < end; pos += 4) {
-                float4 a[4];
+        for (int j0 = 0; j0 < n; j0 += 8) {
+            float2 c[8];
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    a[u] = pos + u < end ? __ldg(&ix.rec[2 * (pos + u)]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            for (int u = 0; u < 8; ++u) {
+                const int j = j0 + u;
+                const int pos = j < n0 ? beg0 + j : beg1 + (j - n0);
+                c[u] = j < n ? __ldg(&yz[4 * pos]) : make_float2(INFINITY, INFINITY);
+            }
+            unsigned mask = 0;
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (pos + u < end)
-                        test_record<NH>(a[u], pos + u, ix, tt, z, yh, yl, W, Rz, n2, syy_trk, syz_trk, c11, vyy_res,
-                                        P.resmode, dy_pred, gate, P.cut, score, L);
+            for (int u = 0; u < 8; ++u) {
+                const float ry = (__fsub_rn(c[u].x, yh) - yl) + tt * (z - c[u].y);
+                const float rz = c[u].y - z;
+                if (fabsf(ry) <= W && fabsf(rz) <= Rz) mask |= 1u << u;
+            }
+            while (mask) {
+                const int u = __ffs(mask) - 1;
+                mask &= mask - 1u;
+                const int j = j0 + u;
+                const int pos = j < n0 ? beg0 + j : beg1 + (j - n0);
+                full_test<NH>(pos, ix, tt, z, yh, yl, n2, syy_trk, syz_trk, c11, vyy_res, P.resmode, dy_pred, gate,
+                              P.cut, score, L);
             }
         }
     }
