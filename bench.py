@@ -237,32 +237,55 @@ def run_ours(args):
         index.rebuild(trk, stream=stream)
         ctx.follow(seeds, index, tf.params, results=res, stream=stream, **shape)
 
+    # the whole step (index rebuild + follow) as one CUDA-graph replay: the
+    # library's single-timeframe batch
+    graph = None
+    if not args.no_graph:
+        graph = ctx.batch_create(seeds, trk, [0, n], [0, tf.n_tracklets], tf.params, res,
+                                 y_bin_width=bin_width, **shape)
+
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             step()
     torch.cuda.synchronize()
     matched = int((res["n_trk"] >= 2).sum().item())
 
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    def timed_steps(run_step, split):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+               torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                run_step()
+            torch.cuda.synchronize()
+            for k in range(args.steps):
+                flush.add_(1.0)  # write 512 MB: evict L2 between timed steps
+                ev[k][0].record(stream)
+                if split:
+                    index.rebuild(trk, stream=stream)
+                    ev[k][1].record(stream)
+                    ctx.follow(seeds, index, tf.params, results=res, stream=stream, **shape)
+                else:
+                    run_step()
+                    ev[k][1].record(stream)
+                ev[k][2].record(stream)
+        torch.cuda.synchronize()
+        return ([a.elapsed_time(c) for a, _, c in ev], [a.elapsed_time(b) for a, b, _ in ev],
+                [b.elapsed_time(c) for _, b, c in ev])
+
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        with torch.cuda.stream(stream):
-            for k in range(args.steps):
-                flush.add_(1.0)  # write 512 MB: evict L2 between timed steps
-                ev[k][0].record(stream)
-                index.rebuild(trk, stream=stream)
-                ev[k][1].record(stream)
-                ctx.follow(seeds, index, tf.params, results=res, stream=stream, **shape)
-                ev[k][2].record(stream)
-        torch.cuda.synchronize()
+        if graph is not None:
+            step_ms, _, _ = timed_steps(lambda: graph.run(stream), False)
+        else:
+            step_ms = None
+        # separate launches, for the split between index build and follower
+        split_ms, index_ms, follow_ms = timed_steps(step, True)
+        if step_ms is None:
+            step_ms = split_ms
     if ws > 1:
         torch.distributed.barrier()
-    step_ms = [a.elapsed_time(c) for a, _, c in ev]
-    follow_ms = [b.elapsed_time(c) for _, b, c in ev]
-    index_ms = [a.elapsed_time(b) for a, b, _ in ev]
     total_s, matched_all = reduce_over_ranks(sum(step_ms) / 1e3, matched, dev)
     value = matched_all * args.steps / total_s
 
@@ -306,8 +329,9 @@ def run_ours(args):
             and tf.n_seeds == 200_000 else None,
             "traffic_unit": "bytes per launch (ncu dram read+write)",
             "algorithmic_bytes_per_launch": n * FOLLOW_BYTES_PER_SEED,
-            "follow_ms": statistics.mean(follow_ms), "index_ms": statistics.mean(index_ms)}
-    launches_per_step = 7  # count, 3 scan kernels, scatter, seed prepare, follow
+            "follow_ms": statistics.mean(follow_ms), "index_ms": statistics.mean(index_ms),
+            "step_ms_separate_launches": statistics.mean(split_ms)}
+    launches_per_step = 7  # count, 3 scan kernels, scatter, seed prepare, follow (one graph)
     clocks = clk.summary()
 
     if rank == 0:
@@ -323,6 +347,8 @@ def run_ours(args):
                        "matched_per_rank_step": matched, "l2": "flushed (512 MB write) between steps",
                        "index_y_bin_cm": bin_width or 2.0, "launch": shape,
                        "autotuned": tuned is not None,
+                       "step": "one CUDA-graph replay (trd_batch_run, 1 timeframe)" if graph is not None
+                       else "trd_index_rebuild + trd_follow launches",
                        "parallelism": f"replicas x{ws} (independent timeframes)"},
             "roofline": roof,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
@@ -566,6 +592,7 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=20_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="time separate launches instead of the graph")
     ap.add_argument("--workload", choices=["timeframe", "batched", "served"], default="timeframe")
     ap.add_argument("--n-tf", type=int, default=64)
     ap.add_argument("--n-payloads", type=int, default=16)
