@@ -43,6 +43,11 @@ RESULT_BYTES = 128
 RECORD_BYTES = 32
 IN_ROAD_PER_SEED = 15.75
 FOLLOW_BYTES_PER_SEED = SEED_BYTES + RESULT_BYTES + RECORD_BYTES * IN_ROAD_PER_SEED
+# FP32 operations of the follower per seed (model of its arithmetic, FMA = 2):
+# per layer transport ~200, material ~60, road set-up ~40, ~6 pre-filtered
+# candidates x 10, 2.6 in-road candidates x 25, Joseph update ~240 on ~80 % of
+# layers; six layers.
+FOLLOW_FLOPS_PER_SEED = 3700
 L2_FLUSH_BYTES = 512 << 20
 # DRAM bytes (read + write) of one k_follow launch on this workload from one
 # ncu capture (profiles/kernels_timeframe.md), valid only for the kernel source
@@ -289,33 +294,37 @@ def run_ours(args):
     total_s, matched_all = reduce_over_ranks(sum(step_ms) / 1e3, matched, dev)
     value = matched_all * args.steps / total_s
 
-    # end to end: pinned host inputs -> device, index + follow, results -> host
+    # end to end through the library's host-buffer entry point (the server):
+    # pinned host inputs -> device, index + follow, results -> host, with the
+    # copies of one timeframe overlapping the kernels of another
     host_in = {k: torch.from_numpy(v).pin_memory() for k, v in tf.seeds.items()}
     host_trk = {k: torch.from_numpy(v).pin_memory() for k, v in tf.tracklets.items()}
-    host_out = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in res.items()}
     h2d = sum(v.numel() * v.element_size() for v in list(host_in.values()) + list(host_trk.values()))
-    d2h = sum(v.numel() * v.element_size() for v in host_out.values())
-    dev_in = {k: torch.empty_like(v, device=dev) for k, v in host_in.items()}
-    dev_trk = {k: torch.empty_like(v, device=dev) for k, v in host_trk.items()}
-    e_steps = max(3, args.steps // 2)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with torch.cuda.stream(stream):
-        for it in range(e_steps + 1):
-            if it == 1:
-                e0.record(stream)
-            for k, v in host_in.items():
-                dev_in[k].copy_(v, non_blocking=True)
-            for k, v in host_trk.items():
-                dev_trk[k].copy_(v, non_blocking=True)
-            index.rebuild(dev_trk, stream=stream)
-            ctx.follow(dev_in, index, tf.params, results=res, stream=stream, **shape)
-            for k, v in res.items():
-                host_out[k].copy_(v, non_blocking=True)
-        e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_s = e0.elapsed_time(e1) / 1e3
-    e2e_matched = int((host_out["n_trk"] >= 2).sum().item())
-    e2e_value = e2e_matched * ws * e_steps / e2e_s
+    slots = 4
+    host_outs = [trd.host_results(n, pinned=True) for _ in range(slots)]
+    d2h = sum(v.numel() * v.element_size() for v in host_outs[0].values())
+    srv = trd.Server(ctx, tf.params, max_slots=slots, y_bin_width=bin_width, **shape)
+    for o in host_outs:  # warm: every slot's resident index
+        srv.wait(srv.submit(host_in, host_trk, o))
+    e_steps = max(8, args.steps)
+    t0 = time.monotonic()
+    tickets = [srv.submit(host_in, host_trk, host_outs[k % slots]) for k in range(min(slots, e_steps))]
+    done = 0
+    first_submit, last_done = None, 0.0
+    k_next = len(tickets)
+    while tickets:
+        t = tickets.pop(0)
+        tm = srv.wait(t, 60_000)
+        first_submit = tm["submit_s"] if first_submit is None else min(first_submit, tm["submit_s"])
+        last_done = max(last_done, tm["done_s"])
+        done += 1
+        if k_next < e_steps:  # reuse the finished request's output buffer
+            tickets.append(srv.submit(host_in, host_trk, host_outs[k_next % slots]))
+            k_next += 1
+    e2e_s = last_done - first_submit
+    e2e_matched = int((host_outs[0]["n_trk"] >= 2).sum().item())
+    srv.close()
+    e2e_value = e2e_matched * ws * done / e2e_s
 
     peaks = _peaks()
     hbm = peaks.get("hbm_gbs")
@@ -331,6 +340,11 @@ def run_ours(args):
             "algorithmic_bytes_per_launch": n * FOLLOW_BYTES_PER_SEED,
             "follow_ms": statistics.mean(follow_ms), "index_ms": statistics.mean(index_ms),
             "step_ms_separate_launches": statistics.mean(split_ms)}
+    fp32_peak = ctx.fp32_peak_tflops()
+    alu = {"bound": "alu", "achieved": n * FOLLOW_FLOPS_PER_SEED / follow_avg_s / 1e12, "peak": fp32_peak,
+           "unit": "TFLOP/s", "peak_source": "measured by trd_measure_fp32_peak (FMA chains)"}
+    alu["frac"] = alu["achieved"] / fp32_peak
+    roof["alu_check"] = alu
     launches_per_step = 7  # count, 3 scan kernels, scatter, seed prepare, follow (one graph)
     clocks = clk.summary()
 
@@ -353,7 +367,8 @@ def run_ours(args):
             "roofline": roof,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h),
-                    "path": "pinned host -> cudaMemcpyAsync -> trd_index_rebuild + trd_follow -> host"},
+                    "path": "trd_server_submit/wait with pinned host buffers, 4 requests in flight "
+                            "(copies in, index rebuild, follow, copies out per request)"},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
             "seeds_per_s": n * ws * args.steps / total_s,

@@ -300,6 +300,12 @@ TRD_API int trd_server_stats(trd_server_t *server, int32_t *queued, int32_t *in_
                              uint64_t *device_bytes);
 TRD_API int trd_server_destroy(trd_server_t *server);
 
+/* FP32 FMA throughput of the context's device in TFLOP/s (independent FMA
+ * chains on every SM, best of 5 timed launches): the denominator of the
+ * follower's arithmetic roofline.  Measurement only (not a step of the
+ * method); synchronises the device.                                         */
+TRD_API int trd_measure_fp32_peak(trd_ctx_t *ctx, double *tflops);
+
 /* Geometry constants the library was built with, for cross-checks:
  * out[0..12] = n_sectors, n_stacks, n_layers, n_chambers, x_layer0,
  * dx_layer, stack_length, z_min, tilt_deg, drift_length, lorentz_deg,

@@ -23,7 +23,7 @@ EXPORTED = [
     "trd_index_create", "trd_index_rebuild", "trd_index_info", "trd_follow", "trd_follow_tuned",
     "trd_geometry", "trd_version", "trd_index_copy_out", "trd_batch_create", "trd_batch_run",
     "trd_batch_free", "trd_server_create", "trd_server_submit", "trd_server_poll", "trd_server_wait",
-    "trd_server_stats", "trd_server_destroy", "trd_index_build_noalloc",
+    "trd_server_stats", "trd_server_destroy", "trd_index_build_noalloc", "trd_measure_fp32_peak",
 ]
 
 
@@ -107,6 +107,7 @@ def lib():
         L.trd_server_stats.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(C.c_uint64)]
         L.trd_server_destroy.argtypes = [vp]
         L.trd_index_build_noalloc.argtypes = [C.POINTER(Tracklets), f32, vp, vp, vp, vp]
+        L.trd_measure_fp32_peak.argtypes = [vp, C.POINTER(C.c_double)]
         L.trd_version.restype = C.c_char_p
         for fn in EXPORTED:
             if fn != "trd_version":
@@ -345,6 +346,11 @@ class Context:
         _check("trd_ctx_create", lib().trd_ctx_create(int(device), C.byref(h)))
         self.handle = h
         self.device = device
+
+    def fp32_peak_tflops(self) -> float:
+        v = C.c_double()
+        _check("trd_measure_fp32_peak", lib().trd_measure_fp32_peak(self.handle, C.byref(v)))
+        return v.value
 
     @property
     def sm_count(self) -> int:
