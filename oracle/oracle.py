@@ -18,10 +18,33 @@ _i = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 STATUS_PROP_FAIL, STATUS_STOPPED, STATUS_SEED_INVALID = 1, 2, 4
 
 
+class use_library:
+    """Run the wrappers against another build of trd_oracle.c (tests that plant
+    a mistake in a copy of the oracle use this)."""
+
+    def __init__(self, path):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        self.saved = _lib
+        _lib = _load(self.path)
+        return _lib
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
+
+
 def lib():
     global _lib
     if _lib is None:
-        path = _build.build()
+        _lib = _load(_build.build())
+    return _lib
+
+
+def _load(path):
+    if True:
         L = C.CDLL(path)
         L.ora_propagate.argtypes = [_d, _d, C.c_double, C.c_double, C.c_void_p, C.c_void_p]
         L.ora_propagate.restype = C.c_int
@@ -47,8 +70,7 @@ def lib():
         L.ora_candidates.argtypes = [_d, _d, C.c_int, C.c_int, C.c_int, _i, _f, _f, _f, _f, _f,
                                      _f, _d, _i, C.c_int, _i, _d]
         L.ora_candidates.restype = C.c_int
-        _lib = L
-    return _lib
+        return L
 
 
 def _vec(a, n):
@@ -190,5 +212,5 @@ def _params_arrays(params):
     return pd, pi
 
 
-__all__ = ["propagate", "rotate", "material", "bethe", "highland", "update", "chi2",
+__all__ = ["use_library", "propagate", "rotate", "material", "bethe", "highland", "update", "chi2",
            "cov_is_pd", "constants", "follow", "to_layer", "candidates", "lib"]

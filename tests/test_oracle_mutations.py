@@ -1,0 +1,98 @@
+"""Plant plausible mistakes in copies of the oracle and check that a pin
+catches each one (a flipped sign, a dropped Jacobian term, a transposed
+operand, a wrong tilt or Lorentz sign, a broken selection order).  Mistakes
+in the material step are expected to survive: that part has no counterpart in
+the paper beyond "energy loss" and is parity unpinned."""
+import os
+import subprocess
+
+import pytest
+
+from oracle import oracle as O
+import test_oracle_pins as P
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(os.path.dirname(HERE), "oracle", "trd_oracle.c")
+
+PINNED = [
+    ("curvature sign", "const double rho = drho_dk * k;", "const double rho = -drho_dk * k;"),
+    ("dropped dy/dk term", "J[0][4] = dx * dh_df1 * drho_dk * dx;", "J[0][4] = 0.0;"),
+    ("transposed operand in J C J^T", "s += t[i][k] * J[j][k];", "s += t[i][k] * J[k][j];"),
+    ("chord slope", "const double h = (f0 + f1) / rs;", "const double h = (f0 + f1) / (2.0 * rs);"),
+    ("arc series", "return 1.0 + w2 / 6.0 + 3.0 * w2 * w2 / 40.0;", "return 1.0 + w2 / 3.0 + 3.0 * w2 * w2 / 40.0;"),
+    ("rotation dsnp/dy sign", "J[2][0] = -rho * sd;", "J[2][0] = rho * sd;"),
+    ("rotation dy/dy inverted", "J[0][0] = r / rn;", "J[0][0] = rn / r;"),
+    ("pad tilt sign", "static double tilt_tan(int l) { return tan((l % 2 == 0 ? 1.0 : -1.0)",
+     "static double tilt_tan(int l) { return tan((l % 2 == 0 ? -1.0 : 1.0)"),
+    ("tilt term in residual", "o->r[0] = ytl - (st[2] - tt * (st[3] - ztl));",
+     "o->r[0] = ytl - (st[2] + tt * (st[3] - ztl));"),
+    ("dropped tilt in S01", "o->S[1] = c[1] - tt * c[2] + vyz;", "o->S[1] = c[1] + vyz;"),
+    ("chi2 cross-term sign", "o->chi2 = (o->S[2] * o->r[0] * o->r[0] - 2.0 * o->S[1]",
+     "o->chi2 = (o->S[2] * o->r[0] * o->r[0] + 2.0 * o->S[1]"),
+    ("gain index", "K[i][a] = CHt[i][0] * Si[0][a] + CHt[i][1] * Si[1][a];",
+     "K[i][a] = CHt[i][0] * Si[a][0] + CHt[i][1] * Si[a][0];"),
+    ("deflection prediction", "const double dy_pred = kDriftLength * u;", "const double dy_pred = kDriftLength * f;"),
+    ("Lorentz angle sign", "static double lorentz_tan(double bz) { return tan((bz >= 0 ? 1.0 : -1.0)",
+     "static double lorentz_tan(double bz) { return tan((bz >= 0 ? -1.0 : 1.0)"),
+    ("selection keeps the worst", "if (a->score < b->score) return -1;\n    if (a->score > b->score) return 1;",
+     "if (a->score > b->score) return -1;\n    if (a->score < b->score) return 1;"),
+    ("missing budget off by one", "if (work[hi].nmiss < P->max_missing)", "if (work[hi].nmiss <= P->max_missing)"),
+    ("road uses n^2", "const double s[4] = {P->n_sigma_road - ny,", "const double s[4] = {P->n_sigma_road * P->n_sigma_road - ny,"),
+]
+
+UNPINNED = [
+    ("scattering on snp without cos^2", "c[ci(2, 2)] += th2 * r * r * t2;", "c[ci(2, 2)] += th2 * r * t2;"),
+    ("energy loss halved", "const double de = ora_bethe(p / kMassPion) * xrho * 1e-3;",
+     "const double de = 0.5 * ora_bethe(p / kMassPion) * xrho * 1e-3;"),
+]
+
+PINS = [
+    lambda: P.test_helix_matches_circle_intersection(12.6),
+    lambda: P.test_helix_matches_circle_intersection(-25.0),
+    lambda: P.test_transport_jacobian_matches_finite_differences(0.5),
+    lambda: P.test_transport_jacobian_small_curvature_series_branch(),
+    lambda: P.test_transport_covariance_is_j_c_jt_and_stays_pd(),
+    lambda: P.test_rotation_jacobian_matches_finite_differences(0.5),
+    lambda: P.test_rotation_round_trip_is_identity(),
+    lambda: P.test_kalman_update_equals_information_form(0),
+    lambda: P.test_pad_tilt_sign_residual_vanishes_on_tilted_measurement(),
+    lambda: P.test_zero_noise_truth_is_recovered_exactly(),
+    lambda: P.test_zero_noise_with_pad_rows_assigns_truth(),
+    lambda: P.test_dy_gate_at_four_sigma(),
+    lambda: P.test_road_boundary_at_n_sigma(),
+    lambda: P.test_tiny_efficiency_and_purity(),
+    lambda: P.test_greedy_n1_takes_best_chi2_each_layer(),
+    lambda: P.test_beam_search_equals_exhaustive_enumeration(),
+]
+
+
+def _build_mutant(tmp_path, name, old, new):
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation '{name}' does not apply"
+    mut = tmp_path / (name.replace(" ", "_").replace("/", "_") + ".c")
+    mut.write_text(src.replace(old, new))
+    so = str(mut) + ".so"
+    subprocess.run(["gcc", "-O1", "-fopenmp", "-fPIC", "-shared", "-std=c11", str(mut), "-o", so, "-lm"],
+                   check=True)
+    return so
+
+
+def _caught(so):
+    with O.use_library(so):
+        for pin in PINS:
+            try:
+                pin()
+            except (AssertionError, ValueError, FloatingPointError):
+                return True
+    return False
+
+
+@pytest.mark.parametrize("name,old,new", PINNED, ids=[m[0] for m in PINNED])
+def test_pins_catch_planted_mistake(tmp_path, name, old, new):
+    assert _caught(_build_mutant(tmp_path, name, old, new)), f"no pin caught: {name}"
+
+
+@pytest.mark.parametrize("name,old,new", UNPINNED, ids=[m[0] for m in UNPINNED])
+def test_material_mistakes_are_not_pinned(tmp_path, name, old, new):
+    # documents the unpinned part: these survive every pin
+    assert not _caught(_build_mutant(tmp_path, name, old, new)), f"now pinned: {name}"

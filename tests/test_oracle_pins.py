@@ -509,3 +509,31 @@ def test_greedy_n1_takes_best_chi2_each_layer():
                 assert got == -1
                 nmiss += 1
         assert nmiss == r["n_miss"][i]
+
+
+def test_road_boundary_at_n_sigma():
+    """Sec. 3: tracklets inside a search road from the covariance.  Shift the
+    true layer-0 tracklet by 2.9 and 3.1 of its residual's y sigma (3-sigma
+    road; chi2 stays below the cut of 15 either way, so only the road
+    decides)."""
+    p = G.default_params(material_on=0, n_sigma_road=3.0, chi2_cut=15.0)
+    tf = make_timeframe(150, seed=19, noise=0.0, eff=1.0, smear=False, snap_z=False, params=p)
+    ok = np.nonzero(tf.truth_ids[:, 0] >= 0)[0][:60]
+    sig = []
+    for i in ok:
+        st = np.array([tf.seeds[k][i] for k in ("alpha", "x", "y", "z", "snp", "tgl", "q2pt")], dtype=np.float64)
+        c = tf.seeds["cov"][:, i].astype(np.float64)
+        phi = st[0] + math.atan2(st[2], st[1])
+        sec = int(math.floor((phi % (2 * math.pi)) / math.radians(20.0))) % 18
+        _, st, c, _ = O.rotate(st, c, math.radians(20.0 * (sec + 0.5)), p["bz"])
+        _, st, c, sec, ch = O.to_layer(st, c, sec, 0, p)
+        tt = G.pad_tilt_tan(0)
+        syy = c[0] - 2 * tt * c[1] + tt * tt * c[2] + tf.tracklets["vyy"][tf.truth_ids[i, 0]]
+        sig.append(math.sqrt(syy))
+    j = tf.truth_ids[ok, 0]
+    for k, expect in ((2.9, True), (3.1, False)):
+        t2 = {kk: v.copy() for kk, v in tf.tracklets.items()}
+        t2["y"][j] = (t2["y"][j].astype(np.float64) + k * np.array(sig)).astype(np.float32)
+        r = O.follow(tf.seeds, t2, p, seed_index=ok)
+        got = r["tracklet_id"][0] == j
+        assert got.mean() > 0.95 if expect else got.mean() < 0.05
