@@ -25,6 +25,8 @@ constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
+constexpr int kIlp = 4;  // tracklets per thread per loop iteration (loads issued together)
+
 __global__ void __launch_bounds__(kCountThreads)
 k_index_count(const int32_t *__restrict__ ch, const float *__restrict__ y, const float *__restrict__ z,
               const float *__restrict__ dy, const float *__restrict__ vyy, const float *__restrict__ vzz,
@@ -34,24 +36,43 @@ k_index_count(const int32_t *__restrict__ ch, const float *__restrict__ y, const
 {
     float myy = 0.0f, mzz = 0.0f;
     int rejected = 0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int c = ch[i];
-        const float yy = y[i], zz = z[i], dd = dy[i], a = vyy[i], b = vzz[i], cc = vyz[i];
-        const bool ok = c >= 0 && c < trd::kChambers && isfinite(yy) && isfinite(zz) && isfinite(dd) &&
-                        isfinite(a) && isfinite(b) && isfinite(cc) && a >= 0.0f && b >= 0.0f;
-        if (!ok) {
-            bucket[i] = -1;
-            rank[i] = 0;
-            ++rejected;
-            continue;
+    const int stride = gridDim.x * blockDim.x;
+    for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += stride * kIlp) {
+        int c[kIlp];
+        float yy[kIlp], zz[kIlp], dd[kIlp], a[kIlp], b[kIlp], cc[kIlp];
+#pragma unroll
+        for (int u = 0; u < kIlp; ++u) {
+            const int i = i0 + u * stride;
+            const bool in = i < n;
+            c[u] = in ? __ldg(&ch[i]) : -1;
+            yy[u] = in ? __ldg(&y[i]) : 0.0f;
+            zz[u] = in ? __ldg(&z[i]) : 0.0f;
+            dd[u] = in ? __ldg(&dy[i]) : 0.0f;
+            a[u] = in ? __ldg(&vyy[i]) : 0.0f;
+            b[u] = in ? __ldg(&vzz[i]) : 0.0f;
+            cc[u] = in ? __ldg(&vyz[i]) : 0.0f;
         }
-        const int row = trd::row_of_z(zz, trd::stack_z_lo(trd::stack_of_chamber(c)));
-        const int yb = trd::ybin_of(yy, inv_w, nb);
-        const int bk = trd::bucket_of(trd::tf_of(i, toff, n_tf) * trd::kChambers + c, yb, row, nb);
-        bucket[i] = bk;
-        rank[i] = atomicAdd(&counts[bk], 1);
-        myy = fmaxf(myy, a);
-        mzz = fmaxf(mzz, b);
+#pragma unroll
+        for (int u = 0; u < kIlp; ++u) {
+            const int i = i0 + u * stride;
+            if (i >= n) continue;
+            const bool ok = c[u] >= 0 && c[u] < trd::kChambers && isfinite(yy[u]) && isfinite(zz[u]) &&
+                            isfinite(dd[u]) && isfinite(a[u]) && isfinite(b[u]) && isfinite(cc[u]) &&
+                            a[u] >= 0.0f && b[u] >= 0.0f;
+            if (!ok) {
+                bucket[i] = -1;
+                rank[i] = 0;
+                ++rejected;
+                continue;
+            }
+            const int row = trd::row_of_z(zz[u], trd::stack_z_lo(trd::stack_of_chamber(c[u])));
+            const int yb = trd::ybin_of(yy[u], inv_w, nb);
+            const int bk = trd::bucket_of(trd::tf_of(i, toff, n_tf) * trd::kChambers + c[u], yb, row, nb);
+            bucket[i] = bk;
+            rank[i] = atomicAdd(&counts[bk], 1);
+            myy = fmaxf(myy, a[u]);
+            mzz = fmaxf(mzz, b[u]);
+        }
     }
     // block reduction of the maxima and the rejected count
     for (int o = 16; o > 0; o >>= 1) {
@@ -69,16 +90,16 @@ k_index_count(const int32_t *__restrict__ ch, const float *__restrict__ y, const
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        float a = 0.0f, b = 0.0f;
+        float am = 0.0f, bm = 0.0f;
         int r = 0;
         for (int k = 0; k < kCountThreads / 32; ++k) {
-            a = fmaxf(a, s_yy[k]);
-            b = fmaxf(b, s_zz[k]);
+            am = fmaxf(am, s_yy[k]);
+            bm = fmaxf(bm, s_zz[k]);
             r += s_rej[k];
         }
         // non-negative floats order like their bit patterns
-        atomicMax(&stats[0], __float_as_uint(a));
-        atomicMax(&stats[1], __float_as_uint(b));
+        atomicMax(&stats[0], __float_as_uint(am));
+        atomicMax(&stats[1], __float_as_uint(bm));
         if (r) atomicAdd(&stats[2], static_cast<uint32_t>(r));
     }
 }
@@ -175,14 +196,27 @@ k_index_scatter(const float *__restrict__ y, const float *__restrict__ z, const 
                 const int32_t *__restrict__ offsets, float4 *__restrict__ rec, const int32_t *__restrict__ toff,
                 int n_tf)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int b = bucket[i];
-        if (b < 0) continue;
-        const int pos = offsets[b] + rank[i];
-        // ids are local to the tracklet's timeframe
-        const int local = toff ? i - __ldg(&toff[trd::tf_of(i, toff, n_tf)]) : i;
-        rec[2 * pos] = make_float4(y[i], z[i], dy[i], __int_as_float(local));
-        rec[2 * pos + 1] = make_float4(vyy[i], vzz[i], vyz[i], 0.0f);
+    const int stride = gridDim.x * blockDim.x;
+    for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += stride * kIlp) {
+        int bk[kIlp], rk[kIlp], base[kIlp];
+#pragma unroll
+        for (int u = 0; u < kIlp; ++u) {
+            const int i = i0 + u * stride;
+            bk[u] = i < n ? __ldg(&bucket[i]) : -1;
+            rk[u] = i < n ? __ldg(&rank[i]) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < kIlp; ++u) base[u] = bk[u] >= 0 ? __ldg(&offsets[bk[u]]) : 0;
+#pragma unroll
+        for (int u = 0; u < kIlp; ++u) {
+            const int i = i0 + u * stride;
+            if (bk[u] < 0) continue;
+            const int pos = base[u] + rk[u];
+            // ids are local to the tracklet's timeframe
+            const int local = toff ? i - __ldg(&toff[trd::tf_of(i, toff, n_tf)]) : i;
+            rec[2 * pos] = make_float4(__ldg(&y[i]), __ldg(&z[i]), __ldg(&dy[i]), __int_as_float(local));
+            rec[2 * pos + 1] = make_float4(__ldg(&vyy[i]), __ldg(&vzz[i]), __ldg(&vyz[i]), 0.0f);
+        }
     }
 }
 
@@ -197,7 +231,8 @@ int index_rebuild_launch(trd_index *idx, const trd_tracklets_t *t, cudaStream_t 
     const int n = t->n;
     TRD_CUDA_TRY(cudaMemsetAsync(idx->counts, 0, sizeof(int32_t) * idx->n_buckets, s));
     TRD_CUDA_TRY(cudaMemsetAsync(idx->stats, 0, sizeof(uint32_t) * 4, s));
-    const int grid_n = n > 0 ? std::min((n + kCountThreads - 1) / kCountThreads, idx->ctx->sm_count * 8) : 0;
+    const int grid_n =
+        n > 0 ? std::min((n + kCountThreads * kIlp - 1) / (kCountThreads * kIlp), idx->ctx->sm_count * 8) : 0;
     if (n > 0) {
         k_index_count<<<grid_n, kCountThreads, 0, s>>>(t->chamber, t->y, t->z, t->dy, t->vyy, t->vzz, t->vyz, n,
                                                        idx->inv_w, idx->nb, idx->bucket, idx->rank, idx->counts,
@@ -310,7 +345,7 @@ extern "C" int trd_index_build_noalloc(const trd_tracklets_t *t, float y_bin_wid
     // scratch is fully written before it is read
     TRD_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(int32_t) * n_buckets, s));
     TRD_CUDA_TRY(cudaMemsetAsync(stats, 0, sizeof(uint32_t) * 4, s));
-    const int grid_n = n > 0 ? std::min((n + kCountThreads - 1) / kCountThreads, d.sm_count * 8) : 0;
+    const int grid_n = n > 0 ? std::min((n + kCountThreads * kIlp - 1) / (kCountThreads * kIlp), d.sm_count * 8) : 0;
     if (n > 0) {
         k_index_count<<<grid_n, kCountThreads, 0, s>>>(t->chamber, t->y, t->z, t->dy, t->vyy, t->vzz, t->vyz, n,
                                                        inv_w, nb, bucket, rank, counts, stats, nullptr, 1);
