@@ -199,9 +199,10 @@ TRD_API int trd_follow(trd_ctx_t *ctx, const trd_seeds_t *seeds, const trd_index
                const trd_params_t *params, trd_results_t *out, void *stream);
 
 /* Launch shape of the follower (the autotuner's search space).
- *   lanes_per_track   lanes that follow one seed, one hypothesis per lane:
- *                     1, 2, 4 or 8 (0 = smallest power of two >= n_hyp; 1
- *                     needs n_hyp = 1)
+ *   lanes_per_track   lanes that follow one seed, one hypothesis per lane,
+ *                     all of them sharing each hypothesis's road scan:
+ *                     1, 2, 4, 8 or 32 (a whole warp per seed, for wide roads)
+ *                     (0 = smallest power of two >= n_hyp; 1 needs n_hyp = 1)
  *   block_threads     64 or 128 (0 = 128)
  *   min_blocks_per_sm register budget: 128-thread blocks kept resident per SM
  *                     (0 = 4; 1 lane: 4, 5, 6 or 8; more lanes: 3 or 4)      */

@@ -28,7 +28,7 @@ def search_space(n_hyp: int):
         shapes += [(1, b, m) for b in (128, 64) for m in (4, 5, 6, 8)]
         shapes += [(2, 128, m) for m in (3, 4)]
     lanes = 2 if n_hyp <= 2 else (4 if n_hyp <= 4 else 8)
-    for g in sorted({lanes, min(8, 2 * lanes)}):
+    for g in sorted({lanes, min(8, 2 * lanes), 32}):
         if g >= n_hyp and g > 1 and (g, 128, 3) not in shapes:
             shapes += [(g, 128, m) for m in (3, 4)]
     return shapes

@@ -321,8 +321,11 @@ __device__ void kalman_update(TrackState &s, float tt, float ytl, float ztl, flo
 // ---- small sorted extension list (per lane) ---------------------------------
 template <int NH>
 struct ExtList {
+    // extensions kept in the selection order (score, parent rank, tracklet
+    // id; a missing layer has id kMissing and sorts after tracklets)
     float score[NH];
     float chi2[NH];
+    int par[NH];
     int id[NH];
     int pos[NH];
     __device__ __forceinline__ void clear()
@@ -331,31 +334,34 @@ struct ExtList {
         for (int k = 0; k < NH; ++k) {
             score[k] = INFINITY;
             chi2[k] = 0.0f;
+            par[k] = 0x7fffffff;
             id[k] = kMissing;
             pos[k] = -1;
         }
     }
-    __device__ __forceinline__ static bool less(float sa, int ia, float sb, int ib)
+    __device__ __forceinline__ static bool less(float sa, int pa, int ia, float sb, int pb, int ib)
     {
-        return sa < sb || (sa == sb && ia < ib);
+        return sa < sb || (sa == sb && (pa < pb || (pa == pb && ia < ib)));
     }
-    __device__ __forceinline__ void insert(float sc, int tid, int p, float c2)
+    __device__ __forceinline__ void insert(float sc, int parent, int tid, int p, float c2)
     {
-        if (!less(sc, tid, score[NH - 1], id[NH - 1])) return;
+        if (!less(sc, parent, tid, score[NH - 1], par[NH - 1], id[NH - 1])) return;
         // shift larger entries up, then place (unrolled, stays in registers)
         bool placed = false;
 #pragma unroll
         for (int k = NH - 1; k >= 0; --k) {
             if (placed) continue;
-            const bool move = k > 0 && less(sc, tid, score[k - 1], id[k - 1]);
+            const bool move = k > 0 && less(sc, parent, tid, score[k - 1], par[k - 1], id[k - 1]);
             if (move) {
                 score[k] = score[k - 1];
                 chi2[k] = chi2[k - 1];
+                par[k] = par[k - 1];
                 id[k] = id[k - 1];
                 pos[k] = pos[k - 1];
             } else {
                 score[k] = sc;
                 chi2[k] = c2;
+                par[k] = parent;
                 id[k] = tid;
                 pos[k] = p;
                 placed = true;
@@ -368,10 +374,12 @@ struct ExtList {
         for (int k = 0; k + 1 < NH; ++k) {
             score[k] = score[k + 1];
             chi2[k] = chi2[k + 1];
+            par[k] = par[k + 1];
             id[k] = id[k + 1];
             pos[k] = pos[k + 1];
         }
         score[NH - 1] = INFINITY;
+        par[NH - 1] = 0x7fffffff;
         id[NH - 1] = kMissing;
         pos[NH - 1] = -1;
     }
@@ -390,7 +398,7 @@ template <int NH>
 __device__ __forceinline__ void full_test(int pos, const IndexView &ix, float tt, float z, float yh, float yl,
                                           float n2, float syy_trk, float syz_trk, float c11, float vyy_res,
                                           int resmode, float dy_pred, float gate, float cut, float score,
-                                          ExtList<NH> &L)
+                                          int parent, ExtList<NH> &L)
 {
     const float4 a = __ldg(&ix.rec[2 * pos]);
     const float4 v = __ldg(&ix.rec[2 * pos + 1]);
@@ -404,7 +412,7 @@ __device__ __forceinline__ void full_test(int pos, const IndexView &ix, float tt
     if (fabsf(a.z - dy_pred) > gate) return;
     const float chi2 = (S11 * ry * ry - 2.0f * S01 * ry * rz + S00 * rz * rz) / (S00 * S11 - S01 * S01);
     if (!(chi2 < cut)) return;
-    L.insert(score + chi2, __float_as_int(a.w), pos, chi2);
+    L.insert(score + chi2, parent, __float_as_int(a.w), pos, chi2);
 }
 
 template <int NH>
@@ -466,7 +474,101 @@ __device__ void scan_candidates(const TrackState &s, int l, int chamber, int cba
                 const int j = j0 + u;
                 const int pos = j < n0 ? beg0 + j : beg1 + (j - n0);
                 full_test<NH>(pos, ix, tt, z, yh, yl, n2, syy_trk, syz_trk, c11, vyy_res, P.resmode, dy_pred, gate,
-                              P.cut, score, L);
+                              P.cut, score, 0, L);
+            }
+        }
+    }
+}
+
+// Group scan (N > 1): the lanes of a seed's group take its hypotheses one at
+// a time and share each one's road: the road is broadcast from the lane that
+// holds the hypothesis, lane q tests candidates q, q + G, ... (eight at a
+// time), and every extension records its parent.  The candidate set, the
+// arithmetic and the selection order are those of one lane scanning its own
+// hypothesis; the work is spread evenly over the group.
+template <int G, int NH>
+__device__ void scan_group(bool mine, const TrackState &s, int l, int chamber, int cbase, float score,
+                           const Params &P, const IndexView &ix, float vyy_max_in, float vzz_max, unsigned gmask,
+                           int q, ExtList<NH> &L)
+{
+    const float tt = layer_tilt_tan(l);
+    // this lane's own road (used when it is broadcast)
+    float z = 0, yh = 0, yl = 0, W = 0, Rz = 0, syy = 0, syz = 0, c11 = 0, vres = 0, dyp = 0, gate = 0;
+    int r_lo = 0, r_hi = 0, b_lo = 0, b_hi = -1, base_ch = 0;
+    if (mine) {
+        const float f = s.f;
+        const float r = sqrtf((1.0f - f) * (1.0f + f));
+        const float uu = f / r - lorentz_tan(P.bz);
+        vres = kSigY0 * kSigY0 + kSigY1 * kSigY1 * uu * uu;
+        const float vyy_max = P.resmode ? vres : vyy_max_in;
+        const float c10 = s.c[1];
+        c11 = s.c[2];
+        syy = s.c[0] - 2.0f * tt * c10 + tt * tt * c11;
+        syz = c10 - tt * c11;
+        W = P.road * sqrtf(fmaxf(syy + vyy_max, 0.0f)) * 1.0001f + 1e-4f;
+        Rz = P.road * sqrtf(fmaxf(c11 + vzz_max, 0.0f)) * 1.0001f + 1e-4f;
+        dyp = kDriftLength * uu;
+        gate = P.gate * sqrtf(kSigDy0 * kSigDy0 + kSigDy1 * kSigDy1 * uu * uu);
+        z = s.z;
+        yh = s.y.hi;
+        yl = s.y.lo;
+        const float zlo = stack_z_lo(stack_of_chamber(chamber));
+        r_lo = row_of_z(z - Rz, zlo);
+        r_hi = row_of_z(z + Rz, zlo);
+        const float half = W + fabsf(tt) * Rz + 1e-3f + 1e-6f * fabsf(yh);
+        b_lo = ybin_of(yh - half, ix.inv_w, ix.nb);
+        b_hi = ybin_of(yh + half, ix.inv_w, ix.nb);
+        base_ch = bucket_of(cbase + chamber, 0, 0, ix.nb);
+    }
+    const float n2 = P.road * P.road;
+    const float2 *yzs = reinterpret_cast<const float2 *>(ix.rec);
+    for (int h = 0; h < NH; ++h) {  // hypotheses live in lanes 0..NH-1
+        if (!__shfl_sync(gmask, static_cast<int>(mine), h, G)) continue;
+        const float hz = __shfl_sync(gmask, z, h, G), hyh = __shfl_sync(gmask, yh, h, G);
+        const float hyl = __shfl_sync(gmask, yl, h, G), hW = __shfl_sync(gmask, W, h, G);
+        const float hRz = __shfl_sync(gmask, Rz, h, G), hsyy = __shfl_sync(gmask, syy, h, G);
+        const float hsyz = __shfl_sync(gmask, syz, h, G), hc11 = __shfl_sync(gmask, c11, h, G);
+        const float hvres = __shfl_sync(gmask, vres, h, G), hdyp = __shfl_sync(gmask, dyp, h, G);
+        const float hgate = __shfl_sync(gmask, gate, h, G), hscore = __shfl_sync(gmask, score, h, G);
+        const int hr_lo = __shfl_sync(gmask, r_lo, h, G), hr_hi = __shfl_sync(gmask, r_hi, h, G);
+        const int hb_lo = __shfl_sync(gmask, b_lo, h, G), hb_hi = __shfl_sync(gmask, b_hi, h, G);
+        const int hbase = __shfl_sync(gmask, base_ch, h, G);
+        for (int b = hb_lo; b <= hb_hi; b += 2) {
+            const int base = hbase + b * kRowsPerStack;
+            const int beg0 = __ldg(&ix.offsets[base + hr_lo]);
+            const int end0 = __ldg(&ix.offsets[base + hr_hi + 1]);
+            int beg1 = 0, end1 = 0;
+            if (b + 1 <= hb_hi) {
+                beg1 = __ldg(&ix.offsets[base + kRowsPerStack + hr_lo]);
+                end1 = __ldg(&ix.offsets[base + kRowsPerStack + hr_hi + 1]);
+            }
+            const int n0 = end0 - beg0;
+            const int n = n0 + (end1 - beg1);
+            // lane q takes candidates q, q + G, ...: ceil(n / G) of them, four at a time
+            const int per_lane = (n + G - 1) / G;
+            for (int u0 = 0; u0 < per_lane; u0 += 4) {
+                float2 c[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int j = q + G * (u0 + u);
+                    const int pos = j < n0 ? beg0 + j : beg1 + (j - n0);
+                    c[u] = j < n ? __ldg(&yzs[4 * pos]) : make_float2(INFINITY, INFINITY);
+                }
+                unsigned mask = 0;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float ry = (__fsub_rn(c[u].x, hyh) - hyl) + tt * (hz - c[u].y);
+                    const float rz = c[u].y - hz;
+                    if (fabsf(ry) <= hW && fabsf(rz) <= hRz) mask |= 1u << u;
+                }
+                while (mask) {
+                    const int u = __ffs(mask) - 1;
+                    mask &= mask - 1u;
+                    const int j = q + G * (u0 + u);
+                    const int pos = j < n0 ? beg0 + j : beg1 + (j - n0);
+                    full_test<NH>(pos, ix, tt, hz, hyh, hyl, n2, hsyy, hsyz, hc11, hvres, P.resmode, hdyp, hgate,
+                                  P.cut, hscore, h, L);
+                }
             }
         }
     }
@@ -704,8 +806,13 @@ __device__ __forceinline__ bool layer_step(int i, int l, int q, unsigned gmask, 
     const bool live = H.alive && to_layer(s, l, P, chamber);
     ExtList<NH> L;
     L.clear();
-    if (live && chamber >= 0) scan_candidates<NH>(s, l, chamber, H.cbase, H.score, P, ix, vyy_max, vzz_max, L);
-    if (live && H.nmiss < P.maxmiss) L.insert(H.score + P.pmiss, kMissing, -1, 0.0f);
+    if (G == 1) {
+        if (live && chamber >= 0) scan_candidates<NH>(s, l, chamber, H.cbase, H.score, P, ix, vyy_max, vzz_max, L);
+    } else {
+        scan_group<G, NH>(live && chamber >= 0, s, l, chamber, H.cbase, H.score, P, ix, vyy_max, vzz_max, gmask, q,
+                          L);
+    }
+    if (live && H.nmiss < P.maxmiss) L.insert(H.score + P.pmiss, q, kMissing, -1, 0.0f);
 
     // merge the lanes' lists: the k-th best extension goes to lane k
     int my_parent = q, my_id = kMissing, my_pos = -1;
@@ -721,31 +828,34 @@ __device__ __forceinline__ bool layer_step(int i, int l, int q, unsigned gmask, 
         }
     } else {
         for (int rr = 0; rr < P.nhyp; ++rr) {
+            // group minimum of the lanes' heads in (score, parent, id) order;
+            // bh is the lane holding it
             float bs = L.score[0];
-            int bq = q, bid = L.id[0];
+            int bp = L.par[0], bid = L.id[0], bh = q;
 #pragma unroll
             for (int off = G / 2; off > 0; off >>= 1) {
                 const float os = __shfl_xor_sync(gmask, bs, off, G);
-                const int oq = __shfl_xor_sync(gmask, bq, off, G);
+                const int op = __shfl_xor_sync(gmask, bp, off, G);
                 const int oid = __shfl_xor_sync(gmask, bid, off, G);
-                const bool take = os < bs || (os == bs && (oq < bq || (oq == bq && oid < bid)));
-                if (take) {
+                const int oh = __shfl_xor_sync(gmask, bh, off, G);
+                if (ExtList<NH>::less(os, op, oid, bs, bp, bid)) {
                     bs = os;
-                    bq = oq;
+                    bp = op;
                     bid = oid;
+                    bh = oh;
                 }
             }
             if (!(bs < INFINITY)) break;
-            const float wchi2 = __shfl_sync(gmask, L.chi2[0], bq, G);
-            const int wpos = __shfl_sync(gmask, L.pos[0], bq, G);
+            const float wchi2 = __shfl_sync(gmask, L.chi2[0], bh, G);
+            const int wpos = __shfl_sync(gmask, L.pos[0], bh, G);
             if (q == rr) {
-                my_parent = bq;
+                my_parent = bp;
                 my_id = bid;
                 my_pos = wpos;
                 my_score = bs;
                 my_chi2 = wchi2;
             }
-            if (q == bq) L.pop();
+            if (q == bh) L.pop();
             kept = rr + 1;
         }
     }
@@ -891,6 +1001,8 @@ int follow_launch(const trd_ctx *ctx, const trd_seeds_t *seeds, const IndexView 
     case 4 * 16 + 4: return launch<4, 4, 4>(ctx, sv, iv, P, o, s, block, counter);
     case 8 * 16 + 3: return launch<8, 8, 3>(ctx, sv, iv, P, o, s, block, counter);
     case 8 * 16 + 4: return launch<8, 8, 4>(ctx, sv, iv, P, o, s, block, counter);
+    case 32 * 16 + 3: return launch<32, 8, 3>(ctx, sv, iv, P, o, s, block, counter);
+    case 32 * 16 + 4: return launch<32, 8, 4>(ctx, sv, iv, P, o, s, block, counter);
     default: return TRD_EINVAL;
     }
 }

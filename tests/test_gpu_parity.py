@@ -215,3 +215,19 @@ def test_full_calibration_sampled_parity(ctx):
     sel = np.arange(0, tf.n_seeds, 1500)
     o = O.follow(tf.seeds, tf.tracklets, tf.params, seed_index=sel)
     compare(g, o, sel=sel)
+
+
+def test_lane_groups_do_not_change_multi_hypothesis_results(ctx):
+    """N = 6 with 8 lanes per seed (four seeds per warp) and with a whole warp
+    per seed: the same candidates, arithmetic and order, so identical results."""
+    from paper_2003_03174_b300 import trd
+    tf = make_workload("calibration", seed=9, n_seeds=4000)
+    s, t = trd.to_device(tf.seeds), trd.to_device(tf.tracklets)
+    idx = ctx.index_build(t)
+    outs = []
+    for lanes, mb in ((8, 3), (32, 3), (32, 4), (8, 4)):
+        outs.append(to_numpy(ctx.follow(s, idx, tf.params, lanes_per_track=lanes, min_blocks_per_sm=mb)))
+    torch.cuda.synchronize()
+    for o in outs[1:]:
+        for k in outs[0]:
+            np.testing.assert_array_equal(o[k], outs[0][k], err_msg=k)
