@@ -49,10 +49,11 @@ FOLLOW_BYTES_PER_SEED = SEED_BYTES + RESULT_BYTES + RECORD_BYTES * IN_ROAD_PER_S
 # layers; six layers.
 FOLLOW_FLOPS_PER_SEED = 3700
 L2_FLUSH_BYTES = 512 << 20
-# DRAM bytes (read + write) of one k_follow launch on this workload from one
-# ncu capture (profiles/kernels_timeframe.md), valid only for the kernel source
-# it was measured on: reported as null once follow.cu or trd_device.cuh change.
-FOLLOW_TRAFFIC = {"source_sha256_16": "432ed8e557f77c76", "bytes": 67.278336e6}
+# DRAM bytes (read + write) of one trd_follow call (k_seed_prepare 17.6 MB +
+# k_follow 56.8 MB) on this workload from one ncu capture of each kernel, valid
+# only for the kernel source it was measured on: reported as null once
+# follow.cu or trd_device.cuh change.
+FOLLOW_TRAFFIC = {"source_sha256_16": "2a6233ea955bd7c3", "bytes": 74.37e6}
 
 
 def _follow_source_hash():
@@ -330,7 +331,7 @@ def run_ours(args):
     hbm = peaks.get("hbm_gbs")
     follow_avg_s = statistics.mean(follow_ms) / 1e3
     achieved = n * FOLLOW_BYTES_PER_SEED / follow_avg_s / 1e9
-    roof = {"bound": "hbm", "kernel": "k_follow", "achieved": achieved,
+    roof = {"bound": "hbm", "kernel": "trd_follow (k_seed_prepare + k_follow)", "achieved": achieved,
             "peak": hbm if hbm else 6400.0, "unit": "GB/s",
             "peak_source": "measured" if hbm else "fallback",
             "frac": achieved / (hbm if hbm else 6400.0),
@@ -452,7 +453,7 @@ def run_batched(args):
                   "path": f"{len(tfs)} x (trd_index_rebuild + trd_follow) on one stream"},
         "speedup_batched_vs_plain": t_plain / t_batch,
         "results_identical": bool(same),
-        "gpu_launches_per_step": {"batched": 6, "plain": 6 * len(tfs)},
+        "gpu_launches_per_step": {"batched": 7, "plain": 7 * len(tfs)},
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
