@@ -221,7 +221,8 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     ctx = trd.Context(local)
 
-    tf = make_workload(WORKLOAD, seed=rank_workload_seed(rank))  # each rank: its own timeframe
+    tf = make_workload(WORKLOAD, seed=rank_workload_seed(rank),  # each rank: its own timeframe
+                       n_interactions=args.association)
     seeds = trd.to_device(tf.seeds, dev)
     trk = trd.to_device(tf.tracklets, dev)
     n = tf.n_seeds
@@ -359,6 +360,7 @@ def run_ours(args):
             "config": {"workload": f"{WORKLOAD}: {n} seeds, {tf.n_tracklets} tracklets per rank, "
                                    f"N=1, 3-sigma road, chi2<15, <=2 missing",
                        "seeds_per_rank": n, "tracklets_per_rank": tf.n_tracklets,
+                       "interactions": args.association or None,
                        "matched_per_rank_step": matched, "l2": "flushed (512 MB write) between steps",
                        "index_y_bin_cm": bin_width or 2.0, "launch": shape,
                        "autotuned": tuned is not None,
@@ -611,6 +613,8 @@ def main():
     ap.add_argument("--no-graph", action="store_true", help="time separate launches instead of the graph")
     ap.add_argument("--workload", choices=["timeframe", "batched", "served"], default="timeframe")
     ap.add_argument("--n-tf", type=int, default=64)
+    ap.add_argument("--association", type=int, default=0,
+                    help="interactions per timeframe (per-interaction association); 0 = off")
     ap.add_argument("--n-payloads", type=int, default=16)
     ap.add_argument("--requests", type=int, default=64)
     ap.add_argument("--slots", type=int, default=4)

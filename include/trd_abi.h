@@ -66,11 +66,16 @@ typedef struct trd_batch trd_batch_t;
 typedef struct trd_server trd_server_t;
 
 /* Seeds: ITS-TPC tracks extrapolated towards the TRD (Sec. 3), in any frame
- * alpha.  Device pointers, each n floats; cov is [15][n].  Read only.      */
+ * alpha.  Device pointers, each n floats; cov is [15][n].  Read only.
+ * trigger (optional, may be NULL): int32 interaction id of each seed (its
+ * bunch crossing); when both a seed and a tracklet carry an id >= 0, the
+ * tracklet is a candidate only if the ids are equal (Sec. 4: only tracklets
+ * of the track's own interaction are considered).                           */
 typedef struct {
     const float *alpha, *x, *y, *z, *snp, *tgl, *q2pt;
     const float *cov;
     int32_t n;
+    const int32_t *trigger;
 } trd_seeds_t;
 
 /* Tracklets: the FEE straight-line fits of Sec. 3 (local y at the chamber's
@@ -83,6 +88,7 @@ typedef struct {
     const int32_t *chamber;
     const float *y, *z, *dy, *vyy, *vzz, *vyz;
     int32_t n;
+    const int32_t *trigger; /* optional interaction id per tracklet (see trd_seeds_t) */
 } trd_tracklets_t;
 
 /* Follower parameters.
@@ -164,7 +170,8 @@ TRD_API int trd_index_copy_out(const trd_index_t *index, int32_t *offsets, int32
  *   offsets  n_buckets + 1 int32, n_buckets = 540 * 18 * ceil(132 / w)
  *            (bucket = (chamber * n_ybins + y bin) * 18 + pad row)
  *   records  8 floats per tracklet (16-byte aligned): {y, z, dy, input index
- *            as int32 bits}, {vyy, vzz, vyz, 0}, in bucket order; the first
+ *            as int32 bits}, {vyy, vzz, vyz, trigger as int32 bits (-1 when
+ *            the tracklets carry none)}, in bucket order; the first
  *            offsets[n_buckets] records are written
  *   stats    4 uint32: largest vyy and vzz (float bits), rejected count, 0
  * Its scratch is a fixed device array inside the library (about 13.5 MB on

@@ -173,6 +173,9 @@ def follow(seeds: dict, tracklets: dict, params: dict, seed_index=None, brute=Fa
         sidx.ctypes.data_as(C.c_void_p) if sidx is not None else None, C.c_int(int(brute)),
         C.c_int(n_threads)] + [a.ctypes.data_as(C.c_void_p) for a in
                                (st, cv, chi2_, ntrk, nmiss, status, ids, margin, nroad)]
+    trig = [np.ascontiguousarray(np.asarray(d["trigger"], dtype=np.int32)) if d.get("trigger") is not None
+            else None for d in (seeds, tracklets)]
+    args += [t.ctypes.data_as(C.c_void_p) if t is not None else None for t in trig]
     rc = L.ora_follow(*args)
     if rc != 0:
         raise ValueError(f"ora_follow rejected its arguments ({rc})")

@@ -407,6 +407,7 @@ typedef struct {
     const int *start; /* chamber buckets: start[ORA_NCHAMBER + 1] */
     const int *list;
     int brute;        /* 1: scan every tracklet of the input and test its chamber id */
+    const int *trig;  /* interaction id per tracklet, or NULL */
 } ora_tracklets_t;
 
 static int cmp_ext(const void *pa, const void *pb)
@@ -525,8 +526,15 @@ typedef struct {
 
 enum { ORA_ST_PROP_FAIL = 1, ORA_ST_STOPPED = 2, ORA_ST_SEED_INVALID = 4 };
 
-static void follow_one(const double seed_st[7], const double seed_c[15], const ora_tracklets_t *T,
-                       const ora_params_t *P, ora_scratch_t *S, ora_result_t *R)
+/* Sec. 4: in time frames, only tracklets of the track's own interaction are
+ * considered.  An id < 0 on either side means no association.             */
+static int same_interaction(int seed_trig, const ora_tracklets_t *T, int j)
+{
+    return seed_trig < 0 || !T->trig || T->trig[j] < 0 || T->trig[j] == seed_trig;
+}
+
+static void follow_one(const double seed_st[7], const double seed_c[15], int seed_trig,
+                       const ora_tracklets_t *T, const ora_params_t *P, ora_scratch_t *S, ora_result_t *R)
 {
     memset(R, 0, sizeof *R);
     for (int l = 0; l < ORA_NLAYER; ++l) { R->ids[l] = -1; R->margin[l] = INFINITY; }
@@ -575,6 +583,7 @@ static void follow_one(const double seed_st[7], const double seed_c[15], const o
                 for (int q = lo; q < up; ++q) {
                     const int j = T->brute ? q : T->list[q];
                     if (T->brute && T->ch[j] != chamber) continue;
+                    if (!same_interaction(seed_trig, T, j)) continue;
                     double chi2, slack;
                     int in_road;
                     const int acc = test_tracklet(&work[hi], l, T, j, P, &chi2, &slack, &in_road);
@@ -652,7 +661,7 @@ int ora_candidates(const double st[7], const double c[15], int l, int chamber, i
                    const int *pi, int max_out, int *ids_out, double *chi2_out)
 {
     ora_params_t P = {pd[0], pd[1], pd[2], pd[3], pd[4], pi[0], pi[1], pi[2], pi[3]};
-    ora_tracklets_t T = {n_trk, t_ch, t_y, t_z, t_dy, t_vyy, t_vzz, t_vyz, NULL, NULL, 1};
+    ora_tracklets_t T = {n_trk, t_ch, t_y, t_z, t_dy, t_vyy, t_vzz, t_vyz, NULL, NULL, 1, NULL};
     ora_hyp_t h;
     memset(&h, 0, sizeof h);
     memcpy(h.st, st, sizeof h.st);
@@ -678,6 +687,7 @@ int ora_candidates(const double st[7], const double c[15], int l, int chamber, i
  *   margin_out[6][n] (smallest decision slack per layer), nroad_out[6][n]
  * pd = {bz, n_sigma_road, chi2_cut, p_miss, dy_gate_sigma}
  * pi = {n_hyp, max_missing, res_mode, material_on}
+ * seed_trig, t_trig (optional): interaction ids (Sec. 4 association).
  * Returns 0, or -1 on invalid arguments.                                    */
 int ora_follow(int n_seeds, const float *alpha, const float *x, const float *y, const float *z,
                const float *snp, const float *tgl, const float *q2pt, const float *cov,
@@ -685,7 +695,8 @@ int ora_follow(int n_seeds, const float *alpha, const float *x, const float *y, 
                const float *t_vyy, const float *t_vzz, const float *t_vyz,
                const double *pd, const int *pi, int n_out, const int *seed_index, int brute,
                int n_threads, double *st_out, double *cov_out, double *chi2_out, int *ntrk_out,
-               int *nmiss_out, int *status_out, int *ids_out, double *margin_out, int *nroad_out)
+               int *nmiss_out, int *status_out, int *ids_out, double *margin_out, int *nroad_out,
+               const int *seed_trig, const int *t_trig)
 {
     if (n_seeds < 0 || n_trk < 0 || n_out < 0) return -1;
     ora_params_t P = {pd[0], pd[1], pd[2], pd[3], pd[4], pi[0], pi[1], pi[2], pi[3]};
@@ -704,7 +715,7 @@ int ora_follow(int n_seeds, const float *alpha, const float *x, const float *y, 
             if (t_ch[j] >= 0 && t_ch[j] < ORA_NCHAMBER) list[fill[t_ch[j]]++] = j;
         free(fill);
     }
-    ora_tracklets_t T = {n_trk, t_ch, t_y, t_z, t_dy, t_vyy, t_vzz, t_vyz, start, list, brute};
+    ora_tracklets_t T = {n_trk, t_ch, t_y, t_z, t_dy, t_vyy, t_vzz, t_vyz, start, list, brute, t_trig};
 
 #ifdef _OPENMP
     if (n_threads > 0) omp_set_num_threads(n_threads);
@@ -727,7 +738,7 @@ int ora_follow(int n_seeds, const float *alpha, const float *x, const float *y, 
                 double s7[7] = {alpha[i], x[i], y[i], z[i], snp[i], tgl[i], q2pt[i]};
                 double c15[15];
                 for (int k = 0; k < 15; ++k) c15[k] = cov[(size_t)k * n_seeds + i];
-                follow_one(s7, c15, &T, &P, &S, &R);
+                follow_one(s7, c15, seed_trig ? seed_trig[i] : -1, &T, &P, &S, &R);
             }
             for (int k = 0; k < 7; ++k) st_out[(size_t)k * n_out + o] = R.st[k];
             for (int k = 0; k < 15; ++k) cov_out[(size_t)k * n_out + o] = R.c[k];

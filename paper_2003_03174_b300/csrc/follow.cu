@@ -29,6 +29,7 @@ struct SeedsView {
     int n;
     const int32_t *soff;  // [n_tf + 1] seed offsets of a batch of timeframes, or null
     int n_tf;
+    const int32_t *trig;  // interaction id per seed, or null
 };
 
 struct ResultsView {
@@ -398,10 +399,13 @@ template <int NH>
 __device__ __forceinline__ void full_test(int pos, const IndexView &ix, float tt, float z, float yh, float yl,
                                           float n2, float syy_trk, float syz_trk, float c11, float vyy_res,
                                           int resmode, float dy_pred, float gate, float cut, float score,
-                                          int parent, ExtList<NH> &L)
+                                          int parent, int trig, ExtList<NH> &L)
 {
     const float4 a = __ldg(&ix.rec[2 * pos]);
     const float4 v = __ldg(&ix.rec[2 * pos + 1]);
+    // per-interaction association (Sec. 4): other interactions' tracklets are not candidates
+    const int ttrig = __float_as_int(v.w);
+    if (trig >= 0 && ttrig >= 0 && ttrig != trig) return;
     const float ry = (__fsub_rn(a.x, yh) - yl) + tt * (z - a.y);
     const float rz = a.y - z;
     const float vyy = resmode ? vyy_res : v.x;
@@ -417,7 +421,7 @@ __device__ __forceinline__ void full_test(int pos, const IndexView &ix, float tt
 
 template <int NH>
 __device__ void scan_candidates(const TrackState &s, int l, int chamber, int cbase, float score, const Params &P,
-                                const IndexView &ix, float vyy_max_in, float vzz_max, ExtList<NH> &L)
+                                const IndexView &ix, float vyy_max_in, float vzz_max, int trig, ExtList<NH> &L)
 {
     const float tt = layer_tilt_tan(l);
     const float f = s.f;
@@ -474,7 +478,7 @@ __device__ void scan_candidates(const TrackState &s, int l, int chamber, int cba
                 const int j = j0 + u;
                 const int pos = j < n0 ? beg0 + j : beg1 + (j - n0);
                 full_test<NH>(pos, ix, tt, z, yh, yl, n2, syy_trk, syz_trk, c11, vyy_res, P.resmode, dy_pred, gate,
-                              P.cut, score, 0, L);
+                              P.cut, score, 0, trig, L);
             }
         }
     }
@@ -489,7 +493,7 @@ __device__ void scan_candidates(const TrackState &s, int l, int chamber, int cba
 template <int G, int NH>
 __device__ void scan_group(bool mine, const TrackState &s, int l, int chamber, int cbase, float score,
                            const Params &P, const IndexView &ix, float vyy_max_in, float vzz_max, unsigned gmask,
-                           int q, ExtList<NH> &L)
+                           int q, int trig, ExtList<NH> &L)
 {
     const float tt = layer_tilt_tan(l);
     // this lane's own road (used when it is broadcast)
@@ -567,7 +571,7 @@ __device__ void scan_group(bool mine, const TrackState &s, int l, int chamber, i
                     const int j = q + G * (u0 + u);
                     const int pos = j < n0 ? beg0 + j : beg1 + (j - n0);
                     full_test<NH>(pos, ix, tt, hz, hyh, hyl, n2, hsyy, hsyz, hc11, hvres, P.resmode, hdyp, hgate,
-                                  P.cut, hscore, h, L);
+                                  P.cut, hscore, h, trig, L);
                 }
             }
         }
@@ -708,6 +712,7 @@ struct Lane {
     float score, chisum;
     int ntrk, nmiss;
     int cbase;  // first chamber of the seed's timeframe in the index (timeframe * 540)
+    int trig;   // the seed's interaction id (-1: no association)
     int ids[kLayers];
     bool alive;
 };
@@ -783,6 +788,7 @@ __device__ __forceinline__ bool start_seed(int i, int q, const SeedsView &sv, co
 #pragma unroll
     for (int k = 0; k < 15; ++k) s.c[k] = o.cov[k * n + i];
     L.cbase = tf_of(i, sv.soff, sv.n_tf) * kChambers;
+    L.trig = sv.trig ? sv.trig[i] : -1;
     L.alive = q == 0;
     L.score = 0.0f;
     L.chisum = 0.0f;
@@ -807,10 +813,11 @@ __device__ __forceinline__ bool layer_step(int i, int l, int q, unsigned gmask, 
     ExtList<NH> L;
     L.clear();
     if (G == 1) {
-        if (live && chamber >= 0) scan_candidates<NH>(s, l, chamber, H.cbase, H.score, P, ix, vyy_max, vzz_max, L);
+        if (live && chamber >= 0)
+            scan_candidates<NH>(s, l, chamber, H.cbase, H.score, P, ix, vyy_max, vzz_max, H.trig, L);
     } else {
         scan_group<G, NH>(live && chamber >= 0, s, l, chamber, H.cbase, H.score, P, ix, vyy_max, vzz_max, gmask, q,
-                          L);
+                          H.trig, L);
     }
     if (live && H.nmiss < P.maxmiss) L.insert(H.score + P.pmiss, q, kMissing, -1, 0.0f);
 
@@ -980,7 +987,7 @@ int follow_launch(const trd_ctx *ctx, const trd_seeds_t *seeds, const IndexView 
                   int *counter, const int32_t *seed_offsets, int n_tf)
 {
     SeedsView sv{seeds->alpha, seeds->x, seeds->y, seeds->z, seeds->snp, seeds->tgl, seeds->q2pt, seeds->cov,
-                 seeds->n, seed_offsets, n_tf};
+                 seeds->n, seed_offsets, n_tf, seeds->trigger};
     Params P{p->bz, p->n_sigma_road, p->chi2_cut, p->p_miss, p->dy_gate_sigma, p->n_hyp, p->max_missing,
              p->res_mode, p->material_on};
     ResultsView o{out->alpha, out->x, out->par, out->cov, out->chi2, out->n_trk, out->n_miss, out->status,

@@ -194,7 +194,7 @@ k_index_scatter(const float *__restrict__ y, const float *__restrict__ z, const 
                 const float *__restrict__ vyy, const float *__restrict__ vzz, const float *__restrict__ vyz,
                 int n, const int32_t *__restrict__ bucket, const int32_t *__restrict__ rank,
                 const int32_t *__restrict__ offsets, float4 *__restrict__ rec, const int32_t *__restrict__ toff,
-                int n_tf)
+                int n_tf, const int32_t *__restrict__ trig)
 {
     const int stride = gridDim.x * blockDim.x;
     for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += stride * kIlp) {
@@ -215,7 +215,8 @@ k_index_scatter(const float *__restrict__ y, const float *__restrict__ z, const 
             // ids are local to the tracklet's timeframe
             const int local = toff ? i - __ldg(&toff[trd::tf_of(i, toff, n_tf)]) : i;
             rec[2 * pos] = make_float4(__ldg(&y[i]), __ldg(&z[i]), __ldg(&dy[i]), __int_as_float(local));
-            rec[2 * pos + 1] = make_float4(__ldg(&vyy[i]), __ldg(&vzz[i]), __ldg(&vyz[i]), 0.0f);
+            rec[2 * pos + 1] = make_float4(__ldg(&vyy[i]), __ldg(&vzz[i]), __ldg(&vyz[i]),
+                                           __int_as_float(trig ? __ldg(&trig[i]) : -1));
         }
     }
 }
@@ -248,7 +249,8 @@ int index_rebuild_launch(trd_index *idx, const trd_tracklets_t *t, cudaStream_t 
     TRD_CUDA_TRY(cudaGetLastError());
     if (n > 0) {
         k_index_scatter<<<grid_n, kCountThreads, 0, s>>>(t->y, t->z, t->dy, t->vyy, t->vzz, t->vyz, n, idx->bucket,
-                                                         idx->rank, idx->offsets, idx->rec, idx->toff, idx->n_tf);
+                                                         idx->rank, idx->offsets, idx->rec, idx->toff, idx->n_tf,
+                                                         t->trigger);
         TRD_CUDA_TRY(cudaGetLastError());
     }
     return TRD_OK;
@@ -359,7 +361,7 @@ extern "C" int trd_index_build_noalloc(const trd_tracklets_t *t, float y_bin_wid
     TRD_CUDA_TRY(cudaGetLastError());
     if (n > 0) {
         k_index_scatter<<<grid_n, kCountThreads, 0, s>>>(t->y, t->z, t->dy, t->vyy, t->vzz, t->vyz, n, bucket, rank,
-                                                         offsets, rec, nullptr, 1);
+                                                         offsets, rec, nullptr, 1, t->trigger);
         TRD_CUDA_TRY(cudaGetLastError());
     }
     return TRD_OK;

@@ -65,7 +65,9 @@ size_t io_bytes(int n_seeds, int n_trk)
     return align_up(sizeof(float) * 22 * static_cast<size_t>(n_seeds)) +   // seeds
            align_up(sizeof(float) * 23 * static_cast<size_t>(n_seeds)) +   // float results
            align_up(sizeof(int32_t) * 9 * static_cast<size_t>(n_seeds)) +  // int results
-           align_up(28 * static_cast<size_t>(n_trk));                      // tracklets
+           align_up(28 * static_cast<size_t>(n_trk)) +                     // tracklets
+           align_up(sizeof(int32_t) * static_cast<size_t>(n_seeds)) +      // seed interaction ids
+           align_up(sizeof(int32_t) * static_cast<size_t>(n_trk));         // tracklet interaction ids
 }
 
 // bytes of an index for n_trk tracklets (records + build scratch + buckets)
@@ -119,6 +121,10 @@ int start_request(trd_server *S, Slot &slot, Request *r)
     int32_t *di = reinterpret_cast<int32_t *>(p);
     p += align_up(sizeof(int32_t) * 9 * static_cast<size_t>(n));
     char *dt = p;
+    p += align_up(28 * static_cast<size_t>(m));
+    int32_t *dtrig_s = reinterpret_cast<int32_t *>(p);
+    p += align_up(sizeof(int32_t) * static_cast<size_t>(n));
+    int32_t *dtrig_t = reinterpret_cast<int32_t *>(p);
     // seeds: alpha x y z snp tgl q2pt cov[15] (22 rows of n)
     const float *hs[7] = {r->seeds.alpha, r->seeds.x, r->seeds.y, r->seeds.z, r->seeds.snp, r->seeds.tgl,
                           r->seeds.q2pt};
@@ -128,9 +134,14 @@ int start_request(trd_server *S, Slot &slot, Request *r)
                                             cudaMemcpyHostToDevice, st));
     if (n) TRD_CUDA_TRY(cudaMemcpyAsync(ds + 7 * static_cast<size_t>(n), r->seeds.cov, sizeof(float) * 15 * n,
                                         cudaMemcpyHostToDevice, st));
+    if (n && r->seeds.trigger)
+        TRD_CUDA_TRY(cudaMemcpyAsync(dtrig_s, r->seeds.trigger, sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
+    if (m && r->trk.trigger)
+        TRD_CUDA_TRY(cudaMemcpyAsync(dtrig_t, r->trk.trigger, sizeof(int32_t) * m, cudaMemcpyHostToDevice, st));
     trd_seeds_t dseeds{ds, ds + n, ds + 2 * static_cast<size_t>(n), ds + 3 * static_cast<size_t>(n),
                        ds + 4 * static_cast<size_t>(n), ds + 5 * static_cast<size_t>(n),
-                       ds + 6 * static_cast<size_t>(n), ds + 7 * static_cast<size_t>(n), n};
+                       ds + 6 * static_cast<size_t>(n), ds + 7 * static_cast<size_t>(n), n,
+                       r->seeds.trigger ? dtrig_s : nullptr};
     int32_t *dch = reinterpret_cast<int32_t *>(dt);
     float *dtf = reinterpret_cast<float *>(dt) + m;
     if (m) TRD_CUDA_TRY(cudaMemcpyAsync(dch, r->trk.chamber, sizeof(int32_t) * m, cudaMemcpyHostToDevice, st));
@@ -139,7 +150,8 @@ int start_request(trd_server *S, Slot &slot, Request *r)
         if (m) TRD_CUDA_TRY(cudaMemcpyAsync(dtf + static_cast<size_t>(k) * m, ht[k], sizeof(float) * m,
                                             cudaMemcpyHostToDevice, st));
     trd_tracklets_t dtrk{dch, dtf, dtf + m, dtf + 2 * static_cast<size_t>(m), dtf + 3 * static_cast<size_t>(m),
-                         dtf + 4 * static_cast<size_t>(m), dtf + 5 * static_cast<size_t>(m), m};
+                         dtf + 4 * static_cast<size_t>(m), dtf + 5 * static_cast<size_t>(m), m,
+                         r->trk.trigger ? dtrig_t : nullptr};
     trd_results_t dres{dr, dr + n, dr + 2 * static_cast<size_t>(n), dr + 7 * static_cast<size_t>(n),
                        dr + 22 * static_cast<size_t>(n), di, di + n, di + 2 * static_cast<size_t>(n),
                        di + 3 * static_cast<size_t>(n)};

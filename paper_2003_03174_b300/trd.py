@@ -35,12 +35,12 @@ class TrdError(RuntimeError):
 
 class Seeds(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in ("alpha", "x", "y", "z", "snp", "tgl", "q2pt", "cov")] + [
-        ("n", C.c_int32)]
+        ("n", C.c_int32), ("trigger", C.c_void_p)]
 
 
 class Tracklets(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in ("chamber", "y", "z", "dy", "vyy", "vzz", "vyz")] + [
-        ("n", C.c_int32)]
+        ("n", C.c_int32), ("trigger", C.c_void_p)]
 
 
 class Params(C.Structure):
@@ -153,12 +153,14 @@ def params_struct(p: dict) -> Params:
 
 def seeds_struct(s: dict) -> Seeds:
     n = int(s["alpha"].shape[0])
-    return Seeds(*[_ptr(s[k]) for k in ("alpha", "x", "y", "z", "snp", "tgl", "q2pt", "cov")], n)
+    return Seeds(*[_ptr(s[k]) for k in ("alpha", "x", "y", "z", "snp", "tgl", "q2pt", "cov")], n,
+                 _ptr(s.get("trigger")))
 
 
 def tracklets_struct(t: dict) -> Tracklets:
     n = int(t["chamber"].shape[0])
-    return Tracklets(*[_ptr(t[k]) for k in ("chamber", "y", "z", "dy", "vyy", "vzz", "vyz")], n)
+    return Tracklets(*[_ptr(t[k]) for k in ("chamber", "y", "z", "dy", "vyy", "vzz", "vyz")], n,
+                     _ptr(t.get("trigger")))
 
 
 def alloc_results(n: int, device="cuda"):
@@ -266,8 +268,10 @@ class Server:
     def submit(self, seeds: dict, tracklets: dict, results: dict) -> int:
         n = int(seeds["alpha"].shape[0])
         m = int(tracklets["chamber"].shape[0])
-        ss = Seeds(*[_hptr(seeds[k]) for k in ("alpha", "x", "y", "z", "snp", "tgl", "q2pt", "cov")], n)
-        ts = Tracklets(*[_hptr(tracklets[k]) for k in ("chamber", "y", "z", "dy", "vyy", "vzz", "vyz")], m)
+        ss = Seeds(*[_hptr(seeds[k]) for k in ("alpha", "x", "y", "z", "snp", "tgl", "q2pt", "cov")], n,
+                   _hptr(seeds["trigger"]) if seeds.get("trigger") is not None else None)
+        ts = Tracklets(*[_hptr(tracklets[k]) for k in ("chamber", "y", "z", "dy", "vyy", "vzz", "vyz")], m,
+                       _hptr(tracklets["trigger"]) if tracklets.get("trigger") is not None else None)
         rs = Results(*[_hptr(results[k]) for k in ("alpha", "x", "par", "cov", "chi2", "n_trk",
                                                    "n_miss", "status", "tracklet_id")])
         t = C.c_uint64()

@@ -177,7 +177,7 @@ def make_timeframe(n_seeds: int, seed: int = 0, noise: float = 0.2, bz: float = 
                    eff: float = 0.9, smear: bool = True, snap_z: bool = True,
                    distortion: bool = False, sys_y: float = 0.0,
                    off_centre_frac: float = 0.1, name: str = "custom",
-                   params: dict | None = None) -> Timeframe:
+                   params: dict | None = None, n_interactions: int = 0) -> Timeframe:
     """Draw one timeframe.
 
     Truth: |eta| < 0.9, uniform phi, q = +-1, pT exponential with mean 0.6
@@ -187,7 +187,10 @@ def make_timeframe(n_seeds: int, seed: int = 0, noise: float = 0.2, bz: float = 
     at x = 290 cm smeared by the diagonal covariance (0.1 cm, 0.1 cm, 1e-3,
     1e-3, 1 % of q/pT).  With `distortion`, seeds get a coherent y offset of
     1-5 cm (smooth in radius and azimuth) and `sys_y` is added in quadrature
-    to their y error.
+    to their y error.  With n_interactions > 0, every track belongs to one of
+    that many interactions (uniform), its seed and tracklets carry the id
+    ("trigger"), and noise tracklets get a uniform random id (drawn from a
+    separate stream, so the rest of the timeframe is unchanged).
     """
     rng = np.random.Generator(np.random.Philox(key=seed))
     n_draw = int(n_seeds * 1.5) + 256
@@ -265,6 +268,13 @@ def make_timeframe(n_seeds: int, seed: int = 0, noise: float = 0.2, bz: float = 
         owner = np.concatenate([owner, np.full(n_noise, -1)])
         tlayer = np.concatenate([tlayer, nlayer])
     m = ch.shape[0]
+    trig_trk = trig_seed = None
+    if n_interactions > 0:
+        irng = np.random.Generator(np.random.Philox(key=seed + 7_777_777))
+        inter = irng.integers(0, n_interactions, n)
+        trig_seed = inter.astype(np.int32)
+        trig_trk = np.where(owner >= 0, inter[np.maximum(owner, 0)],
+                            irng.integers(0, n_interactions, m)).astype(np.int32)
     perm = rng.permutation(m)
     inv = np.empty(m, dtype=np.int64)
     inv[perm] = np.arange(m)
@@ -280,6 +290,8 @@ def make_timeframe(n_seeds: int, seed: int = 0, noise: float = 0.2, bz: float = 
         vzz=np.full(m, ROW_LENGTH ** 2 / 12.0, np.float32),
         vyz=np.zeros(m, np.float32),
     )
+    if trig_trk is not None:
+        tracklets["trigger"] = trig_trk[perm]
 
     # seeds
     z_s = tgl * s_s
@@ -311,20 +323,24 @@ def make_timeframe(n_seeds: int, seed: int = 0, noise: float = 0.2, bz: float = 
         tgl=t0.astype(np.float32), q2pt=k0.astype(np.float32),
         cov=np.ascontiguousarray(cov.astype(np.float32)),
     )
+    if trig_seed is not None:
+        seeds["trigger"] = trig_seed
     return Timeframe(name=name, seeds=seeds, tracklets=tracklets,
                      params=params if params is not None else default_params(bz),
                      truth_ids=truth, truth_pt=pt.astype(np.float32))
 
 
-def make_workload(name: str, seed: int = 0, n_seeds: int | None = None) -> Timeframe:
+def make_workload(name: str, seed: int = 0, n_seeds: int | None = None,
+                  n_interactions: int = 0) -> Timeframe:
     """One of the named workloads (tiny, timeframe, calibration), optionally
-    with a different seed count (same distributions)."""
+    with a different seed count (same distributions) and with interaction ids
+    (n_interactions > 0: per-interaction association, Sec. 4)."""
     w = WORKLOADS[name]
     params = default_params(0.5, n_sigma_road=w["road"], chi2_cut=w["chi2_cut"],
                             n_hyp=w["n_hyp"], max_missing=w["max_missing"])
     return make_timeframe(n_seeds or w["n_seeds"], seed=seed, noise=w["noise"],
                           distortion=w["distortion"], sys_y=2.0 if w["distortion"] else 0.0,
-                          name=name, params=params)
+                          name=name, params=params, n_interactions=n_interactions)
 
 
 def batched_seed_counts(n_tf=64, lo=5_000, hi=400_000, seed=0):

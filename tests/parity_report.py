@@ -23,13 +23,14 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="calibration")
     ap.add_argument("--stride", type=int, default=1500)
+    ap.add_argument("--association", type=int, default=0, help="interactions per timeframe")
     a = ap.parse_args()
     import torch
     from oracle import oracle as O
     from paper_2003_03174_b300 import trd
     from parity import compare, to_numpy
     from synth import make_workload, efficiency_purity
-    tf = make_workload(a.workload)
+    tf = make_workload(a.workload, n_interactions=a.association)
     ctx = trd.Context(0)
     idx = ctx.index_build(trd.to_device(tf.tracklets))
     g = to_numpy(ctx.follow(trd.to_device(tf.seeds), idx, tf.params))
@@ -38,7 +39,8 @@ def main():
     o = O.follow(tf.seeds, tf.tracklets, tf.params, seed_index=sel)
     rep = compare(g, o, sel=sel)
     names = ["y", "z", "snp", "tgl", "q2pt"]
-    out = {"workload": a.workload, "seeds": tf.n_seeds, "tracklets": tf.n_tracklets,
+    out = {"workload": a.workload, "interactions": a.association, "seeds": tf.n_seeds,
+           "tracklets": tf.n_tracklets,
            "params": {k: tf.params[k] for k in ("n_hyp", "n_sigma_road", "chi2_cut", "max_missing")},
            "sample": len(sel), "same_path": rep["same_path"], "exempt_near_ties": rep["exempt"],
            "param_rel_err": {nm: {"max": rep["max_par_rel_each"][i], "p99": rep["p99_par_rel"][i]}

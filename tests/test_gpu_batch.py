@@ -116,3 +116,18 @@ def test_batch_rejects_bad_offsets(ctx):
         with pytest.raises(trd.TrdError):
             ctx.batch_create(s, t, bad_so, bad_to if len(bad_to) == len(bad_so) else to[:len(bad_so)],
                              tfs[0].params, res)
+
+
+def test_batch_with_association_equals_alone(ctx):
+    from synth.timeframe import default_params, make_timeframe
+    p = default_params(n_hyp=3)
+    tfs = [make_timeframe(n, seed=40 + k, noise=0.3, params=p, n_interactions=30) for k, n in
+           enumerate([2000, 0, 700, 3500])]
+    b, s, t, res, so = _run_batch(ctx, tfs)
+    got = to_numpy(res)
+    for k, tf in enumerate(tfs):
+        alone = _plain(ctx, tf)
+        part = _slice(got, so[k], so[k + 1])
+        for key in alone:
+            np.testing.assert_array_equal(part[key], alone[key], err_msg=f"tf {k} {key}")
+    b.free()

@@ -231,3 +231,16 @@ def test_lane_groups_do_not_change_multi_hypothesis_results(ctx):
     for o in outs[1:]:
         for k in outs[0]:
             np.testing.assert_array_equal(o[k], outs[0][k], err_msg=k)
+
+
+@pytest.mark.parametrize("n_hyp", [1, 3])
+def test_association_parity(ctx, n_hyp):
+    """Per-interaction association (Sec. 4) on the GPU against the oracle."""
+    p = G.default_params(n_hyp=n_hyp)
+    tf = make_timeframe(20_000, seed=31 + n_hyp, noise=0.3, params=p, n_interactions=100)
+    g, _ = run_gpu(ctx, tf, params=p)
+    o = O.follow(tf.seeds, tf.tracklets, p)
+    compare(g, o)
+    ids = g["tracklet_id"]
+    ok = ids >= 0
+    assert np.all(tf.tracklets["trigger"][ids[ok]] == np.broadcast_to(tf.seeds["trigger"], ids.shape)[ok])

@@ -123,3 +123,21 @@ def test_destroy_finishes_pending_work(ctx, tfs):
     for tf, o in zip(tfs, outs):
         if tf.n_seeds:
             np.testing.assert_array_equal(o["tracklet_id"], _alone(ctx, tf)["tracklet_id"])
+
+
+def test_served_association_equals_alone(ctx):
+    from paper_2003_03174_b300 import trd
+    from synth.timeframe import default_params, make_timeframe
+    p = default_params(n_hyp=3)
+    tfs = [make_timeframe(n, seed=50 + k, noise=0.3, params=p, n_interactions=25) for k, n in
+           enumerate([3000, 800, 5000])]
+    srv = trd.Server(ctx, p, max_slots=2)
+    outs = [trd.host_results(tf.n_seeds) for tf in tfs]
+    tickets = [srv.submit(tf.seeds, tf.tracklets, o) for tf, o in zip(tfs, outs)]
+    for t in tickets:
+        assert srv.wait(t, 60_000) is not None
+    for tf, o in zip(tfs, outs):
+        alone = _alone(ctx, tf)
+        for k in alone:
+            np.testing.assert_array_equal(o[k], alone[k], err_msg=k)
+    srv.close()

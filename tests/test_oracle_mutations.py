@@ -37,6 +37,8 @@ PINNED = [
     ("selection keeps the worst", "if (a->score < b->score) return -1;\n    if (a->score > b->score) return 1;",
      "if (a->score > b->score) return -1;\n    if (a->score < b->score) return 1;"),
     ("missing budget off by one", "if (work[hi].nmiss < P->max_missing)", "if (work[hi].nmiss <= P->max_missing)"),
+    ("association ignores the ids", "return seed_trig < 0 || !T->trig || T->trig[j] < 0 || T->trig[j] == seed_trig;",
+     "return 1;"),
     ("road uses n^2", "const double s[4] = {P->n_sigma_road - ny,", "const double s[4] = {P->n_sigma_road * P->n_sigma_road - ny,"),
 ]
 
@@ -60,6 +62,7 @@ PINS = [
     lambda: P.test_zero_noise_with_pad_rows_assigns_truth(),
     lambda: P.test_dy_gate_at_four_sigma(),
     lambda: P.test_road_boundary_at_n_sigma(),
+    lambda: P.test_association_never_crosses_interactions(),
     lambda: P.test_tiny_efficiency_and_purity(),
     lambda: P.test_greedy_n1_takes_best_chi2_each_layer(),
     lambda: P.test_beam_search_equals_exhaustive_enumeration(),

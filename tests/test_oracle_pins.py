@@ -537,3 +537,44 @@ def test_road_boundary_at_n_sigma():
         r = O.follow(tf.seeds, t2, p, seed_index=ok)
         got = r["tracklet_id"][0] == j
         assert got.mean() > 0.95 if expect else got.mean() < 0.05
+
+
+# ---------------------------------------------------------------- association
+def test_association_never_crosses_interactions():
+    """Sec. 4: only tracklets of the track's own interaction are considered."""
+    p = G.default_params()
+    tf = make_timeframe(2000, seed=23, noise=0.5, params=p, n_interactions=40)
+    r = O.follow(tf.seeds, tf.tracklets, p)
+    ids = r["tracklet_id"]
+    ok = ids >= 0
+    seed_trig = np.broadcast_to(tf.seeds["trigger"], ids.shape)
+    assert ok.sum() > 1000
+    assert np.all(tf.tracklets["trigger"][ids[ok]] == seed_trig[ok])
+
+
+def test_association_with_one_interaction_changes_nothing():
+    tf = make_workload("tiny", seed=24)
+    a = O.follow(tf.seeds, tf.tracklets, tf.params)
+    s2 = dict(tf.seeds, trigger=np.full(tf.n_seeds, 3, np.int32))
+    t2 = dict(tf.tracklets, trigger=np.full(tf.n_tracklets, 3, np.int32))
+    b = O.follow(s2, t2, tf.params)
+    untagged = dict(tf.tracklets, trigger=np.full(tf.n_tracklets, -1, np.int32))
+    c = O.follow(s2, untagged, tf.params)  # tracklets without an id stay candidates for every seed
+    for k in ("tracklet_id", "par", "cov", "chi2", "status"):
+        np.testing.assert_array_equal(a[k], b[k])
+        np.testing.assert_array_equal(a[k], c[k])
+
+
+def test_association_improves_purity_at_timeframe_density():
+    """With Run-3 time frames of many collisions (Sec. 3.1), restricting the
+    candidates to the track's interaction removes the other collisions' fakes."""
+    base = make_workload("timeframe", seed=2, n_seeds=40_000)
+    p = base.params
+    assoc = make_timeframe(40_000, seed=2, noise=0.3, params=p, name="timeframe", n_interactions=600)
+    sel = np.arange(0, 40_000, 8)
+    ep0 = efficiency_purity(O.follow(base.seeds, base.tracklets, p, seed_index=sel)["tracklet_id"],
+                            base.truth_ids[sel])
+    ep1 = efficiency_purity(O.follow(assoc.seeds, assoc.tracklets, p, seed_index=sel)["tracklet_id"],
+                            assoc.truth_ids[sel])
+    assert ep1["purity"] > ep0["purity"] + 0.02
+    assert ep1["efficiency_reachable"] >= ep0["efficiency_reachable"] - 0.005
