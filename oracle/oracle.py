@@ -51,6 +51,7 @@ def _load(path):
         L.ora_rotate.argtypes = [_d, _d, C.c_double, C.c_double, C.c_void_p, C.c_void_p]
         L.ora_rotate.restype = C.c_int
         L.ora_material.argtypes = [_d, _d]
+        L.ora_material_inward.argtypes = [_d, _d]
         L.ora_material.restype = C.c_int
         L.ora_bethe.argtypes = [C.c_double]
         L.ora_bethe.restype = C.c_double
@@ -65,6 +66,7 @@ def _load(path):
         L.ora_constants.argtypes = [_d, C.c_int]
         L.ora_constants.restype = None
         L.ora_follow.restype = C.c_int
+        L.ora_refit.restype = C.c_int
         L.ora_to_layer.argtypes = [_d, _d, C.c_void_p, C.c_int, _d, _i, C.c_void_p]
         L.ora_to_layer.restype = C.c_int
         L.ora_candidates.argtypes = [_d, _d, C.c_int, C.c_int, C.c_int, _i, _f, _f, _f, _f, _f,
@@ -98,6 +100,13 @@ def rotate(st, cov, alpha_new, bz):
 def material(st, cov):
     s, c = _vec(st, 7), _vec(cov, 15)
     ok = lib().ora_material(s, c) == 0
+    return ok, s, c
+
+
+def material_inward(st, cov):
+    """The material step of a track moving inward (energy loss added back)."""
+    s, c = _vec(st, 7), _vec(cov, 15)
+    ok = lib().ora_material_inward(s, c) == 0
     return ok, s, c
 
 
@@ -183,6 +192,37 @@ def follow(seeds: dict, tracklets: dict, params: dict, seed_index=None, brute=Fa
                 n_miss=nmiss, status=status, tracklet_id=ids, margin=margin, nroad=nroad)
 
 
+def refit(results: dict, tracklets: dict, params: dict, cov_scale: float = 100.0,
+          n_threads=0) -> dict:
+    """Run the FP64 TRD-only refit (Sec. 2, step 3) on the follower's results.
+
+    results: arrays in the library's result layout (alpha, x [n]; par [5, n];
+    cov [15, n]; status [n]; tracklet_id [6, n]), taken as FP32 like the
+    library reads them.  Returns alpha, x, par, cov, chi2, n_upd, status."""
+    L = lib()
+    n = int(np.asarray(results["alpha"]).shape[0])
+    m = int(tracklets["chamber"].shape[0])
+    a = [_f32(results["alpha"]), _f32(results["x"]), _f32(results["par"]).reshape(5, n),
+         _f32(results["cov"]).reshape(15, n)]
+    st_in = np.ascontiguousarray(np.asarray(results["status"], dtype=np.int32))
+    ids = np.ascontiguousarray(np.asarray(results["tracklet_id"], dtype=np.int32).reshape(6, n))
+    tk = [np.ascontiguousarray(np.asarray(tracklets["chamber"], dtype=np.int32))] + [
+        _f32(tracklets[k]) for k in ("y", "z", "vyy", "vzz", "vyz")]
+    pd, pi = _params_arrays(params)
+    st = np.zeros((7, n))
+    cv = np.zeros((15, n))
+    chi2_ = np.zeros(n)
+    nupd = np.zeros(n, np.int32)
+    status = np.zeros(n, np.int32)
+    ptr = lambda v: v.ctypes.data_as(C.c_void_p)  # noqa: E731
+    rc = L.ora_refit(C.c_int(n), *[ptr(v) for v in a], ptr(st_in), ptr(ids), C.c_int(m),
+                     *[ptr(v) for v in tk], ptr(pd), ptr(pi), C.c_double(cov_scale),
+                     C.c_int(n_threads), ptr(st), ptr(cv), ptr(chi2_), ptr(nupd), ptr(status))
+    if rc != 0:
+        raise ValueError(f"ora_refit rejected its arguments ({rc})")
+    return dict(alpha=st[0], x=st[1], par=st[2:7], cov=cv, chi2=chi2_, n_upd=nupd, status=status)
+
+
 def to_layer(st, cov, sector, layer, params):
     """Carry a state to the plane of `layer` (transport, sector change,
     material).  Returns (ok, st, cov, sector, chamber)."""
@@ -216,4 +256,5 @@ def _params_arrays(params):
 
 
 __all__ = ["use_library", "propagate", "rotate", "material", "bethe", "highland", "update", "chi2",
-           "cov_is_pd", "constants", "follow", "to_layer", "candidates", "lib"]
+           "cov_is_pd", "constants", "follow", "refit", "to_layer", "candidates", "lib",
+           "material_inward"]

@@ -271,7 +271,12 @@ double ora_highland(double p, double beta, double xx0)
 /* One material step: multiple scattering widens snp, tgl, q2pt; the mean
  * energy loss of a pion reduces |p| and scales q2pt and its covariance row
  * by p/p'.  Returns -1 when the particle stops.                            */
-int ora_material(double st[7], double c[15])
+/* One material step at the current position.  dir = +1 for a track moving
+ * outward (the mean loss is subtracted), -1 for a track moving inward (the
+ * refit of Sec. 2, step 3: the loss is added back).  The scattering term is
+ * the same in both directions; the loss is evaluated at the momentum on
+ * entering the step.                                                       */
+static int material_dir(double st[7], double c[15], double dir)
 {
     const double f = st[4], t = st[5], k = st[6];
     if (k == 0.0) return 0;
@@ -289,7 +294,7 @@ int ora_material(double st[7], double c[15])
     c[ci(4, 3)] += th2 * t * t2 * k;
     c[ci(4, 4)] += th2 * t * t * k * k;
     const double de = ora_bethe(p / kMassPion) * xrho * 1e-3;
-    const double e1 = e - de;
+    const double e1 = e - dir * de;
     if (e1 <= kMassPion) return -1;
     const double p1 = sqrt(e1 * e1 - kMassPion * kMassPion);
     const double sc = p / p1;
@@ -298,6 +303,9 @@ int ora_material(double st[7], double c[15])
     c[ci(4, 4)] *= sc * sc;
     return 0;
 }
+
+int ora_material(double st[7], double c[15]) { return material_dir(st, c, 1.0); }
+int ora_material_inward(double st[7], double c[15]) { return material_dir(st, c, -1.0); }
 
 /* ---- measurement model with pad tilt (Sec. 3) -----------------------------
  * Only y and z enter the chi2.  The tilted pads make the measured y depend on
@@ -758,5 +766,130 @@ int ora_follow(int n_seeds, const float *alpha, const float *x, const float *y, 
     }
     free(start);
     free(list);
+    return 0;
+}
+
+/* ---- the TRD-only refit (Sec. 2, step 3) ------------------------------------
+ * The calibration chain refits each matched track twice, once from the ITS
+ * and once from TRD and TOF alone, without the TPC clusters.  This is the
+ * TRD half (no TOF points are modelled).  Reading, in order:
+ *   1. only tracks with at least two tracklets (matched, Sec. 3.1) whose
+ *      follower status is not SEED_INVALID are refitted;
+ *   2. the prior is the follower's final state with its covariance reduced
+ *      to the diagonal and scaled by cov_scale (the TPC-derived correlations
+ *      are dropped and the variances widened, so the prior carries little of
+ *      the TPC's information);
+ *   3. the prior is carried (helix, no material) into the sector frame of the
+ *      outermost tracklet and to that layer's plane;
+ *   4. for l from that layer down to 0: transport to x_l (from the second
+ *      layer on), entering the tracklet's sector when it lies in another one
+ *      (or the neighbour sector at the azimuthal edge when the layer has no
+ *      tracklet), Kalman update with the layer's tracklet, then the layer's
+ *      material with the energy loss added back (the material of layer l
+ *      sits just inside x_l, where the outward follower meets it before its
+ *      update);
+ *   5. the result is the state at x_0 after the material of layer 0, with the
+ *      sum of the update chi2 values and the number of updates.
+ * A transport or rotation that fails (|snp| limit) stops the refit (status
+ * PROP_FAIL); the result is then the state as far as it was carried (a
+ * failing transport or rotation leaves the state untouched).               */
+enum { ORA_RF_PROP_FAIL = 1, ORA_RF_SKIPPED = 8 };
+
+typedef struct {
+    double st[7], c[15], chi2;
+    int nupd, status;
+} ora_refit_result_t;
+
+static void refit_one(const double in_st[7], const double in_cdiag[5], int in_status, const int ids[ORA_NLAYER],
+                      const ora_tracklets_t *T, const ora_params_t *P, double cov_scale, ora_refit_result_t *R)
+{
+    memset(R, 0, sizeof *R);
+    memcpy(R->st, in_st, sizeof R->st);
+    int ntrk = 0, ltop = -1;
+    for (int l = 0; l < ORA_NLAYER; ++l)
+        if (ids[l] >= 0) { ++ntrk; ltop = l; }
+    if (ntrk < 2 || (in_status & ORA_ST_SEED_INVALID)) { R->status = ORA_RF_SKIPPED; return; }
+    for (int l = 0; l < ORA_NLAYER; ++l)
+        if (ids[l] >= T->n || (ids[l] >= 0 && (T->ch[ids[l]] < 0 || T->ch[ids[l]] >= ORA_NCHAMBER))) {
+            R->status = ORA_RF_SKIPPED;
+            return;
+        }
+
+    ora_hyp_t h;
+    memset(&h, 0, sizeof h);
+    memcpy(h.st, in_st, sizeof h.st);
+    /* step 2: diagonal prior */
+    for (int i = 0; i < 5; ++i) h.c[ci(i, i)] = cov_scale * in_cdiag[i];
+    h.sector = sector_of_alpha(in_st[0]);
+
+    int fail = 0;
+    for (int l = ltop; l >= 0 && !fail; --l) {
+        const double xl = layer_x(l);
+        const int j = ids[l];
+        /* step 3 (l == ltop) and step 4: into the tracklet's sector, to x_l */
+        if (ora_propagate(h.st, h.c, xl, P->bz, NULL, NULL)) { fail = 1; break; }
+        int target = h.sector;
+        if (j >= 0)
+            target = T->ch[j] / (ORA_NSTACK * ORA_NLAYER);
+        else if (fabs(h.st[2]) > xl * half_sector_tan())
+            target = (h.sector + (h.st[2] > 0 ? 1 : -1) + ORA_NSECTOR) % ORA_NSECTOR;
+        if (target != h.sector) {
+            if (ora_rotate(h.st, h.c, sector_alpha(target), P->bz, NULL, NULL)) { fail = 1; break; }
+            h.sector = target;
+            if (ora_propagate(h.st, h.c, xl, P->bz, NULL, NULL)) { fail = 1; break; }
+        }
+        if (j >= 0) {
+            double m5[5] = {T->y[j], T->z[j], T->vyy[j], T->vzz[j], T->vyz[j]};
+            if (P->res_mode) {
+                const double f = h.st[4], r = sqrt((1.0 - f) * (1.0 + f));
+                const double u = f / r - lorentz_tan(P->bz);
+                m5[2] = kSigY0 * kSigY0 + kSigY1 * kSigY1 * u * u;
+            }
+            h.chi2 += ora_update(h.st, h.c, l, m5, 0);
+            h.ntrk += 1;
+        }
+        if (P->material_on && material_dir(h.st, h.c, -1.0)) { fail = 1; break; }
+    }
+    memcpy(R->st, h.st, sizeof R->st);
+    memcpy(R->c, h.c, sizeof R->c);
+    R->chi2 = h.chi2;
+    R->nupd = h.ntrk;
+    R->status = fail ? ORA_RF_PROP_FAIL : 0;
+}
+
+/* Entry point of the refit.  The follower's results (FP32 arrays in the
+ * library's layout, n tracks) and the tracklets (input order) are widened
+ * to double.  Outputs: st_out[7][n], cov_out[15][n], chi2_out[n],
+ * nupd_out[n], status_out[n].  pd/pi as for ora_follow.  Returns 0, or -1
+ * on invalid arguments.                                                     */
+int ora_refit(int n, const float *alpha, const float *x, const float *par, const float *cov,
+              const int *status, const int *ids, int n_trk, const int *t_ch, const float *t_y,
+              const float *t_z, const float *t_vyy, const float *t_vzz, const float *t_vyz,
+              const double *pd, const int *pi, double cov_scale, int n_threads, double *st_out,
+              double *cov_out, double *chi2_out, int *nupd_out, int *status_out)
+{
+    if (n < 0 || n_trk < 0 || !(cov_scale > 0)) return -1;
+    ora_params_t P = {pd[0], pd[1], pd[2], pd[3], pd[4], pi[0], pi[1], pi[2], pi[3]};
+    ora_tracklets_t T = {n_trk, t_ch, t_y, NULL, NULL, t_vyy, t_vzz, t_vyz, NULL, NULL, 1, NULL};
+    T.z = t_z;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 256)
+#endif
+    for (int i = 0; i < n; ++i) {
+        double s7[7] = {alpha[i], x[i]};
+        for (int k = 0; k < 5; ++k) s7[2 + k] = par[(size_t)k * n + i];
+        double cd[5];
+        for (int k = 0; k < 5; ++k) cd[k] = cov[(size_t)ci(k, k) * n + i];
+        int id6[ORA_NLAYER];
+        for (int l = 0; l < ORA_NLAYER; ++l) id6[l] = ids[(size_t)l * n + i];
+        ora_refit_result_t R;
+        refit_one(s7, cd, status[i], id6, &T, &P, cov_scale, &R);
+        for (int k = 0; k < 7; ++k) st_out[(size_t)k * n + i] = R.st[k];
+        for (int k = 0; k < 15; ++k) cov_out[(size_t)k * n + i] = R.c[k];
+        chi2_out[i] = R.chi2;
+        nupd_out[i] = R.nupd;
+        status_out[i] = R.status;
+    }
     return 0;
 }

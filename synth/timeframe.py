@@ -118,6 +118,17 @@ def _cross_chamber_plane(phi0, k, xp):
     return sec, s, yl, sinl, ok
 
 
+def truth_at_plane(truth: dict, alpha, xp):
+    """The truth track's local state where it crosses the plane x = xp of the
+    frame of azimuth alpha: (y, z, sin(phi), tan(lambda), q/pT, ok), arrays
+    over the truth entries (alpha may be an array)."""
+    phi0, k, tgl = truth["phi0"], truth["kcurv"], truth["tgl"]
+    a = np.broadcast_to(np.asarray(alpha, dtype=np.float64), phi0.shape)
+    s, ok = _cross_plane(phi0, k, a, xp)
+    _, y = _local_xy(s, phi0, k, a)
+    return y, tgl * s, np.sin(phi0 + k * s - a), tgl, truth["q2pt"], ok
+
+
 def pad_tilt_tan(layer: int) -> float:
     """tan of the pad tilt: +2 degrees on even layers, -2 on odd (a reading)."""
     return math.tan(math.radians(PAD_TILT_DEG if layer % 2 == 0 else -PAD_TILT_DEG))
@@ -154,6 +165,9 @@ class Timeframe:
     params: dict  # follower parameters of the workload
     truth_ids: np.ndarray  # int32[n, 6]: input index of the seed's true tracklet, -1 if none
     truth_pt: np.ndarray = field(default=None)
+    # truth helix per seed: azimuth at the origin phi0, signed curvature kcurv
+    # (d(phi)/ds, 1/cm), tan(lambda), q/pT: float64[n] each
+    truth: dict = field(default=None)
 
     @property
     def n_seeds(self) -> int:
@@ -327,7 +341,8 @@ def make_timeframe(n_seeds: int, seed: int = 0, noise: float = 0.2, bz: float = 
         seeds["trigger"] = trig_seed
     return Timeframe(name=name, seeds=seeds, tracklets=tracklets,
                      params=params if params is not None else default_params(bz),
-                     truth_ids=truth, truth_pt=pt.astype(np.float32))
+                     truth_ids=truth, truth_pt=pt.astype(np.float32),
+                     truth=dict(phi0=phi0, kcurv=kcurv, tgl=tgl, q2pt=q / pt))
 
 
 def make_workload(name: str, seed: int = 0, n_seeds: int | None = None,

@@ -10,6 +10,7 @@ import pytest
 
 from oracle import oracle as O
 import test_oracle_pins as P
+import test_oracle_refit_pins as R
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(os.path.dirname(HERE), "oracle", "trd_oracle.c")
@@ -40,6 +41,17 @@ PINNED = [
     ("association ignores the ids", "return seed_trig < 0 || !T->trig || T->trig[j] < 0 || T->trig[j] == seed_trig;",
      "return 1;"),
     ("road uses n^2", "const double s[4] = {P->n_sigma_road - ny,", "const double s[4] = {P->n_sigma_road * P->n_sigma_road - ny,"),
+    # the TRD-only refit (Sec. 2, step 3)
+    ("refit prior not widened", "for (int i = 0; i < 5; ++i) h.c[ci(i, i)] = cov_scale * in_cdiag[i];",
+     "for (int i = 0; i < 5; ++i) h.c[ci(i, i)] = in_cdiag[i];"),
+    ("refit loss taken with the outward sign", "if (P->material_on && material_dir(h.st, h.c, -1.0)) { fail = 1; break; }",
+     "if (P->material_on && material_dir(h.st, h.c, 1.0)) { fail = 1; break; }"),
+    ("refit skips the outermost update", "for (int l = ltop; l >= 0 && !fail; --l) {",
+     "for (int l = ltop - 1; l >= 0 && !fail; --l) {"),
+    ("refit update with the next layer's tilt", "h.chi2 += ora_update(h.st, h.c, l, m5, 0);",
+     "h.chi2 += ora_update(h.st, h.c, l + 1, m5, 0);"),
+    ("refit stays in its sector", "            target = T->ch[j] / (ORA_NSTACK * ORA_NLAYER);",
+     "            target = h.sector;"),
 ]
 
 UNPINNED = [
@@ -66,6 +78,12 @@ PINS = [
     lambda: P.test_tiny_efficiency_and_purity(),
     lambda: P.test_greedy_n1_takes_best_chi2_each_layer(),
     lambda: P.test_beam_search_equals_exhaustive_enumeration(),
+    lambda: R.test_refit_equals_map_least_squares_without_material(100.0, 0.5, 0.05),
+    lambda: R.test_refit_recovers_noiseless_truth(),
+    lambda: R.test_refit_pulls_are_unit_normal(),
+    lambda: R.test_inward_refit_undoes_the_outward_material(),
+    lambda: R.test_refit_output_frame_is_the_layer0_sector(),
+    lambda: R.test_refit_skips_unmatched_and_invalid_tracks(),
 ]
 
 
