@@ -67,6 +67,10 @@ def _load(path):
         L.ora_constants.restype = None
         L.ora_follow.restype = C.c_int
         L.ora_refit.restype = C.c_int
+        L.ora_voxel_of.argtypes = [C.c_float, C.c_float, C.c_int, C.c_int]
+        L.ora_voxel_of.restype = C.c_int
+        L.ora_residuals.restype = C.c_int
+        L.ora_voxel_solve.restype = C.c_int
         L.ora_to_layer.argtypes = [_d, _d, C.c_void_p, C.c_int, _d, _i, C.c_void_p]
         L.ora_to_layer.restype = C.c_int
         L.ora_candidates.argtypes = [_d, _d, C.c_int, C.c_int, C.c_int, _i, _f, _f, _f, _f, _f,
@@ -214,13 +218,74 @@ def refit(results: dict, tracklets: dict, params: dict, cov_scale: float = 100.0
     chi2_ = np.zeros(n)
     nupd = np.zeros(n, np.int32)
     status = np.zeros(n, np.int32)
+    margin = np.zeros(n)
     ptr = lambda v: v.ctypes.data_as(C.c_void_p)  # noqa: E731
     rc = L.ora_refit(C.c_int(n), *[ptr(v) for v in a], ptr(st_in), ptr(ids), C.c_int(m),
                      *[ptr(v) for v in tk], ptr(pd), ptr(pi), C.c_double(cov_scale),
-                     C.c_int(n_threads), ptr(st), ptr(cv), ptr(chi2_), ptr(nupd), ptr(status))
+                     C.c_int(n_threads), ptr(st), ptr(cv), ptr(chi2_), ptr(nupd), ptr(status),
+                     ptr(margin))
     if rc != 0:
         raise ValueError(f"ora_refit rejected its arguments ({rc})")
-    return dict(alpha=st[0], x=st[1], par=st[2:7], cov=cv, chi2=chi2_, n_upd=nupd, status=status)
+    return dict(alpha=st[0], x=st[1], par=st[2:7], cov=cv, chi2=chi2_, n_upd=nupd, status=status,
+                margin=margin)
+
+
+N_TPC_ROWS = 152
+N_VOXELS = 36 * 152 * 15 * 5
+N_VOX_SUMS = 11
+
+
+def voxel_of(y, z, sector, row) -> int:
+    return int(lib().ora_voxel_of(C.c_float(y), C.c_float(z), int(sector), int(row)))
+
+
+def residuals(its: dict, trd: dict, clusters: dict, bz: float, sums=None, with_clusters=False,
+              n_threads=0) -> dict:
+    """FP64 residual collection (Sec. 2, step 4).  its/trd: refit states in
+    the library's layout (alpha, x, par, cov, status); clusters: y, z [152, n]
+    float32 and sector [152, n] int8.  Returns the voxel sums [N_VOXELS, 11]
+    (added to `sums` when given), their absolute-value twins, and with
+    with_clusters the per-cluster dy, dz, t, u [4, 152, n], voxel [152, n],
+    combined variances [2, 152, n] and per-track slack."""
+    L = lib()
+    n = int(np.asarray(its["alpha"]).shape[0])
+    st = []
+    for d in (its, trd):
+        st += [_f32(d["alpha"]), _f32(d["x"]), _f32(d["par"]).reshape(5, n), _f32(d["cov"]).reshape(15, n),
+               np.ascontiguousarray(np.asarray(d["status"], dtype=np.int32))]
+    cy, cz = _f32(clusters["y"]).reshape(N_TPC_ROWS, n), _f32(clusters["z"]).reshape(N_TPC_ROWS, n)
+    cs = np.ascontiguousarray(np.asarray(clusters["sector"], dtype=np.int8).reshape(N_TPC_ROWS, n))
+    S = np.zeros((N_VOXELS, N_VOX_SUMS)) if sums is None else sums
+    A = np.zeros((N_VOXELS, N_VOX_SUMS))
+    ptr = lambda v: v.ctypes.data_as(C.c_void_p)  # noqa: E731
+    extra = [None, None, None, None]
+    if with_clusters:
+        res = np.zeros((4, N_TPC_ROWS, n), np.float32)
+        vox = np.zeros((N_TPC_ROWS, n), np.int32)
+        var = np.zeros((2, N_TPC_ROWS, n), np.float32)
+        slack = np.zeros(n)
+        extra = [ptr(res), ptr(vox), ptr(var), ptr(slack)]
+    rc = L.ora_residuals(C.c_int(n), *[ptr(v) for v in st], ptr(cy), ptr(cz), ptr(cs), C.c_double(bz),
+                         C.c_int(n_threads), ptr(S), ptr(A), *extra)
+    if rc != 0:
+        raise ValueError(f"ora_residuals rejected its arguments ({rc})")
+    out = dict(sums=S, abs_sums=A)
+    if with_clusters:
+        out.update(res=res, vox=vox, var=var, slack=slack)
+    return out
+
+
+def voxel_solve(sums, min_count=1) -> np.ndarray:
+    """Distortion vector per voxel (Sec. 2, step 5): [N, 6] = Dx, Dy, Dz, n,
+    rms dy, rms dz (NaN where undetermined)."""
+    S = np.ascontiguousarray(np.asarray(sums, dtype=np.float64))
+    nv = S.shape[0]
+    out = np.zeros((nv, 6))
+    rc = lib().ora_voxel_solve(S.ctypes.data_as(C.c_void_p), C.c_int(nv), C.c_int(min_count),
+                               out.ctypes.data_as(C.c_void_p))
+    if rc != 0:
+        raise ValueError("ora_voxel_solve rejected its arguments")
+    return out
 
 
 def to_layer(st, cov, sector, layer, params):
@@ -257,4 +322,4 @@ def _params_arrays(params):
 
 __all__ = ["use_library", "propagate", "rotate", "material", "bethe", "highland", "update", "chi2",
            "cov_is_pd", "constants", "follow", "refit", "to_layer", "candidates", "lib",
-           "material_inward"]
+           "material_inward", "residuals", "voxel_solve", "voxel_of", "N_VOXELS", "N_TPC_ROWS"]

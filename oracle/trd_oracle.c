@@ -798,6 +798,7 @@ enum { ORA_RF_PROP_FAIL = 1, ORA_RF_SKIPPED = 8 };
 typedef struct {
     double st[7], c[15], chi2;
     int nupd, status;
+    double margin; /* smallest slack of a decision (|snp| limit, sector edge) */
 } ora_refit_result_t;
 
 static void refit_one(const double in_st[7], const double in_cdiag[5], int in_status, const int ids[ORA_NLAYER],
@@ -805,6 +806,7 @@ static void refit_one(const double in_st[7], const double in_cdiag[5], int in_st
 {
     memset(R, 0, sizeof *R);
     memcpy(R->st, in_st, sizeof R->st);
+    R->margin = INFINITY;
     int ntrk = 0, ltop = -1;
     for (int l = 0; l < ORA_NLAYER; ++l)
         if (ids[l] >= 0) { ++ntrk; ltop = l; }
@@ -827,17 +829,26 @@ static void refit_one(const double in_st[7], const double in_cdiag[5], int in_st
         const double xl = layer_x(l);
         const int j = ids[l];
         /* step 3 (l == ltop) and step 4: into the tracklet's sector, to x_l */
-        if (ora_propagate(h.st, h.c, xl, P->bz, NULL, NULL)) { fail = 1; break; }
+        double sl = INFINITY;
+        if (ora_propagate(h.st, h.c, xl, P->bz, NULL, &sl)) { fail = 1; }
         int target = h.sector;
-        if (j >= 0)
+        if (!fail && j >= 0) {
             target = T->ch[j] / (ORA_NSTACK * ORA_NLAYER);
-        else if (fabs(h.st[2]) > xl * half_sector_tan())
-            target = (h.sector + (h.st[2] > 0 ? 1 : -1) + ORA_NSECTOR) % ORA_NSECTOR;
-        if (target != h.sector) {
-            if (ora_rotate(h.st, h.c, sector_alpha(target), P->bz, NULL, NULL)) { fail = 1; break; }
-            h.sector = target;
-            if (ora_propagate(h.st, h.c, xl, P->bz, NULL, NULL)) { fail = 1; break; }
+        } else if (!fail) {
+            const double lim = xl * half_sector_tan();
+            sl = fmin(sl, fabs(fabs(h.st[2]) - lim));
+            if (fabs(h.st[2]) > lim) target = (h.sector + (h.st[2] > 0 ? 1 : -1) + ORA_NSECTOR) % ORA_NSECTOR;
         }
+        if (!fail && target != h.sector) {
+            if (ora_rotate(h.st, h.c, sector_alpha(target), P->bz, NULL, &sl)) {
+                fail = 1;
+            } else {
+                h.sector = target;
+                if (ora_propagate(h.st, h.c, xl, P->bz, NULL, &sl)) fail = 1;
+            }
+        }
+        R->margin = fmin(R->margin, sl);
+        if (fail) break;
         if (j >= 0) {
             double m5[5] = {T->y[j], T->z[j], T->vyy[j], T->vzz[j], T->vyz[j]};
             if (P->res_mode) {
@@ -860,13 +871,15 @@ static void refit_one(const double in_st[7], const double in_cdiag[5], int in_st
 /* Entry point of the refit.  The follower's results (FP32 arrays in the
  * library's layout, n tracks) and the tracklets (input order) are widened
  * to double.  Outputs: st_out[7][n], cov_out[15][n], chi2_out[n],
- * nupd_out[n], status_out[n].  pd/pi as for ora_follow.  Returns 0, or -1
+ * nupd_out[n], status_out[n], margin_out[n] (optional: the smallest slack of
+ * a decision, |snp| limit or sector edge, in the units of its test).  pd/pi
+ * as for ora_follow.  Returns 0, or -1
  * on invalid arguments.                                                     */
 int ora_refit(int n, const float *alpha, const float *x, const float *par, const float *cov,
               const int *status, const int *ids, int n_trk, const int *t_ch, const float *t_y,
               const float *t_z, const float *t_vyy, const float *t_vzz, const float *t_vyz,
               const double *pd, const int *pi, double cov_scale, int n_threads, double *st_out,
-              double *cov_out, double *chi2_out, int *nupd_out, int *status_out)
+              double *cov_out, double *chi2_out, int *nupd_out, int *status_out, double *margin_out)
 {
     if (n < 0 || n_trk < 0 || !(cov_scale > 0)) return -1;
     ora_params_t P = {pd[0], pd[1], pd[2], pd[3], pd[4], pi[0], pi[1], pi[2], pi[3]};
@@ -890,6 +903,244 @@ int ora_refit(int n, const float *alpha, const float *x, const float *par, const
         chi2_out[i] = R.chi2;
         nupd_out[i] = R.nupd;
         status_out[i] = R.status;
+        if (margin_out) margin_out[i] = R.margin;
+    }
+    return 0;
+}
+
+/* ---- residuals in TPC sub-volumes and the distortion vector (Sec. 2,
+ * steps 4 and 5) -------------------------------------------------------------
+ * The space-point calibration compares each distorted TPC cluster with the
+ * weighted combination of the two external refits (ITS, and TRD without the
+ * TPC) and collects the residuals per TPC sub-volume; each sub-volume then
+ * yields one distortion vector in x, y and z.  Readings (the paper gives no
+ * numbers for them):
+ *   - 152 pad rows, centres at x_r = 85 + 160 (r + 1/2) / 152 cm (as float);
+ *   - a cluster of sector s (0..17) at row r is compared in the frame of s:
+ *     each refit is rotated into that frame and transported (helix, no
+ *     material in the gas) to x_r;
+ *   - combination: the (y, z) estimates are averaged with their inverse 2x2
+ *     covariances, sin(phi) and tan(lambda) with their inverse variances;
+ *   - residual (dy, dz) = cluster - combination; slopes t = dy/dx =
+ *     tan(phi) and u = dz/dx = tan(lambda) / cos(phi) of the combination;
+ *   - sub-volume (voxel): side (z < 0) x 18 sectors x 152 rows x 15 bins of
+ *     y/x in [-tan 10 deg, tan 10 deg) x 5 bins of |z|/x in [0, 1) (the last
+ *     bins take what lies beyond), decided in FP32 from the cluster's own
+ *     y, z and x_r;
+ *   - distortion of a voxel: a cluster at row x_r was freed at the track
+ *     point x_r - dx and moved by (dy, dz), so to first order its residuals
+ *     are dy_i = Dy - Dx t_i and dz_i = Dz - Dx u_i; (Dx, Dy, Dz) is the
+ *     least-squares solution over the voxel's clusters.
+ * Per voxel the oracle keeps 11 FP64 sums: n, St, Su, Stt, Suu, Sdy, Sdz,
+ * Stdy, Sudz, Sdydy, Sdzdz.                                                 */
+#define ORA_TPC_ROWS 152
+#define ORA_VOX_Y 15
+#define ORA_VOX_Z 5
+#define ORA_VOX_SECT 36
+#define ORA_NVOX (ORA_VOX_SECT * ORA_TPC_ROWS * ORA_VOX_Y * ORA_VOX_Z)
+#define ORA_VOX_SUMS 11
+
+static float tpc_row_x(int r) { return (float)(85.0 + (r + 0.5) * 160.0 / ORA_TPC_ROWS); }
+
+/* Voxel of a cluster (FP32 decisions, in the order written). */
+int ora_voxel_of(float y, float z, int sector, int row)
+{
+    if (sector < 0 || sector >= ORA_NSECTOR || row < 0 || row >= ORA_TPC_ROWS) return -1;
+    const float xr = tpc_row_x(row);
+    const float T = (float)0.17632698070846498; /* tan 10 deg */
+    const float ys = (float)ORA_VOX_Y / (2.0f * T);
+    const float u = y / xr;
+    const float v = u + T;
+    const float fy = v * ys;
+    int iy = (int)floorf(fy);
+    iy = iy < 0 ? 0 : (iy >= ORA_VOX_Y ? ORA_VOX_Y - 1 : iy);
+    const float w = fabsf(z) / xr;
+    const float fz = w * (float)ORA_VOX_Z;
+    int iz = (int)floorf(fz);
+    iz = iz < 0 ? 0 : (iz >= ORA_VOX_Z ? ORA_VOX_Z - 1 : iz);
+    const int side = z < 0.0f ? 1 : 0;
+    return (((side * ORA_NSECTOR + sector) * ORA_TPC_ROWS + row) * ORA_VOX_Y + iy) * ORA_VOX_Z + iz;
+}
+
+/* Carry a refit state along its track to the pad-row plane x_r of sector s
+ * (the cluster's frame): when s is not the state's frame, transport first in
+ * the old frame to x_r (if that fails, the state stays where it is), rotate
+ * there into s, then transport to x_r in s.  Every rotation thus happens
+ * next to the cluster.  *frame = -1: the frame is not a sector's yet (the
+ * first call always rotates).  Returns -1 when a rotation or the final
+ * transport fails (|snp| limit).                                            */
+static int tpc_carry(double st[7], double c[15], int *frame, int s, double xr, double bz, double *slack)
+{
+    if (*frame != s) {
+        (void)ora_propagate(st, c, xr, bz, NULL, slack);
+        if (ora_rotate(st, c, sector_alpha(s), bz, NULL, slack)) return -1;
+        *frame = s;
+    }
+    return ora_propagate(st, c, xr, bz, NULL, slack);
+}
+
+/* The combination of the two refits at one cluster.  out = {dy, dz, t, u,
+ * var y, var z} (residual = cluster - combination; slopes of the combined
+ * direction; variances of the combined y and z).                           */
+static void tpc_combine(const double a[2][7], const double c[2][15], float ycl, float zcl, double out[6])
+{
+    /* W = V1^-1 + V2^-1 on (y, z); m = W^-1 (V1^-1 m1 + V2^-1 m2) */
+    double Vi[2][3], g[2][2];
+    for (int k = 0; k < 2; ++k) {
+        const double vyy = c[k][0], vyz = c[k][1], vzz = c[k][2];
+        const double det = vyy * vzz - vyz * vyz;
+        Vi[k][0] = vzz / det;
+        Vi[k][1] = -vyz / det;
+        Vi[k][2] = vyy / det;
+        g[k][0] = Vi[k][0] * a[k][2] + Vi[k][1] * a[k][3];
+        g[k][1] = Vi[k][1] * a[k][2] + Vi[k][2] * a[k][3];
+    }
+    const double W00 = Vi[0][0] + Vi[1][0], W01 = Vi[0][1] + Vi[1][1], W11 = Vi[0][2] + Vi[1][2];
+    const double dW = W00 * W11 - W01 * W01;
+    const double b0 = g[0][0] + g[1][0], b1 = g[0][1] + g[1][1];
+    const double my = (W11 * b0 - W01 * b1) / dW;
+    const double mz = (-W01 * b0 + W00 * b1) / dW;
+    const double f = (a[0][4] / c[0][5] + a[1][4] / c[1][5]) / (1.0 / c[0][5] + 1.0 / c[1][5]);
+    const double tl = (a[0][5] / c[0][9] + a[1][5] / c[1][9]) / (1.0 / c[0][9] + 1.0 / c[1][9]);
+    const double r = sqrt((1.0 - f) * (1.0 + f));
+    out[0] = (double)ycl - my;
+    out[1] = (double)zcl - mz;
+    out[2] = f / r;
+    out[3] = tl / r;
+    out[4] = W11 / dW;
+    out[5] = W00 / dW;
+}
+
+/* Accumulate the residuals of n tracks into sums[ORA_NVOX][ORA_VOX_SUMS]
+ * (added to what is there) and, optionally, abs_sums (the same sums of
+ * absolute values, for tolerances).  Inputs are the FP32 arrays the library
+ * reads: refit states (alpha, x [n], par [5][n], cov [15][n], status [n]; only
+ * tracks with both statuses 0 contribute) and clusters (y, z [152][n], sector
+ * int8 [152][n], -1 = none).  Per track, the TRD refit is carried inward
+ * through the rows with a cluster (151 down to 0) and the ITS refit outward
+ * (0 up to 151), each with tpc_carry; a cluster where both arrive gives a
+ * residual.  Optional per-cluster outputs: res_out [4][152][n] (dy, dz, t, u;
+ * NaN where none), vox_out [152][n] (-1 where none), var_out [2][152][n]
+ * (variance of the combined y and z), and slack_out [n] (smallest slack of
+ * the track's |snp| decisions).                                             */
+int ora_residuals(int n, const float *ia, const float *ix, const float *ipar, const float *icov, const int *ist,
+                  const float *ta, const float *tx, const float *tpar, const float *tcov, const int *tst,
+                  const float *cy, const float *cz, const signed char *csec, double bz, int n_threads,
+                  double *sums, double *abs_sums, float *res_out, int *vox_out, float *var_out,
+                  double *slack_out)
+{
+    if (n < 0 || !sums) return -1;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel
+#endif
+    {
+        double (*trd_st)[7] = malloc(sizeof(double[7]) * ORA_TPC_ROWS);
+        double (*trd_c)[15] = malloc(sizeof(double[15]) * ORA_TPC_ROWS);
+        int *trd_ok = malloc(sizeof(int) * ORA_TPC_ROWS);
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 64)
+#endif
+        for (int i = 0; i < n; ++i) {
+            double sI[7] = {ia[i], ix[i]}, sT[7] = {ta[i], tx[i]}, cI[15], cT[15];
+            for (int k = 0; k < 5; ++k) {
+                sI[2 + k] = ipar[(size_t)k * n + i];
+                sT[2 + k] = tpar[(size_t)k * n + i];
+            }
+            for (int k = 0; k < 15; ++k) {
+                cI[k] = icov[(size_t)k * n + i];
+                cT[k] = tcov[(size_t)k * n + i];
+            }
+            const int use = ist[i] == 0 && tst[i] == 0;
+            double slack = INFINITY;
+            /* the TRD refit, inward */
+            int frame = -1;
+            for (int r = ORA_TPC_ROWS - 1; r >= 0; --r) {
+                const int s = csec[(size_t)r * n + i];
+                trd_ok[r] = 0;
+                if (!use || s < 0 || s >= ORA_NSECTOR) continue;
+                if (tpc_carry(sT, cT, &frame, s, tpc_row_x(r), bz, &slack)) continue;
+                memcpy(trd_st[r], sT, sizeof sT);
+                memcpy(trd_c[r], cT, sizeof cT);
+                trd_ok[r] = 1;
+            }
+            /* the ITS refit, outward; combine where both arrived */
+            frame = -1;
+            for (int r = 0; r < ORA_TPC_ROWS; ++r) {
+                const size_t q = (size_t)r * n + i;
+                const int s = csec[q];
+                double o[6];
+                int vox = -1;
+                if (use && s >= 0 && s < ORA_NSECTOR && tpc_carry(sI, cI, &frame, s, tpc_row_x(r), bz, &slack) == 0 &&
+                    trd_ok[r]) {
+                    double a2[2][7], c2[2][15];
+                    memcpy(a2[0], sI, sizeof sI);
+                    memcpy(c2[0], cI, sizeof cI);
+                    memcpy(a2[1], trd_st[r], sizeof sI);
+                    memcpy(c2[1], trd_c[r], sizeof cI);
+                    tpc_combine(a2, c2, cy[q], cz[q], o);
+                    vox = ora_voxel_of(cy[q], cz[q], s, r);
+                }
+                if (res_out)
+                    for (int k = 0; k < 4; ++k) res_out[(size_t)k * ORA_TPC_ROWS * n + q] = vox >= 0 ? (float)o[k] : NAN;
+                if (var_out)
+                    for (int k = 0; k < 2; ++k)
+                        var_out[(size_t)k * ORA_TPC_ROWS * n + q] = vox >= 0 ? (float)o[4 + k] : NAN;
+                if (vox_out) vox_out[q] = vox;
+                if (vox < 0) continue;
+                const double dy = o[0], dz = o[1], t = o[2], u = o[3];
+                const double term[ORA_VOX_SUMS] = {1.0, t, u, t * t, u * u, dy, dz, t * dy, u * dz, dy * dy, dz * dz};
+                double *S = sums + (size_t)vox * ORA_VOX_SUMS;
+                for (int k = 0; k < ORA_VOX_SUMS; ++k) {
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+                    S[k] += term[k];
+                }
+                if (abs_sums) {
+                    double *A = abs_sums + (size_t)vox * ORA_VOX_SUMS;
+                    for (int k = 0; k < ORA_VOX_SUMS; ++k) {
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+                        A[k] += fabs(term[k]);
+                    }
+                }
+            }
+            if (slack_out) slack_out[i] = slack;
+        }
+        free(trd_st);
+        free(trd_c);
+        free(trd_ok);
+    }
+    return 0;
+}
+
+/* The distortion vector of each voxel: least squares of dy_i = Dy - Dx t_i,
+ * dz_i = Dz - Dx u_i.  Eliminating Dy and Dz:
+ *   Dx = -[n (Stdy + Sudz) - St Sdy - Su Sdz] / [n (Stt + Suu) - St^2 - Su^2],
+ *   Dy = (Sdy + St Dx) / n,  Dz = (Sdz + Su Dx) / n.
+ * out[nvox][6] = {Dx, Dy, Dz, n, rms dy, rms dz} (rms of the raw residuals
+ * about their mean); a voxel with fewer than min_count clusters or no spread
+ * in angle gets NaN for Dx, Dy, Dz.                                         */
+int ora_voxel_solve(const double *sums, int nvox, int min_count, double *out)
+{
+    if (!sums || !out || nvox < 0) return -1;
+    for (int v = 0; v < nvox; ++v) {
+        const double *S = sums + (size_t)v * ORA_VOX_SUMS;
+        double *o = out + (size_t)v * 6;
+        const double n = S[0];
+        o[3] = n;
+        o[0] = o[1] = o[2] = o[4] = o[5] = NAN;
+        if (n < (double)(min_count > 1 ? min_count : 1)) continue;
+        o[4] = sqrt(fmax(S[9] / n - (S[5] / n) * (S[5] / n), 0.0));
+        o[5] = sqrt(fmax(S[10] / n - (S[6] / n) * (S[6] / n), 0.0));
+        const double den = n * (S[3] + S[4]) - S[1] * S[1] - S[2] * S[2];
+        if (!(den > 1e-12 * n * n)) continue;
+        const double dx = -(n * (S[7] + S[8]) - S[1] * S[5] - S[2] * S[6]) / den;
+        o[0] = dx;
+        o[1] = (S[5] + S[1] * dx) / n;
+        o[2] = (S[6] + S[2] * dx) / n;
     }
     return 0;
 }

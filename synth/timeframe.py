@@ -69,14 +69,15 @@ def _local_xy(s, phi0, k, a):
     return ch * np.cos(phi0 + half - a), ch * np.sin(phi0 + half - a)
 
 
-def _cross_plane(phi0, k, a, xp):
-    """Smallest arc length at which the helix crosses local x = xp, by Newton.
+def _cross_plane(phi0, k, a, xp, s0=None):
+    """Smallest arc length at which the helix crosses local x = xp, by Newton
+    (started from s0 when given, e.g. the crossing of a nearby plane).
 
     Returns (s, ok).  ok is False where the helix turns back before reaching
     the plane or the iteration did not converge.
     """
     d0 = np.cos(phi0 - a)
-    s = xp / np.maximum(d0, 0.3)
+    s = xp / np.maximum(d0, 0.3) if s0 is None else np.asarray(s0, dtype=np.float64).copy()
     smax = np.where(np.abs(k) > 0, math.pi / np.maximum(np.abs(k), 1e-12), 1e9)
     for _ in range(40):
         xl, _ = _local_xy(s, phi0, k, a)
@@ -87,7 +88,7 @@ def _cross_plane(phi0, k, a, xp):
         s = np.clip(s - (xl - xp) / der, 0.0, smax)
     xl, _ = _local_xy(s, phi0, k, a)
     outgoing = np.cos(phi0 + k * s - a) > 0.05
-    ok = (np.abs(xl - xp) < 1e-7 * max(xp, 1.0)) & outgoing & (s > 0)
+    ok = (np.abs(xl - xp) < 1e-7 * np.maximum(xp, 1.0)) & outgoing & (s > 0)
     return s, ok
 
 

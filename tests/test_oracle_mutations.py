@@ -11,6 +11,7 @@ import pytest
 from oracle import oracle as O
 import test_oracle_pins as P
 import test_oracle_refit_pins as R
+import test_oracle_residual_pins as Q
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(os.path.dirname(HERE), "oracle", "trd_oracle.c")
@@ -52,6 +53,17 @@ PINNED = [
      "h.chi2 += ora_update(h.st, h.c, l + 1, m5, 0);"),
     ("refit stays in its sector", "            target = T->ch[j] / (ORA_NSTACK * ORA_NLAYER);",
      "            target = h.sector;"),
+    # residuals in TPC sub-volumes and the distortion vector (Sec. 2, steps 4-5)
+    ("residual sign", "out[0] = (double)ycl - my;", "out[0] = my - (double)ycl;"),
+    ("y slope without 1/cos", "out[2] = f / r;", "out[2] = f;"),
+    ("z slope without 1/cos", "out[3] = tl / r;", "out[3] = tl;"),
+    ("combination drops the TRD refit", "const double b0 = g[0][0] + g[1][0], b1 = g[0][1] + g[1][1];",
+     "const double b0 = g[0][0] + g[0][0], b1 = g[0][1] + g[0][1];"),
+    ("combined variance of one refit", "out[4] = W11 / dW;", "out[4] = c[0][0];"),
+    ("voxel side from y", "const int side = z < 0.0f ? 1 : 0;", "const int side = y < 0.0f ? 1 : 0;"),
+    ("y bin without offset", "const float v = u + T;", "const float v = u;"),
+    ("solve sign of Dx", "const double dx = -(n * (S[7] + S[8])", "const double dx = (n * (S[7] + S[8])"),
+    ("solve drops the angular mean", "o[1] = (S[5] + S[1] * dx) / n;", "o[1] = S[5] / n;"),
 ]
 
 UNPINNED = [
@@ -84,6 +96,12 @@ PINS = [
     lambda: R.test_inward_refit_undoes_the_outward_material(),
     lambda: R.test_refit_output_frame_is_the_layer0_sector(),
     lambda: R.test_refit_skips_unmatched_and_invalid_tracks(),
+    lambda: Q.test_voxel_of_hand_placed_clusters(),
+    lambda: Q.test_no_distortion_exact_refits_give_zero_residuals(),
+    lambda: Q.test_residuals_follow_the_injected_field(),
+    lambda: Q.test_combined_estimate_has_unit_pulls(),
+    lambda: Q.test_voxel_solve_equals_least_squares(),
+    lambda: Q.test_map_recovers_a_uniform_displacement(),
 ]
 
 
