@@ -49,18 +49,39 @@ FOLLOW_BYTES_PER_SEED = SEED_BYTES + RESULT_BYTES + RECORD_BYTES * IN_ROAD_PER_S
 # layers; six layers.
 FOLLOW_FLOPS_PER_SEED = 3700
 L2_FLUSH_BYTES = 512 << 20
-# DRAM bytes (read + write) of one trd_follow call (k_seed_prepare 17.6 MB +
-# k_follow 56.8 MB) on this workload from one ncu capture of each kernel, valid
+# TRD-only refit (trd_refit), algorithmic bytes: per track the follower
+# result fields it reads (alpha, x, 5 parameters, 5 covariance diagonal
+# terms, status, 6 ids: 76 B) and the refit it writes (alpha, x, 5
+# parameters, 15 covariance terms, chi2, n_upd, status: 100 B); per attached
+# tracklet the 6 words it gathers (chamber, y, z, vyy, vzz, vyz: 24 B).
+REFIT_BYTES_PER_TRACK = 76 + 100
+REFIT_BYTES_PER_TRACKLET = 24
+# FP32 operations per refitted layer (model: transport ~150, Joseph update
+# ~250, material ~60)
+REFIT_FLOPS_PER_LAYER = 460
+# DRAM bytes (read + write) of one k_refit launch on the 200k-seed timeframe
+# from one ncu capture (39.05 MB read, 0.85 MB written: the 20 MB of output
+# is still in L2 when the kernel ends), valid only for the source measured.
+REFIT_TRAFFIC = {"source_sha256_16": "cdaab0d31a37f941", "bytes": 39.90e6}
+# DRAM bytes (read + write) of one trd_follow call (k_seed_prepare 17.62 MB +
+# k_follow 56.31 MB) on this workload from one ncu capture of each kernel, valid
 # only for the kernel source it was measured on: reported as null once
-# follow.cu or trd_device.cuh change.
-FOLLOW_TRAFFIC = {"source_sha256_16": "2a6233ea955bd7c3", "bytes": 74.37e6}
+# follow.cu, trd_device.cuh or track_model.cuh change.
+FOLLOW_TRAFFIC = {"source_sha256_16": "c0e9326825a8b5d8", "bytes": 73.93e6}
+
+
+def _source_hash(files=("follow.cu", "trd_device.cuh", "track_model.cuh")):
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2003_03174_b300", "csrc")
+    data = b"".join(open(os.path.join(csrc, f), "rb").read() for f in files)
+    return hashlib.sha256(data).hexdigest()[:16]
 
 
 def _follow_source_hash():
-    import hashlib
-    csrc = os.path.join(ROOT, "paper_2003_03174_b300", "csrc")
-    data = b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("follow.cu", "trd_device.cuh"))
-    return hashlib.sha256(data).hexdigest()[:16]
+    return _source_hash()
+
+
+REFIT_SOURCES = ("refit.cu", "trd_device.cuh", "track_model.cuh")
 
 
 def _dist():
@@ -349,6 +370,7 @@ def run_ours(args):
     roof["alu_check"] = alu
     launches_per_step = 7  # count, 3 scan kernels, scatter, seed prepare, follow (one graph)
     clocks = clk.summary()
+    refit = time_refit(ctx, res, trk, tf.params, stream, flush, args.steps, args.warmup, hbm, fp32_peak)
 
     if rank == 0:
         line = {
@@ -375,6 +397,7 @@ def run_ours(args):
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
             "seeds_per_s": n * ws * args.steps / total_s,
+            "refit": refit,
         }
         if ws == 1 and not args.no_cpu_baseline:
             cb = cpu_baseline(tf, args.cpu_sample)
@@ -383,6 +406,47 @@ def run_ours(args):
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def time_refit(ctx, res, trk, params, stream, flush, steps, warmup, hbm, fp32_peak):
+    """The TRD-only refit (trd_refit, one k_refit launch) of the follower's
+    results, timed alone with CUDA events on its stream, L2 flushed before
+    each launch; its roofline against the measured HBM and FP32 peaks."""
+    import torch
+    from paper_2003_03174_b300 import trd
+    n = int(res["alpha"].shape[0])
+    out = trd.alloc_refit(n, res["alpha"].device)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        for _ in range(max(warmup, 3)):
+            ctx.refit(res, trk, params, out=out, stream=stream)
+        for k in range(steps):
+            flush.add_(1.0)
+            ev[k][0].record(stream)
+            ctx.refit(res, trk, params, out=out, stream=stream)
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    ntrk = res["n_trk"].clamp(min=0).sum().item()
+    st = out["status"]
+    refitted = int((st == 0).sum().item())
+    bytes_ = n * REFIT_BYTES_PER_TRACK + ntrk * REFIT_BYTES_PER_TRACKLET
+    # layers visited by a refitted track: from its outermost tracklet to layer 0
+    ids = res["tracklet_id"]
+    top = torch.where(ids >= 0, torch.arange(6, device=ids.device)[:, None], -1).max(0).values
+    layers = int((top[st == 0] + 1).sum().item())
+    flops = layers * REFIT_FLOPS_PER_LAYER
+    achieved = bytes_ / (ms / 1e3) / 1e9
+    peak = hbm if hbm else 6400.0
+    return {"metric": "refitted tracks/s", "value": refitted / (ms / 1e3), "ms": ms,
+            "tracks": n, "refitted": refitted, "launches": 1,
+            "roofline": {"bound": "hbm", "kernel": "k_refit", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": REFIT_TRAFFIC["bytes"] if n == 200_000 and
+                         _source_hash(REFIT_SOURCES) == REFIT_TRAFFIC["source_sha256_16"] else None,
+                         "algorithmic_bytes_per_launch": int(bytes_),
+                         "alu_check": {"achieved": flops / (ms / 1e3) / 1e12, "peak": fp32_peak,
+                                       "unit": "TFLOP/s", "frac": flops / (ms / 1e3) / 1e12 / fp32_peak}}}
 
 
 def run_batched(args):
@@ -460,6 +524,142 @@ def run_batched(args):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+# Residual collection (Sec. 2, steps 4-5), algorithmic bytes per track: the
+# two refit states read (alpha, x, 5 parameters, 15 covariance terms,
+# status: 92 B each) and the 152 rows of clusters (y, z: 8 B; sector: 1 B);
+# the 11 int64 sums a cluster updates live in the L2-resident voxel array
+# (36 MB) and are not HBM traffic.
+RES_BYTES_PER_TRACK = 2 * 92 + 152 * 9
+# FP32 operations per contributing cluster (model: two helix transports with
+# their covariance, ~170 each; the combination, ~60; slopes, binning and
+# fixed-point conversion, ~20)
+RES_FLOPS_PER_CLUSTER = 420
+
+
+def run_residuals(args):
+    """One distortion map (Sec. 2: a map needs at least 450k matched tracks):
+    450,000 tracks, ~61 M TPC clusters.  A step zeroes the voxel sums,
+    collects the residual of every cluster to the combined ITS + TRD refits
+    (trd_residuals) and solves every voxel (trd_voxel_solve)."""
+    from synth import tpc
+    w = tpc.make_map_workload(args.map_tracks, seed=0, workers=os.cpu_count())  # spawn pool before any CUDA call
+    n = w.n_tracks
+    n_cl_in = w.n_clusters
+    cb = None
+    if not args.no_cpu_baseline:
+        cb = residual_cpu_baseline(w, args.cpu_sample_tracks)
+    import torch
+    from paper_2003_03174_b300 import trd
+    dev = torch.device("cuda", 0)
+    ctx = trd.Context(0)
+    its, trf, cl = trd.to_device(w.its, dev), trd.to_device(w.trd, dev), trd.to_device(w.clusters, dev)
+    sums = torch.zeros(trd.N_VOXELS, trd.VOX_SUMS, dtype=torch.int64, device=dev)
+    vmap = torch.empty(trd.N_VOXELS, 6, dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    def step():
+        sums.zero_()
+        ctx.residuals(its, trf, cl, w.bz, sums=sums, stream=stream)
+        ctx.voxel_solve(sums, args.min_count, out=vmap, stream=stream)
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    with ClockSampler(0) as clk:
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                step()
+            torch.cuda.synchronize()
+            for k in range(args.steps):
+                e = ev[k]
+                e[0].record(stream)
+                sums.zero_()
+                e[1].record(stream)
+                ctx.residuals(its, trf, cl, w.bz, sums=sums, stream=stream)
+                e[2].record(stream)
+                ctx.voxel_solve(sums, args.min_count, out=vmap, stream=stream)
+                e[3].record(stream)
+        torch.cuda.synchronize()
+    step_ms = [e[0].elapsed_time(e[3]) for e in ev]
+    res_ms = [e[1].elapsed_time(e[2]) for e in ev]
+    solve_ms = [e[2].elapsed_time(e[3]) for e in ev]
+    n_cl = int(sums[:, 0].sum().item())
+    solved = int((~torch.isnan(vmap[:, 0])).sum().item())
+    t_step = statistics.mean(step_ms) / 1e3
+
+    # end to end through the binding with host buffers: pinned inputs -> device,
+    # the step, the map -> pinned host, every step
+    h_in = [{k: torch.from_numpy(v).pin_memory() for k, v in d.items()} for d in (w.its, w.trd, w.clusters)]
+    d_in = [its, trf, cl]
+    h_map = torch.empty(trd.N_VOXELS, 6, dtype=torch.float32).pin_memory()
+    h2d = sum(v.numel() * v.element_size() for d in h_in for v in d.values())
+    d2h = h_map.numel() * 4
+    e_steps = max(3, args.steps)
+    with torch.cuda.stream(stream):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(e_steps):
+            for hd, dd in zip(h_in, d_in):
+                for k in hd:
+                    dd[k].copy_(hd[k], non_blocking=True)
+            step()
+            h_map.copy_(vmap, non_blocking=True)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    t_e2e = e0.elapsed_time(e1) / 1e3 / e_steps
+
+    peaks = _peaks()
+    hbm = peaks.get("hbm_gbs") or 6400.0
+    fp32 = ctx.fp32_peak_tflops()
+    t_res = statistics.mean(res_ms) / 1e3
+    achieved = n * RES_BYTES_PER_TRACK / t_res / 1e9
+    line = {
+        "metric": "TPC cluster residuals/s", "workload": "residuals", "value": n_cl / t_step,
+        "unit": "clusters/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (truth helices through 152 pad rows, smooth space-charge-like "
+                                "displacement, 0.1 cm smearing; honest ITS and TRD refit states)",
+        "config": {"workload": f"distortion map: {n} tracks, {n_cl_in} clusters, {trd.N_VOXELS} voxels "
+                               f"(36 sectors x 152 rows x 15 y/x x 5 z/x), min {args.min_count} per voxel",
+                   "l2": "inputs (~0.7 GB) larger than L2; the 36 MB voxel sums are zeroed each step",
+                   "step": "zero sums + trd_residuals + trd_voxel_solve"},
+        "tracks_per_s": n / t_step, "maps_per_s": 1.0 / t_step,
+        "clusters_used": n_cl, "voxels_solved": solved,
+        "residuals_ms": 1e3 * t_res, "solve_ms": statistics.mean(solve_ms),
+        "roofline": {"bound": "hbm", "kernel": "k_residuals", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None,
+                     "algorithmic_bytes_per_launch": n * RES_BYTES_PER_TRACK,
+                     "alu_check": {"achieved": n_cl * RES_FLOPS_PER_CLUSTER / t_res / 1e12, "peak": fp32,
+                                   "unit": "TFLOP/s",
+                                   "frac": n_cl * RES_FLOPS_PER_CLUSTER / t_res / 1e12 / fp32},
+                     "atomics_per_s": 11 * n_cl / t_res},
+        "e2e": {"value": n_cl / t_e2e, "unit": "clusters/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h),
+                "path": "pinned host inputs -> device, zero + trd_residuals + trd_voxel_solve, map -> pinned host"},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk.summary(),
+    }
+    if cb is not None:
+        line["cpu_baseline"] = cb
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def residual_cpu_baseline(w, sample_tracks):
+    """The FP64 oracle's residual collection and solve on the host cores, on
+    the first `sample_tracks` tracks of the map workload."""
+    from oracle import oracle as O
+    m = min(sample_tracks, w.n_tracks)
+    part = lambda d: {k: v[..., :m] for k, v in d.items()}  # noqa: E731
+    its, trf = part(w.its), part(w.trd)
+    cl = {k: v[:, :m] for k, v in w.clusters.items()}
+    t0 = time.perf_counter()
+    r = O.residuals(its, trf, cl, w.bz)
+    O.voxel_solve(r["sums"], 50)
+    dt = time.perf_counter() - t0
+    n_cl = int(r["sums"][:, 0].sum())
+    return {"value": n_cl / dt, "unit": "clusters/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"first {m} of {w.n_tracks} tracks ({n_cl} clusters); {dt:.2f} s"}
 
 
 def _pct(v, q):
@@ -611,7 +811,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="time separate launches instead of the graph")
-    ap.add_argument("--workload", choices=["timeframe", "batched", "served"], default="timeframe")
+    ap.add_argument("--workload", choices=["timeframe", "batched", "served", "residuals"], default="timeframe")
+    ap.add_argument("--map-tracks", type=int, default=450_000, help="tracks of the residual workload")
+    ap.add_argument("--min-count", type=int, default=50, help="clusters a voxel needs to be solved")
+    ap.add_argument("--cpu-sample-tracks", type=int, default=60_000)
     ap.add_argument("--n-tf", type=int, default=64)
     ap.add_argument("--association", type=int, default=0,
                     help="interactions per timeframe (per-interaction association); 0 = off")
@@ -631,6 +834,8 @@ def main():
         return run_batched(args)
     if args.workload == "served":
         return run_served(args)
+    if args.workload == "residuals":
+        return run_residuals(args)
     return run_ours(args)
 
 

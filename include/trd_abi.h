@@ -223,6 +223,116 @@ TRD_API int trd_follow_tuned(trd_ctx_t *ctx, const trd_seeds_t *seeds, const trd
                              const trd_params_t *params, trd_results_t *out, void *stream,
                              const trd_launch_t *launch);
 
+/* ---- TRD-only refit (Sec. 2, step 3) ----------------------------------------
+ * The space-point calibration refits each matched track twice without the TPC
+ * clusters: from the ITS, and from TRD and TOF.  trd_refit is the TRD half
+ * (no TOF point is modelled).  For every track with at least two tracklets
+ * whose follower status lacks TRD_ST_SEED_INVALID:
+ *   1. prior: the follower's final state, its covariance reduced to the
+ *      diagonal and multiplied by cov_scale (> 0; e.g. 100 widens every
+ *      error tenfold), so little of the TPC-derived information is kept
+ *      (FP32: up to cov_scale ~1e3 the results stay within 1e-4 of the FP64
+ *      refit; a wider prior costs accuracy in the first update);
+ *   2. from the outermost layer with a tracklet down to layer 0: transport
+ *      to the layer plane (entering the tracklet's sector, or the neighbour
+ *      sector at the azimuthal edge of a layer without tracklet), Kalman
+ *      update with the tracklet (same pad-tilt model, res_mode and Joseph
+ *      form as trd_follow), then, with material_on, the layer's material
+ *      with the mean energy loss added back;
+ *   3. output: the state at the plane of layer 0 (x = 300 cm) in its sector
+ *      frame, the covariance, the sum of the update chi2, the number of
+ *      updates and a status.
+ * tracks (read only, device): results of trd_follow for n tracks (alpha, x,
+ *   par, cov diagonal, status, tracklet_id are read; the other fields are
+ *   ignored).  tracklets (read only, device): the arrays the ids refer to
+ *   (chamber, y, z, vyy, vzz, vyz; dy and trigger are not read).
+ *   params: bz, res_mode and material_on are used.
+ * out (device, caller-owned): alpha, x [n]; par [5][n]; cov [15][n];
+ *   chi2 [n]; n_upd, status [n] (int32).  status: TRD_RF_OK, TRD_RF_PROP_FAIL
+ *   (|snp| limit reached; the state is as far as it was carried), or
+ *   TRD_RF_SKIPPED (fewer than two tracklets, an invalid seed, or a tracklet
+ *   id or chamber outside the tracklet arrays; the output is the input
+ *   state with a zero covariance).
+ * Asynchronous on `stream`.  Errors: TRD_EINVAL (NULL pointers, n < 0,
+ * cov_scale not finite and positive), TRD_ECUDA.                             */
+#define TRD_RF_OK 0
+#define TRD_RF_PROP_FAIL 1
+#define TRD_RF_SKIPPED 8
+
+typedef struct {
+    float *alpha, *x, *par, *cov, *chi2;
+    int32_t *n_upd, *status;
+} trd_refit_t;
+
+TRD_API int trd_refit(trd_ctx_t *ctx, const trd_results_t *tracks, int32_t n,
+                      const trd_tracklets_t *tracklets, const trd_params_t *params, float cov_scale,
+                      trd_refit_t *out, void *stream);
+
+/* ---- residuals in TPC sub-volumes and the distortion map (Sec. 2, steps 4
+ * and 5) ----------------------------------------------------------------------
+ * The calibration compares each distorted TPC cluster with the weighted
+ * combination of the ITS refit and the TRD-only refit (trd_refit) of its
+ * track, collects the residuals per TPC sub-volume, and derives one
+ * distortion vector per sub-volume.
+ *
+ * Geometry (readings; the paper gives none): TRD_TPC_ROWS pad rows with
+ * centres x_r = 85 + 160 (r + 1/2) / 152 cm, rounded to float; the 18
+ * sectors of the TRD's segmentation; sub-volume (voxel) index
+ *   (((side * 18 + sector) * 152 + row) * 15 + iy) * 5 + iz,
+ * side = 1 for z < 0; iy = floor((y/x_r + tan 10 deg) * 15 / (2 tan 10 deg)),
+ * iz = floor(|z|/x_r * 5), both clamped into range, evaluated in FP32 with
+ * correctly rounded operations in that order.
+ *
+ * trd_residuals: for each of n tracks with both refit statuses 0, each
+ * refit is carried along the track to every pad row with a cluster: to the
+ * row plane in its current frame, and where the cluster lies in another
+ * sector, rotated there into the cluster's sector and carried to the plane
+ * again (helix transport, no material in the gas).  At each cluster the two
+ * (y, z) estimates are combined with their inverse 2x2 covariances, sin(phi)
+ * and tan(lambda) with their inverse variances; the residual (dy, dz) =
+ * cluster - combination, with the combination's slopes t = tan(phi) and
+ * u = tan(lambda) / cos(phi), is added to the cluster's voxel.
+ *   its, trd (read only, device): states at any radius and frame (alpha, x
+ *     [n]; par [5][n]; cov [15][n]; status [n]) -- e.g. the output of
+ *     trd_refit for the TRD side.
+ *   clusters (read only, device): y, z float [152][n] (local frame of the
+ *     cluster's sector, z global); sector int8 [152][n], 0..17, any other
+ *     value = no cluster on that row.  Non-finite y or z: no cluster.
+ *   voxel_sums (device, caller-owned, accumulated into, zero it first):
+ *     int64 [TRD_N_VOXELS][TRD_VOX_SUMS] = n, St, Su, Stt, Suu, Sdy, Sdz,
+ *     Stdy, Sudz, Sdydy, Sdzdz; every sum except n holds round(v * 2^24) of
+ *     each FP32 term (exact, order-independent integer sums).
+ *   cluster_res (optional device output, NULL to skip): float [4][152][n] =
+ *     dy, dz, t, u per cluster, NaN where there is none.
+ * trd_voxel_solve: per voxel with at least min_count clusters, the least
+ * squares solution of dy_i = Dy - Dx t_i, dz_i = Dz - Dx u_i (a cluster at
+ * row x_r was freed at the track point x_r - Dx and moved by (Dy, Dz));
+ * map (device, caller-owned) float [TRD_N_VOXELS][6] = Dx, Dy, Dz, n,
+ * rms dy, rms dz (NaN where undetermined).
+ * Both asynchronous on `stream`.  Errors: TRD_EINVAL (NULL pointers, n < 0,
+ * n * 152 beyond int32), TRD_ECUDA.                                          */
+#define TRD_TPC_ROWS 152
+#define TRD_VOX_Y_BINS 15
+#define TRD_VOX_Z_BINS 5
+#define TRD_N_VOXELS (2 * 18 * TRD_TPC_ROWS * TRD_VOX_Y_BINS * TRD_VOX_Z_BINS)
+#define TRD_VOX_SUMS 11
+
+typedef struct {
+    const float *alpha, *x, *par, *cov;
+    const int32_t *status;
+} trd_states_t;
+
+typedef struct {
+    const float *y, *z;
+    const int8_t *sector;
+} trd_tpc_clusters_t;
+
+TRD_API int trd_residuals(trd_ctx_t *ctx, int32_t n, const trd_states_t *its, const trd_states_t *trd,
+                          const trd_tpc_clusters_t *clusters, float bz, int64_t *voxel_sums, float *cluster_res,
+                          void *stream);
+TRD_API int trd_voxel_solve(trd_ctx_t *ctx, const int64_t *voxel_sums, int32_t min_count, float *map,
+                            void *stream);
+
 /* ---- batches of timeframes (Sec. 3.1: Run 3 processes time frames of many
  * collisions; here many time frames at once) ----------------------------------
  * trd_batch_create: prepare one CUDA graph that, for n_tf timeframes stored

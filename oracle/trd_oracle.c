@@ -951,11 +951,11 @@ int ora_voxel_of(float y, float z, int sector, int row)
     const float ys = (float)ORA_VOX_Y / (2.0f * T);
     const float u = y / xr;
     const float v = u + T;
-    const float fy = v * ys;
+    const float fy = fminf(fmaxf(v * ys, -1.0f), (float)ORA_VOX_Y); /* bounded before the cast */
     int iy = (int)floorf(fy);
     iy = iy < 0 ? 0 : (iy >= ORA_VOX_Y ? ORA_VOX_Y - 1 : iy);
     const float w = fabsf(z) / xr;
-    const float fz = w * (float)ORA_VOX_Z;
+    const float fz = fminf(w * (float)ORA_VOX_Z, (float)ORA_VOX_Z);
     int iz = (int)floorf(fz);
     iz = iz < 0 ? 0 : (iz >= ORA_VOX_Z ? ORA_VOX_Z - 1 : iz);
     const int side = z < 0.0f ? 1 : 0;
@@ -1016,7 +1016,8 @@ static void tpc_combine(const double a[2][7], const double c[2][15], float ycl, 
  * absolute values, for tolerances).  Inputs are the FP32 arrays the library
  * reads: refit states (alpha, x [n], par [5][n], cov [15][n], status [n]; only
  * tracks with both statuses 0 contribute) and clusters (y, z [152][n], sector
- * int8 [152][n], -1 = none).  Per track, the TRD refit is carried inward
+ * int8 [152][n], -1 = none; a non-finite y or z is no cluster either).  Per
+ * track, the TRD refit is carried inward
  * through the rows with a cluster (151 down to 0) and the ITS refit outward
  * (0 up to 151), each with tpc_carry; a cluster where both arrive gives a
  * residual.  Optional per-cluster outputs: res_out [4][152][n] (dy, dz, t, u;
@@ -1056,9 +1057,10 @@ int ora_residuals(int n, const float *ia, const float *ix, const float *ipar, co
             /* the TRD refit, inward */
             int frame = -1;
             for (int r = ORA_TPC_ROWS - 1; r >= 0; --r) {
-                const int s = csec[(size_t)r * n + i];
+                const size_t q = (size_t)r * n + i;
+                const int s = csec[q];
                 trd_ok[r] = 0;
-                if (!use || s < 0 || s >= ORA_NSECTOR) continue;
+                if (!use || s < 0 || s >= ORA_NSECTOR || !isfinite(cy[q]) || !isfinite(cz[q])) continue;
                 if (tpc_carry(sT, cT, &frame, s, tpc_row_x(r), bz, &slack)) continue;
                 memcpy(trd_st[r], sT, sizeof sT);
                 memcpy(trd_c[r], cT, sizeof cT);
@@ -1071,8 +1073,8 @@ int ora_residuals(int n, const float *ia, const float *ix, const float *ipar, co
                 const int s = csec[q];
                 double o[6];
                 int vox = -1;
-                if (use && s >= 0 && s < ORA_NSECTOR && tpc_carry(sI, cI, &frame, s, tpc_row_x(r), bz, &slack) == 0 &&
-                    trd_ok[r]) {
+                if (use && s >= 0 && s < ORA_NSECTOR && isfinite(cy[q]) && isfinite(cz[q]) &&
+                    tpc_carry(sI, cI, &frame, s, tpc_row_x(r), bz, &slack) == 0 && trd_ok[r]) {
                     double a2[2][7], c2[2][15];
                     memcpy(a2[0], sI, sizeof sI);
                     memcpy(c2[0], cI, sizeof cI);

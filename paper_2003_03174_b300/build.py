@@ -21,7 +21,9 @@ FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr", "-Xcompil
 # The follower needs no correctly rounded division or square root: positions
 # are carried as double-floats and every quotient feeds a derivative, a window
 # or a chi2 where 2-ulp errors are far inside the parity tolerances.
-PER_FILE = {"follow.cu": ["-prec-div=false", "-prec-sqrt=false"]}
+PER_FILE = {"follow.cu": ["-prec-div=false", "-prec-sqrt=false"],
+            "refit.cu": ["-prec-div=false", "-prec-sqrt=false"],
+            "residuals.cu": ["-prec-div=false", "-prec-sqrt=false"]}
 
 
 def sources():

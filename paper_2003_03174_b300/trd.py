@@ -24,7 +24,10 @@ EXPORTED = [
     "trd_geometry", "trd_version", "trd_index_copy_out", "trd_batch_create", "trd_batch_run",
     "trd_batch_free", "trd_server_create", "trd_server_submit", "trd_server_poll", "trd_server_wait",
     "trd_server_stats", "trd_server_destroy", "trd_index_build_noalloc", "trd_measure_fp32_peak",
+    "trd_refit", "trd_residuals", "trd_voxel_solve",
 ]
+TPC_ROWS, VOX_Y_BINS, VOX_Z_BINS, VOX_SUMS = 152, 15, 5, 11
+N_VOXELS = 2 * 18 * TPC_ROWS * VOX_Y_BINS * VOX_Z_BINS
 
 
 class TrdError(RuntimeError):
@@ -57,6 +60,18 @@ class Launch(C.Structure):
 class Results(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in ("alpha", "x", "par", "cov", "chi2", "n_trk", "n_miss",
                                           "status", "tracklet_id")]
+
+
+class RefitOut(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ("alpha", "x", "par", "cov", "chi2", "n_upd", "status")]
+
+
+class States(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ("alpha", "x", "par", "cov", "status")]
+
+
+class TpcClusters(C.Structure):
+    _fields_ = [("y", C.c_void_p), ("z", C.c_void_p), ("sector", C.c_void_p)]
 
 
 class ServerCfg(C.Structure):
@@ -108,6 +123,11 @@ def lib():
         L.trd_server_destroy.argtypes = [vp]
         L.trd_index_build_noalloc.argtypes = [C.POINTER(Tracklets), f32, vp, vp, vp, vp]
         L.trd_measure_fp32_peak.argtypes = [vp, C.POINTER(C.c_double)]
+        L.trd_refit.argtypes = [vp, C.POINTER(Results), i32, C.POINTER(Tracklets), C.POINTER(Params),
+                                f32, C.POINTER(RefitOut), vp]
+        L.trd_residuals.argtypes = [vp, i32, C.POINTER(States), C.POINTER(States), C.POINTER(TpcClusters), f32,
+                                    vp, vp, vp]
+        L.trd_voxel_solve.argtypes = [vp, vp, i32, vp, vp]
         L.trd_version.restype = C.c_char_p
         for fn in EXPORTED:
             if fn != "trd_version":
@@ -176,6 +196,15 @@ def alloc_results(n: int, device="cuda"):
 def results_struct(r: dict) -> Results:
     return Results(*[_ptr(r[k]) for k in ("alpha", "x", "par", "cov", "chi2", "n_trk", "n_miss",
                                           "status", "tracklet_id")])
+
+
+def alloc_refit(n: int, device="cuda"):
+    import torch
+    f = dict(dtype=torch.float32, device=device)
+    i = dict(dtype=torch.int32, device=device)
+    return dict(alpha=torch.empty(n, **f), x=torch.empty(n, **f), par=torch.empty(5, n, **f),
+                cov=torch.empty(15, n, **f), chi2=torch.empty(n, **f), n_upd=torch.empty(n, **i),
+                status=torch.empty(n, **i))
 
 
 def to_device(arrays: dict, device="cuda") -> dict:
@@ -391,6 +420,50 @@ class Context:
                                   C.byref(rs), _stream_handle(stream))
             _check("trd_follow", rc)
         return results
+
+    def refit(self, tracks: dict, tracklets: dict, params: dict, cov_scale: float = 100.0,
+              out: dict | None = None, stream=None) -> dict:
+        """TRD-only refit (trd_refit) of the follower's results `tracks`
+        against the device tracklet arrays their ids refer to."""
+        n = int(tracks["alpha"].shape[0])
+        if out is None:
+            out = alloc_refit(n, device=tracks["alpha"].device)
+        rs = results_struct(tracks)
+        ts, ps = tracklets_struct(tracklets), params_struct(params)
+        os_ = RefitOut(*[_ptr(out[k]) for k in ("alpha", "x", "par", "cov", "chi2", "n_upd", "status")])
+        rc = lib().trd_refit(self.handle, C.byref(rs), n, C.byref(ts), C.byref(ps), float(cov_scale),
+                             C.byref(os_), _stream_handle(stream))
+        _check("trd_refit", rc)
+        return out
+
+    def residuals(self, its: dict, trd: dict, clusters: dict, bz: float, sums=None,
+                  cluster_res: bool = False, stream=None):
+        """Accumulate the residuals of the tracks' TPC clusters into the voxel
+        sums (trd_residuals; int64 [N_VOXELS, 11], zeroed here when not
+        given).  Returns the sums, and with cluster_res the per-cluster
+        (dy, dz, t, u) float [4, 152, n]."""
+        import torch
+        n = int(its["alpha"].shape[0])
+        dev = its["alpha"].device
+        if sums is None:
+            sums = torch.zeros(N_VOXELS, VOX_SUMS, dtype=torch.int64, device=dev)
+        res = torch.empty(4, TPC_ROWS, n, dtype=torch.float32, device=dev) if cluster_res else None
+        st = [States(*[_ptr(d[k]) for k in ("alpha", "x", "par", "cov", "status")]) for d in (its, trd)]
+        cl = TpcClusters(_ptr(clusters["y"]), _ptr(clusters["z"]), _ptr(clusters["sector"]))
+        rc = lib().trd_residuals(self.handle, n, C.byref(st[0]), C.byref(st[1]), C.byref(cl), float(bz),
+                                 _ptr(sums), _ptr(res), _stream_handle(stream))
+        _check("trd_residuals", rc)
+        return (sums, res) if cluster_res else sums
+
+    def voxel_solve(self, sums, min_count: int = 10, out=None, stream=None):
+        """Distortion vector per voxel (trd_voxel_solve): float [N_VOXELS, 6]
+        = Dx, Dy, Dz, n, rms dy, rms dz."""
+        import torch
+        if out is None:
+            out = torch.empty(N_VOXELS, 6, dtype=torch.float32, device=sums.device)
+        rc = lib().trd_voxel_solve(self.handle, _ptr(sums), int(min_count), _ptr(out), _stream_handle(stream))
+        _check("trd_voxel_solve", rc)
+        return out
 
     def batch_create(self, seeds: dict, tracklets: dict, seed_offsets, tracklet_offsets,
                      params: dict, results: dict, y_bin_width: float = 0.0,

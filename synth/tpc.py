@@ -147,3 +147,37 @@ def make_residual_workload(n_tracks: int, seed: int = 0, distorted: bool = True,
         st["status"][rng.uniform(0, 1, n) < fail_frac / 2] = 1
     return ResidualWorkload(its=its, trd=trd, clusters=dict(y=cy, z=cz, sector=cs), truth=truth, bz=bz,
                             applied=dict(dx=app[0], dy=app[1], dz=app[2]))
+
+
+def _chunk(args):
+    n, seed, kw = args
+    return make_residual_workload(n, seed=seed, **kw)
+
+
+def concat_workloads(parts) -> ResidualWorkload:
+    """Tracks of several workloads side by side (same field, same bz)."""
+    cat = lambda key, d: np.concatenate([getattr(p, d)[key] for p in parts], axis=-1)  # noqa: E731
+    its = {k: cat(k, "its") for k in parts[0].its}
+    trd = {k: cat(k, "trd") for k in parts[0].trd}
+    cl = {k: cat(k, "clusters") for k in parts[0].clusters}
+    truth = {k: cat(k, "truth") for k in parts[0].truth}
+    app = {k: cat(k, "applied") for k in parts[0].applied}
+    return ResidualWorkload(its=its, trd=trd, clusters=cl, truth=truth, bz=parts[0].bz, applied=app)
+
+
+def make_map_workload(n_tracks: int = 450_000, seed: int = 0, chunk: int = 15_000, workers: int = 0,
+                      **kw) -> ResidualWorkload:
+    """The tracks of one distortion map (Sec. 2: a map needs at least 450k
+    matched tracks), drawn in chunks of `chunk` tracks (chunk k seeded with
+    seed * 100003 + k) by a spawn-started process pool."""
+    import multiprocessing as mp
+    import os
+    sizes = [min(chunk, n_tracks - a) for a in range(0, n_tracks, chunk)]
+    jobs = [(m, seed * 100003 + k, kw) for k, m in enumerate(sizes)]
+    workers = workers or min(len(jobs), os.cpu_count() or 1)
+    if workers <= 1 or len(jobs) == 1:
+        parts = [_chunk(j) for j in jobs]
+    else:
+        with mp.get_context("spawn").Pool(workers) as pool:
+            parts = pool.map(_chunk, jobs)
+    return concat_workloads(parts)

@@ -88,3 +88,58 @@ def compare(gpu: dict, ora: dict, sel=None, max_exempt_frac=0.02) -> dict:
     assert not msgs, "\n".join(msgs) + f"\nreport: {rep}"
     assert rep["exempt"] <= max_exempt_frac * n + 2, rep
     return rep
+
+
+def _cov_norm(cov):
+    d = np.sqrt(np.maximum(cov[[0, 2, 5, 9, 14]], 1e-30))
+    out = np.empty_like(cov)
+    k = 0
+    for i in range(5):
+        for j in range(i + 1):
+            out[k] = d[i] * d[j]
+            k += 1
+    return out
+
+
+def compare_refit(gpu: dict, ora: dict, sel=None, max_exempt_frac=0.02) -> dict:
+    """The refit's results against the oracle's, with the follower's
+    tolerances (parameters 1e-4 of max(|v|, sigma), chi2 1e-3 absolute,
+    covariance 1e-3 of sqrt(C_ii C_jj)); status and update count identical
+    unless the oracle's smallest decision slack (|snp| limit, sector edge)
+    is below 1e-3, in which case the track is exempt."""
+    n = ora["chi2"].shape[0]
+    idx = np.arange(n) if sel is None else np.asarray(sel)
+    g = {k: v[..., idx] for k, v in gpu.items()}
+    same = (g["status"] == ora["status"]) & (g["n_upd"] == ora["n_upd"])
+    exempt = ~same & (ora["margin"] < MARGIN)
+    bad_path = ~same & ~exempt
+    sig = np.sqrt(np.maximum(ora["cov"][[0, 2, 5, 9, 14]], 0.0))
+    par_err = np.abs(g["par"] - ora["par"]) / np.maximum(np.maximum(np.abs(ora["par"]), sig), 1e-30)
+    chi2_err = np.abs(g["chi2"] - ora["chi2"])
+    cov_err = np.abs(g["cov"] - ora["cov"]) / _cov_norm(ora["cov"])
+    x_err = np.abs(g["x"] - ora["x"])
+    a_err = np.abs(np.angle(np.exp(1j * (g["alpha"].astype(np.float64) - ora["alpha"]))))
+    bad = {
+        "path": bad_path,
+        "par": same & (par_err.max(0) > PAR_REL),
+        "chi2": same & (chi2_err > CHI2_ABS),
+        "cov": same & (cov_err.max(0) > COV_REL),
+        "geo": same & ((x_err > 1e-4 * np.abs(ora["x"])) | (a_err > 1e-6)),
+    }
+    rep = dict(n=int(n), same=int(same.sum()), exempt=int(exempt.sum()),
+               refitted=int((same & (ora["status"] == 0)).sum()),
+               max_par_rel_each=[float(par_err[i, same].max(initial=0.0)) for i in range(5)],
+               max_chi2_abs=float(chi2_err[same].max(initial=0.0)),
+               max_cov_rel=float(cov_err[:, same].max(initial=0.0)))
+    msgs = []
+    for name, mask in bad.items():
+        if mask.any():
+            j = int(np.nonzero(mask)[0][0])
+            msgs.append(f"{name}: {int(mask.sum())} tracks, first {int(idx[j])}: gpu st {int(g['status'][j])} "
+                        f"n_upd {int(g['n_upd'][j])} chi2 {float(g['chi2'][j]):.6g} par {g['par'][:, j].tolist()} "
+                        f"| oracle st {int(ora['status'][j])} n_upd {int(ora['n_upd'][j])} chi2 "
+                        f"{float(ora['chi2'][j]):.6g} par {ora['par'][:, j].tolist()} margin "
+                        f"{float(ora['margin'][j]):.3g}")
+    assert not msgs, "\n".join(msgs) + f"\nreport: {rep}"
+    assert rep["exempt"] <= max_exempt_frac * n + 2, rep
+    return rep

@@ -48,6 +48,7 @@ def test_invalid_arguments_are_rejected_without_a_gpu():
     assert L.trd_ctx_destroy(None) == trd.TRD_EINVAL
     assert L.trd_index_free(None) == trd.TRD_EINVAL
     assert L.trd_geometry(None, 3) == trd.TRD_EINVAL
+    assert L.trd_refit(None, None, 0, None, None, 100.0, None, None) == trd.TRD_EINVAL
     h = C.c_void_p()
     rc = L.trd_ctx_create(0, C.byref(h))
     # no GPU in this container: the call must fail cleanly, never fall back
