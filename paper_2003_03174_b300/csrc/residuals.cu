@@ -103,7 +103,8 @@ __device__ __forceinline__ bool carry(Carrier &c, int sec, df xr, float bz, Trac
         c.anchor = w;
         c.frame = to;
     }
-    return propagate(w, xr, bz);
+    // the row's copy needs only the (y, z) block and the angle variances
+    return propagate_t<false>(w, xr, bz);
 }
 
 // Sub-volume of a cluster, decided in FP32 with correctly rounded operations
@@ -126,7 +127,12 @@ __device__ __forceinline__ int voxel_of(float y, float z, int sec, int row, floa
 
 __device__ __forceinline__ long long fixed24(float v) { return __float2ll_rn(v * 16777216.0f); }
 
-__global__ void __launch_bounds__(128) k_residuals(StatesView I, StatesView Tr, ClustersView cl, int n, float bz,
+// Resident 128-thread blocks per SM the register budget is sized for.
+#ifndef TRD_RESIDUALS_MIN_BLOCKS
+#define TRD_RESIDUALS_MIN_BLOCKS 5
+#endif
+
+__global__ void __launch_bounds__(128, TRD_RESIDUALS_MIN_BLOCKS) k_residuals(StatesView I, StatesView Tr, ClustersView cl, int n, float bz,
                                                    unsigned long long *sums, float *res_out)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -148,23 +154,39 @@ __global__ void __launch_bounds__(128) k_residuals(StatesView I, StatesView Tr, 
 
     // the ITS refit outward: only where the cluster sector changes does the
     // path matter (the rotations); the anchor ends at the last of them
+    // (only the 1-byte sectors are read; y and z where a rotation is due)
     int last = -1;
-#pragma unroll 1
+#pragma unroll 4
     for (int r = 0; r < kRows; ++r) {
         const size_t q = static_cast<size_t>(r) * n + i;
         const int s = cl.sector[q];
-        if (s < 0 || s >= kSectors || !isfinite(cl.y[q]) || !isfinite(cl.z[q])) continue;
+        if (s < 0 || s >= kSectors) continue;
         last = r;
-        if (s != A.anchor.sector) (void)carry(A, s, df{c_rows.x[r], 0.0f}, bz, a);
+        if (s != A.anchor.sector && isfinite(cl.y[q]) && isfinite(cl.z[q]))
+            (void)carry(A, s, df{c_rows.x[r], 0.0f}, bz, a);
     }
 
-    // both inward, row by row
+    // both inward, row by row; the next row's cluster is loaded while this
+    // row is computed
+    int s_next = last >= 0 ? cl.sector[static_cast<size_t>(last) * n + i] : -1;
+    float y_next = last >= 0 ? cl.y[static_cast<size_t>(last) * n + i] : 0.0f;
+    float z_next = last >= 0 ? cl.z[static_cast<size_t>(last) * n + i] : 0.0f;
+    if (res_out)
+        for (int r = kRows - 1; r > last; --r)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) res_out[k * plane + static_cast<size_t>(r) * n + i] = __int_as_float(0x7fc00000);
 #pragma unroll 1
-    for (int r = kRows - 1; r >= 0; --r) {
+    for (int r = last; r >= 0; --r) {
         const size_t q = static_cast<size_t>(r) * n + i;
-        const int s = r <= last ? cl.sector[q] : -1;
+        const int s = s_next;
+        const float ycl = y_next, zcl = z_next;
+        if (r > 0) {
+            const size_t qn = q - n;
+            s_next = cl.sector[qn];
+            y_next = cl.y[qn];
+            z_next = cl.z[qn];
+        }
         float dy = __int_as_float(0x7fc00000), dz = dy, t = dy, u = dy;
-        const float ycl = cl.y[q], zcl = cl.z[q];
         if (s >= 0 && s < kSectors && isfinite(ycl) && isfinite(zcl)) {
             const df xr = {c_rows.x[r], 0.0f};
             const bool okb = carry(B, s, xr, bz, b);

