@@ -67,6 +67,7 @@ def _load(path):
         L.ora_constants.restype = None
         L.ora_follow.restype = C.c_int
         L.ora_refit.restype = C.c_int
+        L.ora_propagate_map.restype = C.c_int
         L.ora_voxel_of.argtypes = [C.c_float, C.c_float, C.c_int, C.c_int]
         L.ora_voxel_of.restype = C.c_int
         L.ora_residuals.restype = C.c_int
@@ -114,6 +115,22 @@ def material_inward(st, cov):
     return ok, s, c
 
 
+def propagate_map(st, cov, x_to, bz, field=None):
+    """One transport step with the field map's midpoint field (the
+    follower's step when a map is given).  Returns (ok, st, cov)."""
+    s_, c_ = _vec(st, 7), _vec(cov, 15)
+    if field is not None:
+        fb = _f32(field["bz"])
+        box = np.array([field["r_min"], field["r_max"], field["z_min"], field["z_max"]], dtype=np.float64)
+        ok = lib().ora_propagate_map(s_.ctypes.data_as(C.c_void_p), c_.ctypes.data_as(C.c_void_p),
+                                     C.c_double(x_to), C.c_double(bz), fb.ctypes.data_as(C.c_void_p),
+                                     C.c_int(fb.shape[1]), C.c_int(fb.shape[0]), box.ctypes.data_as(C.c_void_p)) == 0
+    else:
+        ok = lib().ora_propagate_map(s_.ctypes.data_as(C.c_void_p), c_.ctypes.data_as(C.c_void_p),
+                                     C.c_double(x_to), C.c_double(bz), None, C.c_int(0), C.c_int(0), None) == 0
+    return ok, s_, c_
+
+
 def bethe(bg: float) -> float:
     return lib().ora_bethe(float(bg))
 
@@ -151,7 +168,7 @@ def _f32(a):
 
 
 def follow(seeds: dict, tracklets: dict, params: dict, seed_index=None, brute=False,
-           n_threads=0) -> dict:
+           n_threads=0, chamber_x=None, field=None) -> dict:
     """Run the FP64 follower.  seeds/tracklets are the FP32 input arrays
     (the same ones the library reads).  Returns numpy arrays keyed like the
     library's results, plus 'margin' [6, n] and 'nroad' [6, n]."""
@@ -189,6 +206,19 @@ def follow(seeds: dict, tracklets: dict, params: dict, seed_index=None, brute=Fa
     trig = [np.ascontiguousarray(np.asarray(d["trigger"], dtype=np.int32)) if d.get("trigger") is not None
             else None for d in (seeds, tracklets)]
     args += [t.ctypes.data_as(C.c_void_p) if t is not None else None for t in trig]
+    # misalignment and field map (Sec. 3): per-tracklet radius, per-chamber
+    # average radius, Bz map = dict(bz [nz, nr], r_min, r_max, z_min, z_max)
+    tx = _f32(tracklets["x"]) if tracklets.get("x") is not None else None
+    cx = _f32(chamber_x) if chamber_x is not None else None
+    if field is not None:
+        fb = _f32(field["bz"])
+        box = np.array([field["r_min"], field["r_max"], field["z_min"], field["z_max"]], dtype=np.float64)
+        fargs = [fb.ctypes.data_as(C.c_void_p), C.c_int(fb.shape[1]), C.c_int(fb.shape[0]),
+                 box.ctypes.data_as(C.c_void_p)]
+    else:
+        fargs = [None, C.c_int(0), C.c_int(0), None]
+    args += [tx.ctypes.data_as(C.c_void_p) if tx is not None else None,
+             cx.ctypes.data_as(C.c_void_p) if cx is not None else None] + fargs
     rc = L.ora_follow(*args)
     if rc != 0:
         raise ValueError(f"ora_follow rejected its arguments ({rc})")
@@ -322,4 +352,4 @@ def _params_arrays(params):
 
 __all__ = ["use_library", "propagate", "rotate", "material", "bethe", "highland", "update", "chi2",
            "cov_is_pd", "constants", "follow", "refit", "to_layer", "candidates", "lib",
-           "material_inward", "residuals", "voxel_solve", "voxel_of", "N_VOXELS", "N_TPC_ROWS"]
+           "material_inward", "propagate_map", "residuals", "voxel_solve", "voxel_of", "N_VOXELS", "N_TPC_ROWS"]

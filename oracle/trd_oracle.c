@@ -393,6 +393,12 @@ double ora_chi2(const double st[7], const double c[15], int layer, const double 
 typedef struct {
     double bz, n_sigma_road, chi2_cut, p_miss, dy_gate_sigma;
     int n_hyp, max_missing, res_mode, material_on;
+    /* misalignment and field (Sec. 3, the paragraph on misalignment): an
+     * optional average radius per chamber, an optional Bz(r, z) map */
+    const float *chamber_x;        /* [540] or NULL: nominal layer radii */
+    const float *field;            /* [nz][nr] or NULL: homogeneous bz */
+    int f_nr, f_nz;
+    double f_r0, f_r1, f_z0, f_z1;
 } ora_params_t;
 
 typedef struct {
@@ -416,6 +422,7 @@ typedef struct {
     const int *list;
     int brute;        /* 1: scan every tracklet of the input and test its chamber id */
     const int *trig;  /* interaction id per tracklet, or NULL */
+    const float *x;   /* radius of each tracklet (misalignment), or NULL: the layer's */
 } ora_tracklets_t;
 
 static int cmp_ext(const void *pa, const void *pb)
@@ -439,6 +446,87 @@ static int sector_of_alpha(double a)
 
 static double sector_alpha(int s) { return (s + 0.5) * sector_width(); }
 
+/* ---- field map (reading for the field inhomogeneities of Sec. 3) ----------
+ * Bz on a regular grid in (r, z): nodes r_i = r0 + i (r1 - r0) / (nr - 1),
+ * z_j likewise, value field[j * nr + i]; bilinear between the nodes, the grid
+ * box clamps.  A transport step uses the field at its midpoint, estimated
+ * along the straight line from the start: x_m = (x0 + x1) / 2, y_m and z_m
+ * advanced by half the step along the start direction, r_m = |(x_m, y_m)|;
+ * the helix of that constant field is then exact for the step (the field's
+ * gradient is not carried into the Jacobian).  A rotation uses the field at
+ * the state's own point.  Without a map every step uses bz.                */
+static ora_params_t make_params(const double *pd, const int *pi)
+{
+    ora_params_t P;
+    memset(&P, 0, sizeof P);
+    P.bz = pd[0];
+    P.n_sigma_road = pd[1];
+    P.chi2_cut = pd[2];
+    P.p_miss = pd[3];
+    P.dy_gate_sigma = pd[4];
+    P.n_hyp = pi[0];
+    P.max_missing = pi[1];
+    P.res_mode = pi[2];
+    P.material_on = pi[3];
+    return P;
+}
+
+static double field_at(const ora_params_t *P, double r, double z)
+{
+    if (!P->field) return P->bz;
+    double fr = (P->f_nr - 1) * (r - P->f_r0) / (P->f_r1 - P->f_r0);
+    double fz = (P->f_nz - 1) * (z - P->f_z0) / (P->f_z1 - P->f_z0);
+    fr = fmin(fmax(fr, 0.0), (double)(P->f_nr - 1));
+    fz = fmin(fmax(fz, 0.0), (double)(P->f_nz - 1));
+    int i = (int)floor(fr), j = (int)floor(fz);
+    if (i > P->f_nr - 2) i = P->f_nr - 2;
+    if (j > P->f_nz - 2) j = P->f_nz - 2;
+    const double wr = fr - i, wz = fz - j;
+    const float *F = P->field;
+    const int nr = P->f_nr;
+    return (1 - wz) * ((1 - wr) * F[j * nr + i] + wr * F[j * nr + i + 1]) +
+           wz * ((1 - wr) * F[(j + 1) * nr + i] + wr * F[(j + 1) * nr + i + 1]);
+}
+
+static double step_field(const ora_params_t *P, const double st[7], double x1)
+{
+    if (!P->field) return P->bz;
+    const double f = st[4];
+    if (!(fabs(f) < 1.0)) return field_at(P, hypot(st[1], st[2]), st[3]);
+    const double r = sqrt((1.0 - f) * (1.0 + f)), h = 0.5 * (x1 - st[1]);
+    return field_at(P, hypot(st[1] + h, st[2] + h * f / r), st[3] + h * st[5] / r);
+}
+
+static int fprop(double st[7], double c[15], double x1, const ora_params_t *P, double *slack)
+{
+    return ora_propagate(st, c, x1, step_field(P, st, x1), NULL, slack);
+}
+
+static int frot(double st[7], double c[15], double alpha, const ora_params_t *P, double *slack)
+{
+    return ora_rotate(st, c, alpha, field_at(P, hypot(st[1], st[2]), st[3]), NULL, slack);
+}
+
+/* Test helper: one field-map transport step (fprop above) of a state to x1.
+ * field [nz][nr] with box = {r0, r1, z0, z1}; NULL field: homogeneous bz.   */
+int ora_propagate_map(double st[7], double c[15], double x1, double bz, const float *field, int nr, int nz,
+                      const double *box)
+{
+    ora_params_t P;
+    memset(&P, 0, sizeof P);
+    P.bz = bz;
+    if (field) {
+        P.field = field;
+        P.f_nr = nr;
+        P.f_nz = nz;
+        P.f_r0 = box[0];
+        P.f_r1 = box[1];
+        P.f_z0 = box[2];
+        P.f_z1 = box[3];
+    }
+    return fprop(st, c, x1, &P, NULL);
+}
+
 /* Carry a hypothesis to the plane of layer l: helix transport; if the track
  * left the sector's azimuthal extent, rotate into the neighbour sector and
  * transport again; then one material step.  Sets *chamber (-1 when z is
@@ -447,14 +535,14 @@ static int to_layer(ora_hyp_t *h, int l, const ora_params_t *P, int *chamber, do
 {
     const double xl = layer_x(l);
     double sl = INFINITY;
-    if (ora_propagate(h->st, h->c, xl, P->bz, NULL, &sl)) { *margin = fmin(*margin, sl); return -1; }
+    if (fprop(h->st, h->c, xl, P, &sl)) { *margin = fmin(*margin, sl); return -1; }
     const double lim = xl * half_sector_tan();
     *margin = fmin(*margin, fabs(fabs(h->st[2]) - lim));
     if (fabs(h->st[2]) > lim) {
         const int ns = (h->sector + (h->st[2] > 0 ? 1 : -1) + ORA_NSECTOR) % ORA_NSECTOR;
-        if (ora_rotate(h->st, h->c, sector_alpha(ns), P->bz, NULL, &sl)) { *margin = fmin(*margin, sl); return -1; }
+        if (frot(h->st, h->c, sector_alpha(ns), P, &sl)) { *margin = fmin(*margin, sl); return -1; }
         h->sector = ns;
-        if (ora_propagate(h->st, h->c, xl, P->bz, NULL, &sl)) { *margin = fmin(*margin, sl); return -1; }
+        if (fprop(h->st, h->c, xl, P, &sl)) { *margin = fmin(*margin, sl); return -1; }
     }
     *margin = fmin(*margin, sl);
     if (P->material_on && ora_material(h->st, h->c)) return -1;
@@ -466,6 +554,13 @@ static int to_layer(ora_hyp_t *h, int l, const ora_params_t *P, int *chamber, do
     if (u >= 0 && u < ORA_NSTACK) {
         const int stack = (int)floor(u);
         *chamber = h->sector * (ORA_NSTACK * ORA_NLAYER) + stack * ORA_NLAYER + l;
+        /* misalignment: on to the chamber's average radius (the chamber is the
+         * one found at the nominal radius) */
+        if (P->chamber_x && (double)P->chamber_x[*chamber] != xl) {
+            sl = INFINITY;
+            if (fprop(h->st, h->c, P->chamber_x[*chamber], P, &sl)) { *margin = fmin(*margin, sl); return -1; }
+            *margin = fmin(*margin, sl);
+        }
     } else {
         *chamber = -1;
     }
@@ -484,8 +579,18 @@ static int test_tracklet(const ora_hyp_t *h, int l, const ora_tracklets_t *T, in
     const double u = f / r - lorentz_tan(P->bz);
     double vyy = T->vyy[j];
     if (P->res_mode) vyy = kSigY0 * kSigY0 + kSigY1 * kSigY1 * u * u;
+    /* a tracklet at another radius (misalignment): the fast linear
+     * extrapolation of the track to it (straight line along its direction;
+     * covariance as at the chamber radius) for the tests */
+    double sx[7];
+    memcpy(sx, h->st, sizeof sx);
+    if (T->x) {
+        const double dx = (double)T->x[j] - h->st[1];
+        sx[2] += dx * f / r;
+        sx[3] += dx * h->st[5] / r;
+    }
     ora_resid_t o;
-    ora_residual(h->st, h->c, tilt_tan(l), T->y[j], T->z[j], vyy, T->vzz[j], T->vyz[j], &o);
+    ora_residual(sx, h->c, tilt_tan(l), T->y[j], T->z[j], vyy, T->vzz[j], T->vyz[j], &o);
     const double ny = fabs(o.r[0]) / sqrt(o.S[0]);
     const double nz = fabs(o.r[1]) / sqrt(o.S[2]);
     const double dy_pred = kDriftLength * u;
@@ -568,7 +673,7 @@ static void follow_one(const double seed_st[7], const double seed_c[15], int see
         const double rad = hypot(seed_st[1], seed_st[2]);
         R->margin[0] = fmin(R->margin[0], rad * fmin(u, w - u));
         double sl = INFINITY;
-        if (ora_rotate(set[0].st, set[0].c, sector_alpha(s), P->bz, NULL, &sl)) {
+        if (frot(set[0].st, set[0].c, sector_alpha(s), P, &sl)) {
             R->margin[0] = fmin(R->margin[0], sl);
             R->status = ORA_ST_PROP_FAIL;
             return;
@@ -619,6 +724,9 @@ static void follow_one(const double seed_st[7], const double seed_c[15], int see
             } else {
                 double m5[5] = {T->y[x->id], T->z[x->id], T->vyy[x->id], T->vzz[x->id],
                                 T->vyz[x->id]};
+                /* before the update: the precise transport to the tracklet's
+                 * own radius (a failed transport leaves the state where it is) */
+                if (T->x) (void)fprop(h.st, h.c, (double)T->x[x->id], P, NULL);
                 if (P->res_mode) {
                     const double f = h.st[4], r = sqrt((1.0 - f) * (1.0 + f));
                     const double u = f / r - lorentz_tan(P->bz);
@@ -649,7 +757,7 @@ static void follow_one(const double seed_st[7], const double seed_c[15], int see
 int ora_to_layer(double st[7], double c[15], int *sector_io, int l, const double *pd,
                  const int *pi, int *chamber)
 {
-    ora_params_t P = {pd[0], pd[1], pd[2], pd[3], pd[4], pi[0], pi[1], pi[2], pi[3]};
+    ora_params_t P = make_params(pd, pi);
     ora_hyp_t h;
     memset(&h, 0, sizeof h);
     memcpy(h.st, st, sizeof h.st);
@@ -668,8 +776,8 @@ int ora_candidates(const double st[7], const double c[15], int l, int chamber, i
                    const float *t_vyy, const float *t_vzz, const float *t_vyz, const double *pd,
                    const int *pi, int max_out, int *ids_out, double *chi2_out)
 {
-    ora_params_t P = {pd[0], pd[1], pd[2], pd[3], pd[4], pi[0], pi[1], pi[2], pi[3]};
-    ora_tracklets_t T = {n_trk, t_ch, t_y, t_z, t_dy, t_vyy, t_vzz, t_vyz, NULL, NULL, 1, NULL};
+    ora_params_t P = make_params(pd, pi);
+    ora_tracklets_t T = {n_trk, t_ch, t_y, t_z, t_dy, t_vyy, t_vzz, t_vyz, NULL, NULL, 1, NULL, NULL};
     ora_hyp_t h;
     memset(&h, 0, sizeof h);
     memcpy(h.st, st, sizeof h.st);
@@ -696,6 +804,9 @@ int ora_candidates(const double st[7], const double c[15], int l, int chamber, i
  * pd = {bz, n_sigma_road, chi2_cut, p_miss, dy_gate_sigma}
  * pi = {n_hyp, max_missing, res_mode, material_on}
  * seed_trig, t_trig (optional): interaction ids (Sec. 4 association).
+ * t_x (optional): the radius of each tracklet; chamber_x (optional, [540]):
+ * the average radius of each chamber (misalignment, Sec. 3).  field
+ * (optional, [f_nz][f_nr]) with f_box = {r0, r1, z0, z1}: a Bz map.
  * Returns 0, or -1 on invalid arguments.                                    */
 int ora_follow(int n_seeds, const float *alpha, const float *x, const float *y, const float *z,
                const float *snp, const float *tgl, const float *q2pt, const float *cov,
@@ -704,11 +815,23 @@ int ora_follow(int n_seeds, const float *alpha, const float *x, const float *y, 
                const double *pd, const int *pi, int n_out, const int *seed_index, int brute,
                int n_threads, double *st_out, double *cov_out, double *chi2_out, int *ntrk_out,
                int *nmiss_out, int *status_out, int *ids_out, double *margin_out, int *nroad_out,
-               const int *seed_trig, const int *t_trig)
+               const int *seed_trig, const int *t_trig, const float *t_x, const float *chamber_x,
+               const float *field, int f_nr, int f_nz, const double *f_box)
 {
     if (n_seeds < 0 || n_trk < 0 || n_out < 0) return -1;
-    ora_params_t P = {pd[0], pd[1], pd[2], pd[3], pd[4], pi[0], pi[1], pi[2], pi[3]};
+    ora_params_t P = make_params(pd, pi);
     if (P.n_hyp < 1 || P.n_hyp > ORA_MAXHYP) return -1;
+    P.chamber_x = chamber_x;
+    if (field) {
+        if (f_nr < 2 || f_nz < 2 || !f_box || !(f_box[1] > f_box[0]) || !(f_box[3] > f_box[2])) return -1;
+        P.field = field;
+        P.f_nr = f_nr;
+        P.f_nz = f_nz;
+        P.f_r0 = f_box[0];
+        P.f_r1 = f_box[1];
+        P.f_z0 = f_box[2];
+        P.f_z1 = f_box[3];
+    }
 
     /* chamber buckets: a counting pass, then a fill in input order */
     int *start = calloc(ORA_NCHAMBER + 1, sizeof(int));
@@ -723,7 +846,7 @@ int ora_follow(int n_seeds, const float *alpha, const float *x, const float *y, 
             if (t_ch[j] >= 0 && t_ch[j] < ORA_NCHAMBER) list[fill[t_ch[j]]++] = j;
         free(fill);
     }
-    ora_tracklets_t T = {n_trk, t_ch, t_y, t_z, t_dy, t_vyy, t_vzz, t_vyz, start, list, brute, t_trig};
+    ora_tracklets_t T = {n_trk, t_ch, t_y, t_z, t_dy, t_vyy, t_vzz, t_vyz, start, list, brute, t_trig, t_x};
 
 #ifdef _OPENMP
     if (n_threads > 0) omp_set_num_threads(n_threads);
@@ -882,8 +1005,8 @@ int ora_refit(int n, const float *alpha, const float *x, const float *par, const
               double *cov_out, double *chi2_out, int *nupd_out, int *status_out, double *margin_out)
 {
     if (n < 0 || n_trk < 0 || !(cov_scale > 0)) return -1;
-    ora_params_t P = {pd[0], pd[1], pd[2], pd[3], pd[4], pi[0], pi[1], pi[2], pi[3]};
-    ora_tracklets_t T = {n_trk, t_ch, t_y, NULL, NULL, t_vyy, t_vzz, t_vyz, NULL, NULL, 1, NULL};
+    ora_params_t P = make_params(pd, pi);
+    ora_tracklets_t T = {n_trk, t_ch, t_y, NULL, NULL, t_vyy, t_vzz, t_vyz, NULL, NULL, 1, NULL, NULL};
     T.z = t_z;
 #ifdef _OPENMP
     if (n_threads > 0) omp_set_num_threads(n_threads);

@@ -169,6 +169,7 @@ class Timeframe:
     # truth helix per seed: azimuth at the origin phi0, signed curvature kcurv
     # (d(phi)/ds, 1/cm), tan(lambda), q/pT: float64[n] each
     truth: dict = field(default=None)
+    chamber_x: np.ndarray = None  # float32[540] average chamber radii when misaligned
 
     @property
     def n_seeds(self) -> int:
@@ -192,7 +193,8 @@ def make_timeframe(n_seeds: int, seed: int = 0, noise: float = 0.2, bz: float = 
                    eff: float = 0.9, smear: bool = True, snap_z: bool = True,
                    distortion: bool = False, sys_y: float = 0.0,
                    off_centre_frac: float = 0.1, name: str = "custom",
-                   params: dict | None = None, n_interactions: int = 0) -> Timeframe:
+                   params: dict | None = None, n_interactions: int = 0,
+                   misalign: float = 0.0, x_jitter: float = 0.0) -> Timeframe:
     """Draw one timeframe.
 
     Truth: |eta| < 0.9, uniform phi, q = +-1, pT exponential with mean 0.6
@@ -205,7 +207,13 @@ def make_timeframe(n_seeds: int, seed: int = 0, noise: float = 0.2, bz: float = 
     to their y error.  With n_interactions > 0, every track belongs to one of
     that many interactions (uniform), its seed and tracklets carry the id
     ("trigger"), and noise tracklets get a uniform random id (drawn from a
-    separate stream, so the rest of the timeframe is unchanged).
+    separate stream, so the rest of the timeframe is unchanged).  With
+    misalign > 0 or x_jitter > 0 (cm), every chamber gets an average radius
+    x_l + U(-misalign, misalign) and every tracklet a radius x_chamber +
+    U(-x_jitter, x_jitter) (a third stream); the tracklet then measures the
+    truth where it crosses the plane of its own radius (the chamber is still
+    the one crossed at the nominal radius), and the timeframe carries
+    tracklets["x"] and chamber_x.
     """
     rng = np.random.Generator(np.random.Philox(key=seed))
     n_draw = int(n_seeds * 1.5) + 256
@@ -234,7 +242,13 @@ def make_timeframe(n_seeds: int, seed: int = 0, noise: float = 0.2, bz: float = 
     n = n_seeds
 
     # tracklets from truth crossings
-    ch_l, y_l, z_l, dy_l, owner_l, layer_l = [], [], [], [], [], []
+    aligned = misalign <= 0.0 and x_jitter <= 0.0
+    chamber_x = None
+    if not aligned:
+        arng = np.random.Generator(np.random.Philox(key=seed + 9_999_999))
+        nominal = np.repeat(np.array([layer_x(l) for l in range(N_LAYERS)])[None, :], N_SECTORS * N_STACKS, 0)
+        chamber_x = (nominal.reshape(-1) + arng.uniform(-misalign, misalign, N_CHAMBERS)).astype(np.float32)
+    ch_l, y_l, z_l, dy_l, owner_l, layer_l, x_l = [], [], [], [], [], [], []
     for layer in range(N_LAYERS):
         xp = layer_x(layer)
         sec, s, yl, sinl, ok = _cross_chamber_plane(phi0, kcurv, xp)
@@ -242,6 +256,21 @@ def make_timeframe(n_seeds: int, seed: int = 0, noise: float = 0.2, bz: float = 
         ok &= (z >= Z_MIN) & (z < -Z_MIN) & (np.abs(sinl) < 0.95)
         ok &= rng.uniform(0, 1, n) < eff
         stack = np.clip(np.floor((z - Z_MIN) / STACK_LENGTH), 0, N_STACKS - 1).astype(np.int64)
+        if not aligned:
+            # the tracklet sits at its own radius: the truth there, in the same chamber
+            ch_n = sec * (N_STACKS * N_LAYERS) + stack * N_LAYERS + layer
+            xt = chamber_x[ch_n].astype(np.float64) + arng.uniform(-x_jitter, x_jitter, n)
+            xt = xt.astype(np.float32).astype(np.float64)
+            a_s = sector_alpha(sec)
+            s2, ok2 = _cross_plane(phi0, kcurv, a_s, xt, s0=s)
+            _, yl = _local_xy(s2, phi0, kcurv, a_s)
+            sinl = np.sin(phi0 + kcurv * s2 - a_s)
+            z = tgl * s2
+            # a crossing that left the chamber's stack between the two radii
+            # gives no tracklet in that chamber
+            ok &= ok2 & (np.abs(sinl) < 0.95) & (z >= Z_MIN + STACK_LENGTH * stack) & \
+                (z < Z_MIN + STACK_LENGTH * (stack + 1))
+            x_l.append(xt)
         row = np.clip(np.floor((z - Z_MIN - STACK_LENGTH * stack) / ROW_LENGTH), 0,
                       ROWS_PER_STACK - 1)
         z_row = Z_MIN + STACK_LENGTH * stack + ROW_LENGTH * (row + 0.5)
@@ -254,6 +283,8 @@ def make_timeframe(n_seeds: int, seed: int = 0, noise: float = 0.2, bz: float = 
             y_meas = y_meas + rng.normal(0.0, 0.04, n)
             dyv = dyv + rng.normal(0.0, 1.0, n) * sdy
         sel = np.nonzero(ok)[0]
+        if not aligned:
+            x_l[-1] = x_l[-1][sel]
         ch_l.append(sec[sel] * (N_STACKS * N_LAYERS) + stack[sel] * N_LAYERS + layer)
         y_l.append(y_meas[sel])
         z_l.append(z_meas[sel])
@@ -269,8 +300,11 @@ def make_timeframe(n_seeds: int, seed: int = 0, noise: float = 0.2, bz: float = 
     n_sig = ch.shape[0]
 
     n_noise = int(round(noise * n_sig))
+    tx = np.concatenate(x_l) if not aligned else None
     if n_noise:
         nch = rng.integers(0, N_CHAMBERS, n_noise)
+        if not aligned:
+            tx = np.concatenate([tx, chamber_x[nch] + arng.uniform(-x_jitter, x_jitter, n_noise)])
         nlayer = nch % N_LAYERS
         nstack = (nch // N_LAYERS) % N_STACKS
         nrow = rng.integers(0, ROWS_PER_STACK, n_noise)
@@ -307,6 +341,8 @@ def make_timeframe(n_seeds: int, seed: int = 0, noise: float = 0.2, bz: float = 
     )
     if trig_trk is not None:
         tracklets["trigger"] = trig_trk[perm]
+    if not aligned:
+        tracklets["x"] = tx[perm].astype(np.float32)
 
     # seeds
     z_s = tgl * s_s
@@ -343,7 +379,7 @@ def make_timeframe(n_seeds: int, seed: int = 0, noise: float = 0.2, bz: float = 
     return Timeframe(name=name, seeds=seeds, tracklets=tracklets,
                      params=params if params is not None else default_params(bz),
                      truth_ids=truth, truth_pt=pt.astype(np.float32),
-                     truth=dict(phi0=phi0, kcurv=kcurv, tgl=tgl, q2pt=q / pt))
+                     truth=dict(phi0=phi0, kcurv=kcurv, tgl=tgl, q2pt=q / pt), chamber_x=chamber_x)
 
 
 def make_workload(name: str, seed: int = 0, n_seeds: int | None = None,

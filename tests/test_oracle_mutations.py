@@ -12,6 +12,7 @@ from oracle import oracle as O
 import test_oracle_pins as P
 import test_oracle_refit_pins as R
 import test_oracle_residual_pins as Q
+import test_oracle_alignment_pins as M
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(os.path.dirname(HERE), "oracle", "trd_oracle.c")
@@ -64,6 +65,14 @@ PINNED = [
     ("y bin without offset", "const float v = u + T;", "const float v = u;"),
     ("solve sign of Dx", "const double dx = -(n * (S[7] + S[8])", "const double dx = (n * (S[7] + S[8])"),
     ("solve drops the angular mean", "o[1] = (S[5] + S[1] * dx) / n;", "o[1] = S[5] / n;"),
+    # misalignment and the field map (Sec. 3)
+    ("no linear extrapolation to the tracklet radius", "        sx[2] += dx * f / r;", "        sx[2] += 0.0 * dx * f / r;"),
+    ("no precise transport before the update", "if (T->x) (void)fprop(h.st, h.c, (double)T->x[x->id], P, NULL);", ""),
+    ("chamber radius ignored", "if (P->chamber_x && (double)P->chamber_x[*chamber] != xl) {", "if (0) {"),
+    ("step field at the start point", "    return field_at(P, hypot(st[1] + h, st[2] + h * f / r), st[3] + h * st[5] / r);",
+     "    return field_at(P, hypot(st[1], st[2]), st[3]);"),
+    ("field map axes swapped", "    return (1 - wz) * ((1 - wr) * F[j * nr + i] + wr * F[j * nr + i + 1]) +",
+     "    return (1 - wr) * ((1 - wz) * F[j * nr + i] + wz * F[j * nr + i + 1]) +"),
 ]
 
 UNPINNED = [
@@ -102,6 +111,12 @@ PINS = [
     lambda: Q.test_combined_estimate_has_unit_pulls(),
     lambda: Q.test_voxel_solve_equals_least_squares(),
     lambda: Q.test_map_recovers_a_uniform_displacement(),
+    lambda: M.test_misaligned_truth_is_found_with_the_radii_and_not_without(),
+    lambda: M.test_state_after_the_last_update_is_the_truth_at_that_radius(),
+    lambda: M.test_a_layer_without_tracklet_ends_at_the_chamber_radius(),
+    lambda: M.test_nominal_radii_reproduce_the_aligned_follower(),
+    lambda: M.test_uniform_field_map_is_the_homogeneous_field(),
+    lambda: M.test_field_map_step_agrees_with_runge_kutta(),
 ]
 
 
