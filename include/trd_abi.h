@@ -89,6 +89,10 @@ typedef struct {
     const float *y, *z, *dy, *vyy, *vzz, *vyz;
     int32_t n;
     const int32_t *trigger; /* optional interaction id per tracklet (see trd_seeds_t) */
+    const float *x;         /* optional radius of each tracklet in its sector frame (cm): with
+                               misalignment not every tracklet sits at its layer's radius (Sec. 3);
+                               NULL = the layer's nominal radius.  A non-finite x rejects the
+                               tracklet.  Not accepted by trd_index_build_noalloc. */
 } trd_tracklets_t;
 
 /* Follower parameters.
@@ -223,6 +227,39 @@ TRD_API int trd_follow_tuned(trd_ctx_t *ctx, const trd_seeds_t *seeds, const trd
                              const trd_params_t *params, trd_results_t *out, void *stream,
                              const trd_launch_t *launch);
 
+/* ---- misalignment and field map (Sec. 3) ---------------------------------------
+ * Misaligned chambers put tracklets at different radii; the paper carries a
+ * track to the average radius of the chamber (through the field's
+ * inhomogeneities), compares it with each tracklet by a fast linear
+ * extrapolation to that tracklet's radius, and transports it precisely to
+ * the matched tracklet's radius before the update.
+ *   chamber_x (device, [540] float, or NULL): average radius of each chamber
+ *     (cm); a hypothesis in chamber c is carried from its layer's nominal
+ *     radius (where the chamber is found from z) on to chamber_x[c].
+ *   bz_map (device, [nz][nr] float, or NULL): Bz (T) at r_i = r_min + i (r_max -
+ *     r_min) / (nr - 1), z_j likewise, bilinear between nodes, clamped to the
+ *     box; every transport step uses the map at its midpoint (estimated along
+ *     the straight line from the step's start), every rotation the map at the
+ *     state's point.  The Lorentz-angle sign still follows params.bz.
+ * Per-tracklet radii come with the tracklets (trd_tracklets_t.x, stored in
+ * the index by trd_index_build/rebuild): a candidate is then tested at its
+ * own radius by extrapolating the hypothesis along its direction
+ * (covariance as at the chamber radius), and a matched tracklet's hypothesis
+ * is transported to its radius before the update.
+ * trd_follow_aligned: trd_follow_tuned with an alignment (NULL = none).
+ * Errors as trd_follow_tuned, plus TRD_EINVAL for nr or nz < 2 or an empty
+ * box.                                                                      */
+typedef struct {
+    const float *chamber_x;
+    const float *bz_map;
+    int32_t nr, nz;
+    float r_min, r_max, z_min, z_max;
+} trd_alignment_t;
+
+TRD_API int trd_follow_aligned(trd_ctx_t *ctx, const trd_seeds_t *seeds, const trd_index_t *index,
+                               const trd_params_t *params, const trd_alignment_t *align, trd_results_t *out,
+                               void *stream, const trd_launch_t *launch);
+
 /* ---- TRD-only refit (Sec. 2, step 3) ----------------------------------------
  * The space-point calibration refits each matched track twice without the TPC
  * clusters: from the ITS, and from TRD and TOF.  trd_refit is the TRD half
@@ -245,7 +282,9 @@ TRD_API int trd_follow_tuned(trd_ctx_t *ctx, const trd_seeds_t *seeds, const trd
  * tracks (read only, device): results of trd_follow for n tracks (alpha, x,
  *   par, cov diagonal, status, tracklet_id are read; the other fields are
  *   ignored).  tracklets (read only, device): the arrays the ids refer to
- *   (chamber, y, z, vyy, vzz, vyz; dy and trigger are not read).
+ *   (chamber, y, z, vyy, vzz, vyz, and x when given: a layer with a
+ *   tracklet is then refitted at that tracklet's own radius; dy and trigger
+ *   are not read).  The field is homogeneous (params.bz).
  *   params: bz, res_mode and material_on are used.
  * out (device, caller-owned): alpha, x [n]; par [5][n]; cov [15][n];
  *   chi2 [n]; n_upd, status [n] (int32).  status: TRD_RF_OK, TRD_RF_PROP_FAIL

@@ -253,7 +253,7 @@ def refit(results: dict, tracklets: dict, params: dict, cov_scale: float = 100.0
     rc = L.ora_refit(C.c_int(n), *[ptr(v) for v in a], ptr(st_in), ptr(ids), C.c_int(m),
                      *[ptr(v) for v in tk], ptr(pd), ptr(pi), C.c_double(cov_scale),
                      C.c_int(n_threads), ptr(st), ptr(cv), ptr(chi2_), ptr(nupd), ptr(status),
-                     ptr(margin))
+                     ptr(margin), ptr(_f32(tracklets["x"])) if tracklets.get("x") is not None else None)
     if rc != 0:
         raise ValueError(f"ora_refit rejected its arguments ({rc})")
     return dict(alpha=st[0], x=st[1], par=st[2:7], cov=cv, chi2=chi2_, n_upd=nupd, status=status,

@@ -949,8 +949,9 @@ static void refit_one(const double in_st[7], const double in_cdiag[5], int in_st
 
     int fail = 0;
     for (int l = ltop; l >= 0 && !fail; --l) {
-        const double xl = layer_x(l);
         const int j = ids[l];
+        /* a layer's plane: its tracklet's own radius when given (misalignment) */
+        const double xl = (j >= 0 && T->x) ? (double)T->x[j] : layer_x(l);
         /* step 3 (l == ltop) and step 4: into the tracklet's sector, to x_l */
         double sl = INFINITY;
         if (ora_propagate(h.st, h.c, xl, P->bz, NULL, &sl)) { fail = 1; }
@@ -996,17 +997,18 @@ static void refit_one(const double in_st[7], const double in_cdiag[5], int in_st
  * to double.  Outputs: st_out[7][n], cov_out[15][n], chi2_out[n],
  * nupd_out[n], status_out[n], margin_out[n] (optional: the smallest slack of
  * a decision, |snp| limit or sector edge, in the units of its test).  pd/pi
- * as for ora_follow.  Returns 0, or -1
+ * as for ora_follow; t_x (optional): the tracklets' own radii.  Returns 0, or -1
  * on invalid arguments.                                                     */
 int ora_refit(int n, const float *alpha, const float *x, const float *par, const float *cov,
               const int *status, const int *ids, int n_trk, const int *t_ch, const float *t_y,
               const float *t_z, const float *t_vyy, const float *t_vzz, const float *t_vyz,
               const double *pd, const int *pi, double cov_scale, int n_threads, double *st_out,
-              double *cov_out, double *chi2_out, int *nupd_out, int *status_out, double *margin_out)
+              double *cov_out, double *chi2_out, int *nupd_out, int *status_out, double *margin_out,
+              const float *t_x)
 {
     if (n < 0 || n_trk < 0 || !(cov_scale > 0)) return -1;
     ora_params_t P = make_params(pd, pi);
-    ora_tracklets_t T = {n_trk, t_ch, t_y, NULL, NULL, t_vyy, t_vzz, t_vyz, NULL, NULL, 1, NULL, NULL};
+    ora_tracklets_t T = {n_trk, t_ch, t_y, NULL, NULL, t_vyy, t_vzz, t_vyz, NULL, NULL, 1, NULL, t_x};
     T.z = t_z;
 #ifdef _OPENMP
     if (n_threads > 0) omp_set_num_threads(n_threads);

@@ -31,6 +31,7 @@ void free_index_buffers(trd_index *x)
 {
     cudaFree(x->offsets);
     cudaFree(x->rec);
+    cudaFree(x->recx);
     cudaFree(x->stats);
     cudaFree(x->bucket);
     cudaFree(x->rank);
@@ -78,6 +79,7 @@ int index_alloc(trd_ctx *ctx, int32_t capacity, float y_bin_width, int32_t n_tf,
     const size_t cap = static_cast<size_t>(std::max(capacity, 1));
     bool ok = cudaMalloc(&x->offsets, sizeof(int32_t) * (x->n_buckets + 1)) == cudaSuccess &&
               cudaMalloc(&x->rec, 2 * sizeof(float4) * cap) == cudaSuccess &&
+              cudaMalloc(&x->recx, sizeof(float) * cap) == cudaSuccess &&
               cudaMalloc(&x->stats, sizeof(uint32_t) * 4) == cudaSuccess &&
               cudaMalloc(&x->bucket, sizeof(int32_t) * cap) == cudaSuccess &&
               cudaMalloc(&x->rank, sizeof(int32_t) * cap) == cudaSuccess &&
@@ -232,6 +234,17 @@ int trd_index_copy_out(const trd_index_t *index, int32_t *offsets, int32_t *ids)
 int trd_follow_tuned(trd_ctx_t *ctx, const trd_seeds_t *seeds, const trd_index_t *index,
                      const trd_params_t *p, trd_results_t *out, void *stream, const trd_launch_t *launch)
 {
+    return trd_follow_aligned(ctx, seeds, index, p, nullptr, out, stream, launch);
+}
+
+int trd_follow_aligned(trd_ctx_t *ctx, const trd_seeds_t *seeds, const trd_index_t *index,
+                       const trd_params_t *p, const trd_alignment_t *align, trd_results_t *out, void *stream,
+                       const trd_launch_t *launch)
+{
+    if (align && align->bz_map &&
+        (align->nr < 2 || align->nz < 2 || !(align->r_max > align->r_min) || !(align->z_max > align->z_min) ||
+         !isfinite(align->r_min) || !isfinite(align->r_max) || !isfinite(align->z_min) || !isfinite(align->z_max)))
+        return TRD_EINVAL;
     const int lanes_per_track = launch ? launch->lanes_per_track : 0;
     const int block_threads = launch ? launch->block_threads : 0;
     const int min_blocks = launch ? launch->min_blocks_per_sm : 0;
@@ -250,9 +263,10 @@ int trd_follow_tuned(trd_ctx_t *ctx, const trd_seeds_t *seeds, const trd_index_t
             return TRD_EINVAL;
     }
     TRD_CUDA_TRY(cudaSetDevice(ctx->device));
-    IndexView iv{index->offsets, index->rec, index->stats, index->nb, index->inv_w};
+    IndexView iv{index->offsets, index->rec, index->stats, index->nb, index->inv_w,
+                 index->has_x ? index->recx : nullptr};
     return trd_host::follow_launch(ctx, seeds, iv, p, out, static_cast<cudaStream_t>(stream), lanes_per_track,
-                                   block_threads, min_blocks, trd_host::next_counter(ctx));
+                                   block_threads, min_blocks, trd_host::next_counter(ctx), nullptr, 1, align);
 }
 
 int trd_follow(trd_ctx_t *ctx, const trd_seeds_t *seeds, const trd_index_t *index, const trd_params_t *p,

@@ -105,7 +105,8 @@ int trd_batch_create(trd_ctx_t *ctx, int32_t n_tf, const int32_t *seed_offsets, 
     if (ok) {
         rc = trd_host::index_rebuild_launch(b->index, tracklets, cs);
         if (!rc) {
-            IndexView iv{b->index->offsets, b->index->rec, b->index->stats, b->index->nb, b->index->inv_w};
+            IndexView iv{b->index->offsets, b->index->rec, b->index->stats, b->index->nb, b->index->inv_w,
+                         tracklets->x ? b->index->recx : nullptr};
             rc = trd_host::follow_launch(ctx, seeds, iv, params, results, cs, launch ? launch->lanes_per_track : 0,
                                          launch ? launch->block_threads : 0, launch ? launch->min_blocks_per_sm : 0,
                                          b->counter, n_tf > 1 ? b->soff : nullptr, n_tf);

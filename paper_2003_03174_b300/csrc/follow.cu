@@ -23,7 +23,46 @@ namespace trd {
 struct Params {
     float bz, road, cut, pmiss, gate;
     int nhyp, maxmiss, resmode, material;
+    // misalignment and field map (the EXT kernels only; Sec. 3): average
+    // radius per chamber, Bz on a regular (r, z) grid, or null
+    const float *chamber_x = nullptr;
+    const float *bzmap = nullptr;
+    int nr = 0, nz = 0;
+    float r0 = 0.0f, ir = 0.0f, z0 = 0.0f, iz = 0.0f;  // grid origin and nodes per cm
 };
+
+// ---- field map --------------------------------------------------------------
+// Bilinear between the nodes, the grid box clamps.  A transport step uses the
+// field at its midpoint, estimated along the straight line from the start; a
+// rotation the field at the state's point.  Without a map: the homogeneous bz.
+__device__ __forceinline__ float field_at(const Params &P, float r, float z)
+{
+    const float fr = fminf(fmaxf((r - P.r0) * P.ir, 0.0f), static_cast<float>(P.nr - 1));
+    const float fz = fminf(fmaxf((z - P.z0) * P.iz, 0.0f), static_cast<float>(P.nz - 1));
+    const int i = min(static_cast<int>(fr), P.nr - 2), j = min(static_cast<int>(fz), P.nz - 2);
+    const float wr = fr - static_cast<float>(i), wz = fz - static_cast<float>(j);
+    const float *F = P.bzmap + j * P.nr + i;
+    const float b00 = __ldg(F), b01 = __ldg(F + 1), b10 = __ldg(F + P.nr), b11 = __ldg(F + P.nr + 1);
+    return (1.0f - wz) * ((1.0f - wr) * b00 + wr * b01) + wz * ((1.0f - wr) * b10 + wr * b11);
+}
+
+template <bool EXT>
+__device__ __forceinline__ float point_bz(const Params &P, const TrackState &s)
+{
+    if (!EXT || !P.bzmap) return P.bz;
+    return field_at(P, hypotf(s.x.hi, s.y.hi), s.z);
+}
+
+template <bool EXT>
+__device__ __forceinline__ float step_bz(const Params &P, const TrackState &s, df x1)
+{
+    if (!EXT || !P.bzmap) return P.bz;
+    const float f = s.f;
+    if (!(fabsf(f) < 1.0f)) return point_bz<EXT>(P, s);
+    const float ir = rsqrtf((1.0f - f) * (1.0f + f));
+    const float h = 0.5f * df_to_f(df_add(x1, df_neg(s.x)));
+    return field_at(P, hypotf(s.x.hi + h, s.y.hi + h * f * ir), s.z + h * s.t * ir);
+}
 
 struct SeedsView {
     const float *alpha, *x, *y, *z, *snp, *tgl, *q2pt, *cov;
@@ -40,23 +79,33 @@ struct ResultsView {
 
 // Carry a hypothesis to the plane of layer l; returns false if it is lost.
 // chamber = -1 when z is outside the 5 stacks.
+// With EXT, the steps use the field map and a hypothesis in a chamber moves on
+// to the chamber's average radius (misalignment, Sec. 3).
+template <bool EXT>
 __device__ bool to_layer(TrackState &s, int l, const Params &P, int &chamber)
 {
     const df xl = layer_x_df(l);
-    if (!propagate(s, xl, P.bz)) return false;
+    if (!propagate(s, xl, step_bz<EXT>(P, s, xl))) return false;
     const float lim = xl.hi * half_sector_tan();
     if (fabsf(s.y.hi) > lim) {
         const int dir = s.y.hi > 0.0f ? 1 : -1;
         const int ns = (s.sector + dir + kSectors) % kSectors;
         const df d = dir > 0 ? df{kSectorWidthHi, kSectorWidthLo} : df{-kSectorWidthHi, -kSectorWidthLo};
-        if (!rotate(s, d, ns, P.bz)) return false;
-        if (!propagate(s, xl, P.bz)) return false;
+        if (!rotate(s, d, ns, point_bz<EXT>(P, s))) return false;
+        if (!propagate(s, xl, step_bz<EXT>(P, s, xl))) return false;
     }
     if (P.material && !material<false>(s)) return false;
     const float u = (s.z - kZMin) * (1.0f / kStackLength);
     if (u >= 0.0f && u < static_cast<float>(kStacks)) {
         const int stack = static_cast<int>(u);
         chamber = s.sector * (kStacks * kLayers) + stack * kLayers + l;
+        if (EXT && P.chamber_x) {
+            const float xc = __ldg(&P.chamber_x[chamber]);
+            if (!(xc == xl.hi && xl.lo == 0.0f)) {
+                const df xcd = {xc, 0.0f};
+                if (!propagate(s, xcd, step_bz<EXT>(P, s, xcd))) return false;
+            }
+        }
     } else {
         chamber = -1;
     }
@@ -139,17 +188,32 @@ struct ExtList {
 // keeps those inside the road's y/z bounds, and only those get the full test
 // (record read again from L1).  More than two bins (very wide roads) are
 // handled the same way, two at a time.
-template <int NH>
+// Road geometry of a hypothesis for the EXT kernels: its radius and the
+// straight-line slopes dy/dx = tan(phi), dz/dx = tan(lambda)/cos(phi).
+struct LinExt {
+    float xh, xl, fr, tr;
+};
+
+template <int NH, bool EXT>
 __device__ __forceinline__ void full_test(int pos, const IndexView &ix, float tt, float z, float yh, float yl,
                                           float n2, float syy_trk, float syz_trk, float c11, float vyy_res,
                                           int resmode, float dy_pred, float gate, float cut, float score,
-                                          int parent, int trig, ExtList<NH> &L)
+                                          int parent, int trig, const LinExt &e, ExtList<NH> &L)
 {
     const float4 a = __ldg(&ix.rec[2 * pos]);
     const float4 v = __ldg(&ix.rec[2 * pos + 1]);
     // per-interaction association (Sec. 4): other interactions' tracklets are not candidates
     const int ttrig = __float_as_int(v.w);
     if (trig >= 0 && ttrig >= 0 && ttrig != trig) return;
+    if (EXT && ix.recx) {
+        // a tracklet at its own radius (misalignment, Sec. 3): the fast linear
+        // extrapolation of the hypothesis to it, covariance as at the chamber
+        const float dx = __fsub_rn(__ldg(&ix.recx[pos]), e.xh) - e.xl;
+        const df yy = df_add_f(df{yh, yl}, dx * e.fr);
+        yh = yy.hi;
+        yl = yy.lo;
+        z = fmaf(dx, e.tr, z);
+    }
     const float ry = (__fsub_rn(a.x, yh) - yl) + tt * (z - a.y);
     const float rz = a.y - z;
     const float vyy = resmode ? vyy_res : v.x;
@@ -163,9 +227,10 @@ __device__ __forceinline__ void full_test(int pos, const IndexView &ix, float tt
     L.insert(score + chi2, parent, __float_as_int(a.w), pos, chi2);
 }
 
-template <int NH>
+template <int NH, bool EXT>
 __device__ void scan_candidates(const TrackState &s, int l, int chamber, int cbase, float score, const Params &P,
-                                const IndexView &ix, float vyy_max_in, float vzz_max, int trig, ExtList<NH> &L)
+                                const IndexView &ix, float vyy_max_in, float vzz_max, float dx_max, int trig,
+                                ExtList<NH> &L)
 {
     const float tt = layer_tilt_tan(l);
     const float f = s.f;
@@ -177,8 +242,17 @@ __device__ void scan_candidates(const TrackState &s, int l, int chamber, int cba
     const float syy_trk = s.c[0] - 2.0f * tt * c10 + tt * tt * c11;
     const float syz_trk = c10 - tt * c11;
     const float n2 = P.road * P.road;
-    const float W = P.road * sqrtf(fmaxf(syy_trk + vyy_max, 0.0f)) * 1.0001f + 1e-4f;
-    const float Rz = P.road * sqrtf(fmaxf(c11 + vzz_max, 0.0f)) * 1.0001f + 1e-4f;
+    float W = P.road * sqrtf(fmaxf(syy_trk + vyy_max, 0.0f)) * 1.0001f + 1e-4f;
+    float Rz = P.road * sqrtf(fmaxf(c11 + vzz_max, 0.0f)) * 1.0001f + 1e-4f;
+    LinExt e{s.x.hi, s.x.lo, 0.0f, 0.0f};
+    if (EXT && ix.recx) {
+        // tracklets up to dxb from this radius: the window holds their roads
+        e.fr = f / r;
+        e.tr = s.t / r;
+        const float dxb = dx_max + fabsf(df_to_f(df_add(s.x, df_neg(layer_x_df(l))))) + 1e-4f;
+        W += dxb * fabsf(e.fr) * 1.0001f;
+        Rz += dxb * fabsf(e.tr) * 1.0001f;
+    }
     const float dy_pred = kDriftLength * uu;
     const float gate = P.gate * sqrtf(kSigDy0 * kSigDy0 + kSigDy1 * kSigDy1 * uu * uu);
     const float z = s.z;
@@ -221,8 +295,8 @@ __device__ void scan_candidates(const TrackState &s, int l, int chamber, int cba
                 mask &= mask - 1u;
                 const int j = j0 + u;
                 const int pos = j < n0 ? beg0 + j : beg1 + (j - n0);
-                full_test<NH>(pos, ix, tt, z, yh, yl, n2, syy_trk, syz_trk, c11, vyy_res, P.resmode, dy_pred, gate,
-                              P.cut, score, 0, trig, L);
+                full_test<NH, EXT>(pos, ix, tt, z, yh, yl, n2, syy_trk, syz_trk, c11, vyy_res, P.resmode, dy_pred,
+                                   gate, P.cut, score, 0, trig, e, L);
             }
         }
     }
@@ -234,15 +308,16 @@ __device__ void scan_candidates(const TrackState &s, int l, int chamber, int cba
 // time), and every extension records its parent.  The candidate set, the
 // arithmetic and the selection order are those of one lane scanning its own
 // hypothesis; the work is spread evenly over the group.
-template <int G, int NH>
+template <int G, int NH, bool EXT>
 __device__ void scan_group(bool mine, const TrackState &s, int l, int chamber, int cbase, float score,
-                           const Params &P, const IndexView &ix, float vyy_max_in, float vzz_max, unsigned gmask,
-                           int q, int trig, ExtList<NH> &L)
+                           const Params &P, const IndexView &ix, float vyy_max_in, float vzz_max, float dx_max,
+                           unsigned gmask, int q, int trig, ExtList<NH> &L)
 {
     const float tt = layer_tilt_tan(l);
     // this lane's own road (used when it is broadcast)
     float z = 0, yh = 0, yl = 0, W = 0, Rz = 0, syy = 0, syz = 0, c11 = 0, vres = 0, dyp = 0, gate = 0;
     int r_lo = 0, r_hi = 0, b_lo = 0, b_hi = -1, base_ch = 0;
+    LinExt e{s.x.hi, s.x.lo, 0.0f, 0.0f};
     if (mine) {
         const float f = s.f;
         const float r = sqrtf((1.0f - f) * (1.0f + f));
@@ -255,6 +330,13 @@ __device__ void scan_group(bool mine, const TrackState &s, int l, int chamber, i
         syz = c10 - tt * c11;
         W = P.road * sqrtf(fmaxf(syy + vyy_max, 0.0f)) * 1.0001f + 1e-4f;
         Rz = P.road * sqrtf(fmaxf(c11 + vzz_max, 0.0f)) * 1.0001f + 1e-4f;
+        if (EXT && ix.recx) {
+            e.fr = f / r;
+            e.tr = s.t / r;
+            const float dxb = dx_max + fabsf(df_to_f(df_add(s.x, df_neg(layer_x_df(l))))) + 1e-4f;
+            W += dxb * fabsf(e.fr) * 1.0001f;
+            Rz += dxb * fabsf(e.tr) * 1.0001f;
+        }
         dyp = kDriftLength * uu;
         gate = P.gate * sqrtf(kSigDy0 * kSigDy0 + kSigDy1 * kSigDy1 * uu * uu);
         z = s.z;
@@ -281,6 +363,13 @@ __device__ void scan_group(bool mine, const TrackState &s, int l, int chamber, i
         const int hr_lo = __shfl_sync(gmask, r_lo, h, G), hr_hi = __shfl_sync(gmask, r_hi, h, G);
         const int hb_lo = __shfl_sync(gmask, b_lo, h, G), hb_hi = __shfl_sync(gmask, b_hi, h, G);
         const int hbase = __shfl_sync(gmask, base_ch, h, G);
+        LinExt he{};
+        if (EXT) {
+            he.xh = __shfl_sync(gmask, e.xh, h, G);
+            he.xl = __shfl_sync(gmask, e.xl, h, G);
+            he.fr = __shfl_sync(gmask, e.fr, h, G);
+            he.tr = __shfl_sync(gmask, e.tr, h, G);
+        }
         for (int b = hb_lo; b <= hb_hi; b += 2) {
             const int base = hbase + b * kRowsPerStack;
             const int beg0 = __ldg(&ix.offsets[base + hr_lo]);
@@ -314,8 +403,8 @@ __device__ void scan_group(bool mine, const TrackState &s, int l, int chamber, i
                     mask &= mask - 1u;
                     const int j = q + G * (u0 + u);
                     const int pos = j < n0 ? beg0 + j : beg1 + (j - n0);
-                    full_test<NH>(pos, ix, tt, hz, hyh, hyl, n2, hsyy, hsyz, hc11, hvres, P.resmode, hdyp, hgate,
-                                  P.cut, hscore, h, trig, L);
+                    full_test<NH, EXT>(pos, ix, tt, hz, hyh, hyl, n2, hsyy, hsyz, hc11, hvres, P.resmode, hdyp,
+                                       hgate, P.cut, hscore, h, trig, he, L);
                 }
             }
         }
@@ -496,7 +585,7 @@ __global__ void __launch_bounds__(256) k_seed_prepare(SeedsView sv, Params P, Re
     if (d.hi > 3.14159265f) d = df_add(d, df{-kTwoPiHi, -kTwoPiLo});
     if (d.hi < -3.14159265f) d = df_add(d, df{kTwoPiHi, kTwoPiLo});
     s.sector = sec;
-    if (!rotate(s, d, sec, P.bz)) {
+    if (!rotate(s, d, sec, P.bzmap ? field_at(P, hypotf(sx, sy), s.z) : P.bz)) {
         write_seed_result(o, sv, n, i, TRD_ST_PROP_FAIL);
         return;
     }
@@ -545,23 +634,23 @@ __device__ __forceinline__ bool start_seed(int i, int q, const SeedsView &sv, co
 
 // One layer of seed i for the group.  Returns true when the seed is finished
 // (result written).
-template <int G, int NH>
+template <int G, int NH, bool EXT>
 __device__ __forceinline__ bool layer_step(int i, int l, int q, unsigned gmask, const IndexView &ix, const Params &P,
                                            const ResultsView &o, int n, float *sm, int stride, float vyy_max,
-                                           float vzz_max, Lane &H)
+                                           float vzz_max, float dx_max, Lane &H)
 {
     TrackState &s = H.s;
     if (q == 0) save_state(sm, stride, s);
     int chamber = -1;
-    const bool live = H.alive && to_layer(s, l, P, chamber);
+    const bool live = H.alive && to_layer<EXT>(s, l, P, chamber);
     ExtList<NH> L;
     L.clear();
     if (G == 1) {
         if (live && chamber >= 0)
-            scan_candidates<NH>(s, l, chamber, H.cbase, H.score, P, ix, vyy_max, vzz_max, H.trig, L);
+            scan_candidates<NH, EXT>(s, l, chamber, H.cbase, H.score, P, ix, vyy_max, vzz_max, dx_max, H.trig, L);
     } else {
-        scan_group<G, NH>(live && chamber >= 0, s, l, chamber, H.cbase, H.score, P, ix, vyy_max, vzz_max, gmask, q,
-                          H.trig, L);
+        scan_group<G, NH, EXT>(live && chamber >= 0, s, l, chamber, H.cbase, H.score, P, ix, vyy_max, vzz_max,
+                               dx_max, gmask, q, H.trig, L);
     }
     if (live && H.nmiss < P.maxmiss) L.insert(H.score + P.pmiss, q, kMissing, -1, 0.0f);
 
@@ -647,6 +736,12 @@ __device__ __forceinline__ bool layer_step(int i, int l, int q, unsigned gmask, 
         if (my_id != kMissing) {
             const float4 a = __ldg(&ix.rec[2 * my_pos]);
             const float4 v = __ldg(&ix.rec[2 * my_pos + 1]);
+            if (EXT && ix.recx) {
+                // the precise transport to the matched tracklet's own radius
+                // before the update (a failed transport leaves the state)
+                const df xt = {__ldg(&ix.recx[my_pos]), 0.0f};
+                (void)propagate(s, xt, step_bz<EXT>(P, s, xt));
+            }
             float vyy = v.x;
             if (P.resmode) {
                 const float r = sqrtf((1.0f - s.f) * (1.0f + s.f));
@@ -673,7 +768,7 @@ __device__ __forceinline__ bool layer_step(int i, int l, int q, unsigned gmask, 
 // Persistent follower: every group loops over seeds taken from the launch's
 // counter and over their layers in one flattened loop, so a lane whose seed
 // ends takes the next seed instead of idling while its warp finishes.
-template <int G, int NH, int MINB>
+template <int G, int NH, int MINB, bool EXT>
 __global__ void __launch_bounds__(128, MINB) k_follow(SeedsView sv, IndexView ix, Params P, ResultsView o, int *counter)
 {
     extern __shared__ float smem[];
@@ -684,6 +779,7 @@ __global__ void __launch_bounds__(128, MINB) k_follow(SeedsView sv, IndexView ix
     float *sm = smem + g;
     const float vyy_max = __uint_as_float(__ldg(&ix.stats[0]));
     const float vzz_max = __uint_as_float(__ldg(&ix.stats[1]));
+    const float dx_max = EXT && ix.recx ? __uint_as_float(__ldg(&ix.stats[3])) : 0.0f;
     Lane H;
     int i = 0, l = 0;
     bool have = false;
@@ -695,7 +791,8 @@ __global__ void __launch_bounds__(128, MINB) k_follow(SeedsView sv, IndexView ix
             l = 0;
             if (!have) continue;
         }
-        if (layer_step<G, NH>(i, l, q, gmask, ix, P, o, sv.n, sm, groups, vyy_max, vzz_max, H)) have = false;
+        if (layer_step<G, NH, EXT>(i, l, q, gmask, ix, P, o, sv.n, sm, groups, vyy_max, vzz_max, dx_max, H))
+            have = false;
         ++l;
     }
 }
@@ -706,7 +803,7 @@ namespace trd_host {
 
 using namespace trd;
 
-template <int G, int NH, int MINB>
+template <int G, int NH, int MINB, bool EXT>
 static int launch(const trd_ctx *ctx, const SeedsView &sv, const IndexView &ix, const Params &P,
                   const ResultsView &o, cudaStream_t s, int block, int *counter)
 {
@@ -714,26 +811,60 @@ static int launch(const trd_ctx *ctx, const SeedsView &sv, const IndexView &ix, 
     const int groups = block / G;
     const size_t smem = sizeof(float) * 24 * groups;
     int per_sm = 0;
-    TRD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_follow<G, NH, MINB>, block, smem));
+    TRD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_follow<G, NH, MINB, EXT>, block, smem));
     per_sm = per_sm > 0 ? per_sm : 1;
     const long long need = (static_cast<long long>(sv.n) + groups - 1) / groups;
     const int grid = static_cast<int>(std::min<long long>(need, static_cast<long long>(ctx->sm_count) * per_sm));
     TRD_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), s));
     k_seed_prepare<<<(sv.n + 255) / 256, 256, 0, s>>>(sv, P, o);
     TRD_CUDA_TRY(cudaGetLastError());
-    k_follow<G, NH, MINB><<<grid, block, smem, s>>>(sv, ix, P, o, counter);
+    k_follow<G, NH, MINB, EXT><<<grid, block, smem, s>>>(sv, ix, P, o, counter);
     TRD_CUDA_TRY(cudaGetLastError());
     return TRD_OK;
 }
 
+template <bool EXT>
+static int dispatch(const trd_ctx *ctx, const SeedsView &sv, const IndexView &iv, const Params &P,
+                    const ResultsView &o, cudaStream_t s, int G, int mb, int block, int nhyp, int *counter)
+{
+    switch (G * 16 + mb) {
+    case 1 * 16 + 4: return nhyp == 1 ? launch<1, 1, 4, EXT>(ctx, sv, iv, P, o, s, block, counter) : TRD_EINVAL;
+    case 1 * 16 + 5: return nhyp == 1 ? launch<1, 1, 5, EXT>(ctx, sv, iv, P, o, s, block, counter) : TRD_EINVAL;
+    case 1 * 16 + 6: return nhyp == 1 ? launch<1, 1, 6, EXT>(ctx, sv, iv, P, o, s, block, counter) : TRD_EINVAL;
+    case 1 * 16 + 8: return nhyp == 1 ? launch<1, 1, 8, EXT>(ctx, sv, iv, P, o, s, block, counter) : TRD_EINVAL;
+    case 2 * 16 + 3: return launch<2, 2, 3, EXT>(ctx, sv, iv, P, o, s, block, counter);
+    case 2 * 16 + 4: return launch<2, 2, 4, EXT>(ctx, sv, iv, P, o, s, block, counter);
+    case 4 * 16 + 3: return launch<4, 4, 3, EXT>(ctx, sv, iv, P, o, s, block, counter);
+    case 4 * 16 + 4: return launch<4, 4, 4, EXT>(ctx, sv, iv, P, o, s, block, counter);
+    case 8 * 16 + 3: return launch<8, 8, 3, EXT>(ctx, sv, iv, P, o, s, block, counter);
+    case 8 * 16 + 4: return launch<8, 8, 4, EXT>(ctx, sv, iv, P, o, s, block, counter);
+    case 32 * 16 + 3: return launch<32, 8, 3, EXT>(ctx, sv, iv, P, o, s, block, counter);
+    case 32 * 16 + 4: return launch<32, 8, 4, EXT>(ctx, sv, iv, P, o, s, block, counter);
+    default: return TRD_EINVAL;
+    }
+}
+
 int follow_launch(const trd_ctx *ctx, const trd_seeds_t *seeds, const IndexView &iv, const trd_params_t *p,
                   trd_results_t *out, cudaStream_t s, int lanes_per_track, int block_threads, int min_blocks,
-                  int *counter, const int32_t *seed_offsets, int n_tf)
+                  int *counter, const int32_t *seed_offsets, int n_tf, const trd_alignment_t *align)
 {
     SeedsView sv{seeds->alpha, seeds->x, seeds->y, seeds->z, seeds->snp, seeds->tgl, seeds->q2pt, seeds->cov,
                  seeds->n, seed_offsets, n_tf, seeds->trigger};
     Params P{p->bz, p->n_sigma_road, p->chi2_cut, p->p_miss, p->dy_gate_sigma, p->n_hyp, p->max_missing,
              p->res_mode, p->material_on};
+    if (align) {
+        P.chamber_x = align->chamber_x;
+        if (align->bz_map) {
+            P.bzmap = align->bz_map;
+            P.nr = align->nr;
+            P.nz = align->nz;
+            P.r0 = align->r_min;
+            P.ir = static_cast<float>(align->nr - 1) / (align->r_max - align->r_min);
+            P.z0 = align->z_min;
+            P.iz = static_cast<float>(align->nz - 1) / (align->z_max - align->z_min);
+        }
+    }
+    const bool ext = iv.recx || P.chamber_x || P.bzmap;
     ResultsView o{out->alpha, out->x, out->par, out->cov, out->chi2, out->n_trk, out->n_miss, out->status,
                   out->tracklet_id};
     const int block = block_threads > 0 ? block_threads : 128;
@@ -741,21 +872,8 @@ int follow_launch(const trd_ctx *ctx, const trd_seeds_t *seeds, const IndexView 
     if (G <= 0) G = p->n_hyp <= 1 ? 1 : (p->n_hyp <= 2 ? 2 : (p->n_hyp <= 4 ? 4 : 8));
     if (G < p->n_hyp) return TRD_EINVAL;
     const int mb = min_blocks > 0 ? min_blocks : 4;
-    switch (G * 16 + mb) {
-    case 1 * 16 + 4: return p->n_hyp == 1 ? launch<1, 1, 4>(ctx, sv, iv, P, o, s, block, counter) : TRD_EINVAL;
-    case 1 * 16 + 5: return p->n_hyp == 1 ? launch<1, 1, 5>(ctx, sv, iv, P, o, s, block, counter) : TRD_EINVAL;
-    case 1 * 16 + 6: return p->n_hyp == 1 ? launch<1, 1, 6>(ctx, sv, iv, P, o, s, block, counter) : TRD_EINVAL;
-    case 1 * 16 + 8: return p->n_hyp == 1 ? launch<1, 1, 8>(ctx, sv, iv, P, o, s, block, counter) : TRD_EINVAL;
-    case 2 * 16 + 3: return launch<2, 2, 3>(ctx, sv, iv, P, o, s, block, counter);
-    case 2 * 16 + 4: return launch<2, 2, 4>(ctx, sv, iv, P, o, s, block, counter);
-    case 4 * 16 + 3: return launch<4, 4, 3>(ctx, sv, iv, P, o, s, block, counter);
-    case 4 * 16 + 4: return launch<4, 4, 4>(ctx, sv, iv, P, o, s, block, counter);
-    case 8 * 16 + 3: return launch<8, 8, 3>(ctx, sv, iv, P, o, s, block, counter);
-    case 8 * 16 + 4: return launch<8, 8, 4>(ctx, sv, iv, P, o, s, block, counter);
-    case 32 * 16 + 3: return launch<32, 8, 3>(ctx, sv, iv, P, o, s, block, counter);
-    case 32 * 16 + 4: return launch<32, 8, 4>(ctx, sv, iv, P, o, s, block, counter);
-    default: return TRD_EINVAL;
-    }
+    return ext ? dispatch<true>(ctx, sv, iv, P, o, s, G, mb, block, p->n_hyp, counter)
+               : dispatch<false>(ctx, sv, iv, P, o, s, G, mb, block, p->n_hyp, counter);
 }
 
 }  // namespace trd_host

@@ -32,9 +32,9 @@ k_index_count(const int32_t *__restrict__ ch, const float *__restrict__ y, const
               const float *__restrict__ dy, const float *__restrict__ vyy, const float *__restrict__ vzz,
               const float *__restrict__ vyz, int n, float inv_w, int nb, int32_t *__restrict__ bucket,
               int32_t *__restrict__ rank, int32_t *__restrict__ counts, uint32_t *__restrict__ stats,
-              const int32_t *__restrict__ toff, int n_tf)
+              const int32_t *__restrict__ toff, int n_tf, const float *__restrict__ xs)
 {
-    float myy = 0.0f, mzz = 0.0f;
+    float myy = 0.0f, mzz = 0.0f, mdx = 0.0f;
     int rejected = 0;
     const int stride = gridDim.x * blockDim.x;
     for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += stride * kIlp) {
@@ -56,9 +56,11 @@ k_index_count(const int32_t *__restrict__ ch, const float *__restrict__ y, const
         for (int u = 0; u < kIlp; ++u) {
             const int i = i0 + u * stride;
             if (i >= n) continue;
+            // a tracklet's radius (misalignment) and its offset from the layer's
+            const float xt = xs ? __ldg(&xs[i]) : 0.0f;
             const bool ok = c[u] >= 0 && c[u] < trd::kChambers && isfinite(yy[u]) && isfinite(zz[u]) &&
                             isfinite(dd[u]) && isfinite(a[u]) && isfinite(b[u]) && isfinite(cc[u]) &&
-                            a[u] >= 0.0f && b[u] >= 0.0f;
+                            a[u] >= 0.0f && b[u] >= 0.0f && isfinite(xt);
             if (!ok) {
                 bucket[i] = -1;
                 rank[i] = 0;
@@ -72,35 +74,43 @@ k_index_count(const int32_t *__restrict__ ch, const float *__restrict__ y, const
             rank[i] = atomicAdd(&counts[bk], 1);
             myy = fmaxf(myy, a[u]);
             mzz = fmaxf(mzz, b[u]);
+            if (xs) {
+                const trd::df xl = trd::layer_x_df(c[u] % trd::kLayers);
+                mdx = fmaxf(mdx, fabsf((xt - xl.hi) - xl.lo));
+            }
         }
     }
     // block reduction of the maxima and the rejected count
     for (int o = 16; o > 0; o >>= 1) {
         myy = fmaxf(myy, __shfl_xor_sync(0xffffffffu, myy, o));
         mzz = fmaxf(mzz, __shfl_xor_sync(0xffffffffu, mzz, o));
+        mdx = fmaxf(mdx, __shfl_xor_sync(0xffffffffu, mdx, o));
         rejected += __shfl_xor_sync(0xffffffffu, rejected, o);
     }
-    __shared__ float s_yy[kCountThreads / 32], s_zz[kCountThreads / 32];
+    __shared__ float s_yy[kCountThreads / 32], s_zz[kCountThreads / 32], s_dx[kCountThreads / 32];
     __shared__ int s_rej[kCountThreads / 32];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0) {
         s_yy[w] = myy;
         s_zz[w] = mzz;
+        s_dx[w] = mdx;
         s_rej[w] = rejected;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        float am = 0.0f, bm = 0.0f;
+        float am = 0.0f, bm = 0.0f, dm = 0.0f;
         int r = 0;
         for (int k = 0; k < kCountThreads / 32; ++k) {
             am = fmaxf(am, s_yy[k]);
             bm = fmaxf(bm, s_zz[k]);
+            dm = fmaxf(dm, s_dx[k]);
             r += s_rej[k];
         }
         // non-negative floats order like their bit patterns
         atomicMax(&stats[0], __float_as_uint(am));
         atomicMax(&stats[1], __float_as_uint(bm));
         if (r) atomicAdd(&stats[2], static_cast<uint32_t>(r));
+        if (xs) atomicMax(&stats[3], __float_as_uint(dm));
     }
 }
 
@@ -194,7 +204,7 @@ k_index_scatter(const float *__restrict__ y, const float *__restrict__ z, const 
                 const float *__restrict__ vyy, const float *__restrict__ vzz, const float *__restrict__ vyz,
                 int n, const int32_t *__restrict__ bucket, const int32_t *__restrict__ rank,
                 const int32_t *__restrict__ offsets, float4 *__restrict__ rec, const int32_t *__restrict__ toff,
-                int n_tf, const int32_t *__restrict__ trig)
+                int n_tf, const int32_t *__restrict__ trig, const float *__restrict__ xs, float *__restrict__ recx)
 {
     const int stride = gridDim.x * blockDim.x;
     for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += stride * kIlp) {
@@ -217,6 +227,7 @@ k_index_scatter(const float *__restrict__ y, const float *__restrict__ z, const 
             rec[2 * pos] = make_float4(__ldg(&y[i]), __ldg(&z[i]), __ldg(&dy[i]), __int_as_float(local));
             rec[2 * pos + 1] = make_float4(__ldg(&vyy[i]), __ldg(&vzz[i]), __ldg(&vyz[i]),
                                            __int_as_float(trig ? __ldg(&trig[i]) : -1));
+            if (xs) recx[pos] = __ldg(&xs[i]);
         }
     }
 }
@@ -237,7 +248,7 @@ int index_rebuild_launch(trd_index *idx, const trd_tracklets_t *t, cudaStream_t 
     if (n > 0) {
         k_index_count<<<grid_n, kCountThreads, 0, s>>>(t->chamber, t->y, t->z, t->dy, t->vyy, t->vzz, t->vyz, n,
                                                        idx->inv_w, idx->nb, idx->bucket, idx->rank, idx->counts,
-                                                       idx->stats, idx->toff, idx->n_tf);
+                                                       idx->stats, idx->toff, idx->n_tf, t->x);
         TRD_CUDA_TRY(cudaGetLastError());
     }
     const int m = scan_blocks_for(idx->n_buckets);
@@ -250,9 +261,10 @@ int index_rebuild_launch(trd_index *idx, const trd_tracklets_t *t, cudaStream_t 
     if (n > 0) {
         k_index_scatter<<<grid_n, kCountThreads, 0, s>>>(t->y, t->z, t->dy, t->vyy, t->vzz, t->vyz, n, idx->bucket,
                                                          idx->rank, idx->offsets, idx->rec, idx->toff, idx->n_tf,
-                                                         t->trigger);
+                                                         t->trigger, t->x, idx->recx);
         TRD_CUDA_TRY(cudaGetLastError());
     }
+    idx->has_x = t->x != nullptr;
     return TRD_OK;
 }
 
@@ -324,6 +336,7 @@ extern "C" int trd_index_build_noalloc(const trd_tracklets_t *t, float y_bin_wid
     if (!(y_bin_width >= kNoAllocMinBinWidth) || !isfinite(y_bin_width)) return TRD_EINVAL;
     if (reinterpret_cast<uintptr_t>(records) % 16 != 0) return TRD_EINVAL;
     if (t->n > 0 && (!t->chamber || !t->y || !t->z || !t->dy || !t->vyy || !t->vzz || !t->vyz)) return TRD_EINVAL;
+    if (t->x) return TRD_EINVAL;  // no room for per-tracklet radii in the caller's buffers
     int dev = 0;
     TRD_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kNoAllocMaxDevices) return TRD_ECUDA;
@@ -350,7 +363,7 @@ extern "C" int trd_index_build_noalloc(const trd_tracklets_t *t, float y_bin_wid
     const int grid_n = n > 0 ? std::min((n + kCountThreads * kIlp - 1) / (kCountThreads * kIlp), d.sm_count * 8) : 0;
     if (n > 0) {
         k_index_count<<<grid_n, kCountThreads, 0, s>>>(t->chamber, t->y, t->z, t->dy, t->vyy, t->vzz, t->vyz, n,
-                                                       inv_w, nb, bucket, rank, counts, stats, nullptr, 1);
+                                                       inv_w, nb, bucket, rank, counts, stats, nullptr, 1, nullptr);
         TRD_CUDA_TRY(cudaGetLastError());
     }
     k_scan_reduce<<<m, kScanThreads, 0, s>>>(counts, n_buckets, partials);
@@ -361,7 +374,7 @@ extern "C" int trd_index_build_noalloc(const trd_tracklets_t *t, float y_bin_wid
     TRD_CUDA_TRY(cudaGetLastError());
     if (n > 0) {
         k_index_scatter<<<grid_n, kCountThreads, 0, s>>>(t->y, t->z, t->dy, t->vyy, t->vzz, t->vyz, n, bucket, rank,
-                                                         offsets, rec, nullptr, 1, t->trigger);
+                                                         offsets, rec, nullptr, 1, t->trigger, nullptr, nullptr);
         TRD_CUDA_TRY(cudaGetLastError());
     }
     return TRD_OK;

@@ -27,6 +27,7 @@ struct TrackletSoA {
     const int32_t *ch;
     const float *y, *z, *vyy, *vzz, *vyz;
     int n;
+    const float *x;  // own radius per tracklet (misalignment), or null
 };
 
 struct RefitOut {
@@ -65,7 +66,7 @@ __global__ void __launch_bounds__(128) k_refit(RefitIn in, TrackletSoA T, RefitP
 
     // ids and the tracklets they name, all loads issued up front
     int ids[kLayers], ch[kLayers];
-    float ty[kLayers], tz[kLayers], tvy[kLayers], tvz[kLayers], tvyz[kLayers];
+    float ty[kLayers], tz[kLayers], tvy[kLayers], tvz[kLayers], tvyz[kLayers], tx[kLayers];
     int ntrk = 0, ltop = -1;
     bool bad = false;
 #pragma unroll
@@ -80,6 +81,7 @@ __global__ void __launch_bounds__(128) k_refit(RefitIn in, TrackletSoA T, RefitP
         tvy[l] = have ? T.vyy[j] : 0.0f;
         tvz[l] = have ? T.vzz[j] : 0.0f;
         tvyz[l] = have ? T.vyz[j] : 0.0f;
+        tx[l] = have && T.x ? T.x[j] : 0.0f;
         if (j >= 0) {
             ++ntrk;
             ltop = l;
@@ -113,7 +115,7 @@ __global__ void __launch_bounds__(128) k_refit(RefitIn in, TrackletSoA T, RefitP
             // this layer's tracklet, selected without indexing the register
             // arrays by a runtime layer number
             int jl = -1, cl = 0;
-            float yl = 0.0f, zl = 0.0f, vyl = 0.0f, vzl = 0.0f, vyzl = 0.0f;
+            float yl = 0.0f, zl = 0.0f, vyl = 0.0f, vzl = 0.0f, vyzl = 0.0f, xtl = 0.0f;
 #pragma unroll
             for (int q = 0; q < kLayers; ++q)
                 if (q == l) {
@@ -124,8 +126,10 @@ __global__ void __launch_bounds__(128) k_refit(RefitIn in, TrackletSoA T, RefitP
                     vyl = tvy[q];
                     vzl = tvz[q];
                     vyzl = tvyz[q];
+                    xtl = tx[q];
                 }
-            const df xl = layer_x_df(l);
+            // a layer's plane: its tracklet's own radius when given (misalignment)
+            const df xl = (jl >= 0 && T.x) ? df{xtl, 0.0f} : layer_x_df(l);
             if (!propagate(s, xl, P.bz)) { status = TRD_RF_PROP_FAIL; break; }
             int target = s.sector;
             if (jl >= 0)
@@ -186,7 +190,7 @@ extern "C" int trd_refit(trd_ctx_t *ctx, const trd_results_t *tracks, int32_t n,
     TRD_CUDA_TRY(cudaSetDevice(ctx->device));
     trd::RefitIn in{tracks->alpha, tracks->x, tracks->par, tracks->cov, tracks->status, tracks->tracklet_id, n};
     trd::TrackletSoA T{tracklets->chamber, tracklets->y, tracklets->z, tracklets->vyy, tracklets->vzz,
-                       tracklets->vyz, tracklets->n};
+                       tracklets->vyz, tracklets->n, tracklets->x};
     trd::RefitParams P{params->bz, cov_scale, params->res_mode, params->material_on};
     trd::RefitOut o{out->alpha, out->x, out->par, out->cov, out->chi2, out->n_upd, out->status};
     const int threads = 128;

@@ -67,7 +67,8 @@ size_t io_bytes(int n_seeds, int n_trk)
            align_up(sizeof(int32_t) * 9 * static_cast<size_t>(n_seeds)) +  // int results
            align_up(28 * static_cast<size_t>(n_trk)) +                     // tracklets
            align_up(sizeof(int32_t) * static_cast<size_t>(n_seeds)) +      // seed interaction ids
-           align_up(sizeof(int32_t) * static_cast<size_t>(n_trk));         // tracklet interaction ids
+           align_up(sizeof(int32_t) * static_cast<size_t>(n_trk)) +        // tracklet interaction ids
+           align_up(sizeof(float) * static_cast<size_t>(n_trk));           // tracklet radii
 }
 
 // bytes of an index for n_trk tracklets (records + build scratch + buckets)
@@ -75,7 +76,7 @@ size_t index_bytes(int n_trk, float w)
 {
     const size_t nb = static_cast<size_t>(ceilf(2.0f * 66.0f / w));
     const size_t buckets = static_cast<size_t>(TRD_N_CHAMBERS) * 18 * nb;
-    return 40 * static_cast<size_t>(n_trk) + 8 * buckets + 4096;
+    return 44 * static_cast<size_t>(n_trk) + 8 * buckets + 4096;  // records, radii, bucket, rank
 }
 
 void CUDART_CB on_done(void *p)
@@ -125,6 +126,8 @@ int start_request(trd_server *S, Slot &slot, Request *r)
     int32_t *dtrig_s = reinterpret_cast<int32_t *>(p);
     p += align_up(sizeof(int32_t) * static_cast<size_t>(n));
     int32_t *dtrig_t = reinterpret_cast<int32_t *>(p);
+    p += align_up(sizeof(int32_t) * static_cast<size_t>(m));
+    float *dx_t = reinterpret_cast<float *>(p);
     // seeds: alpha x y z snp tgl q2pt cov[15] (22 rows of n)
     const float *hs[7] = {r->seeds.alpha, r->seeds.x, r->seeds.y, r->seeds.z, r->seeds.snp, r->seeds.tgl,
                           r->seeds.q2pt};
@@ -138,6 +141,8 @@ int start_request(trd_server *S, Slot &slot, Request *r)
         TRD_CUDA_TRY(cudaMemcpyAsync(dtrig_s, r->seeds.trigger, sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
     if (m && r->trk.trigger)
         TRD_CUDA_TRY(cudaMemcpyAsync(dtrig_t, r->trk.trigger, sizeof(int32_t) * m, cudaMemcpyHostToDevice, st));
+    if (m && r->trk.x)
+        TRD_CUDA_TRY(cudaMemcpyAsync(dx_t, r->trk.x, sizeof(float) * m, cudaMemcpyHostToDevice, st));
     trd_seeds_t dseeds{ds, ds + n, ds + 2 * static_cast<size_t>(n), ds + 3 * static_cast<size_t>(n),
                        ds + 4 * static_cast<size_t>(n), ds + 5 * static_cast<size_t>(n),
                        ds + 6 * static_cast<size_t>(n), ds + 7 * static_cast<size_t>(n), n,
@@ -151,7 +156,7 @@ int start_request(trd_server *S, Slot &slot, Request *r)
                                             cudaMemcpyHostToDevice, st));
     trd_tracklets_t dtrk{dch, dtf, dtf + m, dtf + 2 * static_cast<size_t>(m), dtf + 3 * static_cast<size_t>(m),
                          dtf + 4 * static_cast<size_t>(m), dtf + 5 * static_cast<size_t>(m), m,
-                         r->trk.trigger ? dtrig_t : nullptr};
+                         r->trk.trigger ? dtrig_t : nullptr, r->trk.x ? dx_t : nullptr};
     trd_results_t dres{dr, dr + n, dr + 2 * static_cast<size_t>(n), dr + 7 * static_cast<size_t>(n),
                        dr + 22 * static_cast<size_t>(n), di, di + n, di + 2 * static_cast<size_t>(n),
                        di + 3 * static_cast<size_t>(n)};

@@ -33,7 +33,9 @@ struct trd_index {
     int32_t *offsets;   // [n_buckets + 1] exclusive prefix of bucket sizes
     float4 *rec;        // [2 * capacity]: per tracklet, in bucket order, a 32-byte
                         // record {y, z, dy, id (bits)}, {vyy, vzz, vyz, 0}
-    uint32_t *stats;    // [4]: max vyy bits, max vzz bits, rejected count, spare
+    uint32_t *stats;    // [4]: max vyy bits, max vzz bits, rejected count, max |x - x_layer| bits
+    float *recx;        // [capacity]: per tracklet, in bucket order, its radius (when given)
+    int has_x;          // the last build's tracklets carried radii
     // build scratch
     int32_t *bucket;    // [capacity] bucket of each input tracklet (-1: rejected)
     int32_t *rank;      // [capacity] position inside its bucket
@@ -51,6 +53,7 @@ struct IndexView {
     const uint32_t *stats;
     int32_t nb;
     float inv_w;
+    const float *recx = nullptr;  // radius per record, or null (every tracklet at its layer's radius)
 };
 
 namespace trd_host {
@@ -58,7 +61,7 @@ int index_rebuild_launch(trd_index *idx, const trd_tracklets_t *t, cudaStream_t 
 int follow_launch(const trd_ctx *ctx, const trd_seeds_t *seeds, const IndexView &iv,
                   const trd_params_t *p, trd_results_t *out, cudaStream_t s, int lanes_per_track,
                   int block_threads, int min_blocks, int *counter, const int32_t *seed_offsets = nullptr,
-                  int n_tf = 1);
+                  int n_tf = 1, const trd_alignment_t *align = nullptr);
 int *next_counter(trd_ctx *ctx);
 int index_alloc(trd_ctx *ctx, int32_t capacity, float y_bin_width, int32_t n_tf, trd_index **out);
 void index_release(trd_index *x);

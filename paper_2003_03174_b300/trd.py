@@ -24,7 +24,7 @@ EXPORTED = [
     "trd_geometry", "trd_version", "trd_index_copy_out", "trd_batch_create", "trd_batch_run",
     "trd_batch_free", "trd_server_create", "trd_server_submit", "trd_server_poll", "trd_server_wait",
     "trd_server_stats", "trd_server_destroy", "trd_index_build_noalloc", "trd_measure_fp32_peak",
-    "trd_refit", "trd_residuals", "trd_voxel_solve",
+    "trd_refit", "trd_residuals", "trd_voxel_solve", "trd_follow_aligned",
 ]
 TPC_ROWS, VOX_Y_BINS, VOX_Z_BINS, VOX_SUMS = 152, 15, 5, 11
 N_VOXELS = 2 * 18 * TPC_ROWS * VOX_Y_BINS * VOX_Z_BINS
@@ -43,7 +43,12 @@ class Seeds(C.Structure):
 
 class Tracklets(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in ("chamber", "y", "z", "dy", "vyy", "vzz", "vyz")] + [
-        ("n", C.c_int32), ("trigger", C.c_void_p)]
+        ("n", C.c_int32), ("trigger", C.c_void_p), ("x", C.c_void_p)]
+
+
+class Alignment(C.Structure):
+    _fields_ = [("chamber_x", C.c_void_p), ("bz_map", C.c_void_p), ("nr", C.c_int32), ("nz", C.c_int32),
+                ("r_min", C.c_float), ("r_max", C.c_float), ("z_min", C.c_float), ("z_max", C.c_float)]
 
 
 class Params(C.Structure):
@@ -107,6 +112,8 @@ def lib():
         L.trd_follow.argtypes = [vp, C.POINTER(Seeds), vp, C.POINTER(Params), C.POINTER(Results), vp]
         L.trd_follow_tuned.argtypes = [vp, C.POINTER(Seeds), vp, C.POINTER(Params),
                                        C.POINTER(Results), vp, C.POINTER(Launch)]
+        L.trd_follow_aligned.argtypes = [vp, C.POINTER(Seeds), vp, C.POINTER(Params), C.POINTER(Alignment),
+                                         C.POINTER(Results), vp, C.POINTER(Launch)]
         L.trd_geometry.argtypes = [C.POINTER(C.c_double), C.c_int]
         L.trd_index_copy_out.argtypes = [vp, vp, vp]
         L.trd_batch_create.argtypes = [vp, i32, vp, vp, C.POINTER(Seeds), C.POINTER(Tracklets),
@@ -180,7 +187,17 @@ def seeds_struct(s: dict) -> Seeds:
 def tracklets_struct(t: dict) -> Tracklets:
     n = int(t["chamber"].shape[0])
     return Tracklets(*[_ptr(t[k]) for k in ("chamber", "y", "z", "dy", "vyy", "vzz", "vyz")], n,
-                     _ptr(t.get("trigger")))
+                     _ptr(t.get("trigger")), _ptr(t.get("x")))
+
+
+def alignment_struct(chamber_x=None, field=None) -> Alignment:
+    """chamber_x: device float [540] or None; field: dict(bz = device float
+    [nz, nr], r_min, r_max, z_min, z_max) or None."""
+    if field is None:
+        return Alignment(_ptr(chamber_x), None, 0, 0, 0.0, 0.0, 0.0, 0.0)
+    nz, nr = int(field["bz"].shape[0]), int(field["bz"].shape[1])
+    return Alignment(_ptr(chamber_x), _ptr(field["bz"]), nr, nz, float(field["r_min"]), float(field["r_max"]),
+                     float(field["z_min"]), float(field["z_max"]))
 
 
 def alloc_results(n: int, device="cuda"):
@@ -300,7 +317,8 @@ class Server:
         ss = Seeds(*[_hptr(seeds[k]) for k in ("alpha", "x", "y", "z", "snp", "tgl", "q2pt", "cov")], n,
                    _hptr(seeds["trigger"]) if seeds.get("trigger") is not None else None)
         ts = Tracklets(*[_hptr(tracklets[k]) for k in ("chamber", "y", "z", "dy", "vyy", "vzz", "vyz")], m,
-                       _hptr(tracklets["trigger"]) if tracklets.get("trigger") is not None else None)
+                       _hptr(tracklets["trigger"]) if tracklets.get("trigger") is not None else None,
+                       _hptr(tracklets["x"]) if tracklets.get("x") is not None else None)
         rs = Results(*[_hptr(results[k]) for k in ("alpha", "x", "par", "cov", "chi2", "n_trk",
                                                    "n_miss", "status", "tracklet_id")])
         t = C.c_uint64()
@@ -405,11 +423,20 @@ class Context:
 
     def follow(self, seeds: dict, index: Index, params: dict, results: dict | None = None,
                stream=None, lanes_per_track: int = 0, block_threads: int = 0,
-               min_blocks_per_sm: int = 0) -> dict:
+               min_blocks_per_sm: int = 0, chamber_x=None, field=None) -> dict:
+        """trd_follow (trd_follow_tuned with a launch shape; trd_follow_aligned
+        with chamber radii and/or a field map, see alignment_struct)."""
         n = int(seeds["alpha"].shape[0])
         if results is None:
             results = alloc_results(n, device=seeds["alpha"].device)
         ss, ps, rs = seeds_struct(seeds), params_struct(params), results_struct(results)
+        if chamber_x is not None or field is not None:
+            al = alignment_struct(chamber_x, field)
+            ln = Launch(int(lanes_per_track), int(block_threads), int(min_blocks_per_sm))
+            rc = lib().trd_follow_aligned(self.handle, C.byref(ss), index.handle, C.byref(ps), C.byref(al),
+                                          C.byref(rs), _stream_handle(stream), C.byref(ln))
+            _check("trd_follow_aligned", rc)
+            return results
         if lanes_per_track or block_threads or min_blocks_per_sm:
             ln = Launch(int(lanes_per_track), int(block_threads), int(min_blocks_per_sm))
             rc = lib().trd_follow_tuned(self.handle, C.byref(ss), index.handle, C.byref(ps),

@@ -184,3 +184,26 @@ def test_field_map_step_agrees_with_runge_kutta():
         assert ok2
         worse += abs(out2[2] - Y) > 3 * abs(out[2] - Y) + 1e-4
     assert worse > 10
+
+
+def test_refit_at_the_tracklet_radii_recovers_the_truth():
+    """The TRD-only refit of misaligned noiseless tracks ends at layer 0's
+    tracklet radius, on the truth helix there."""
+    p, tf = _misaligned(seed=10)
+    r = O.follow(tf.seeds, tf.tracklets, p, chamber_x=tf.chamber_x)
+    rf = O.refit(r, tf.tracklets, p)
+    ok = np.nonzero((tf.truth_ids >= 0).all(1) & (rf["status"] == 0))[0]
+    assert ok.size > 200
+    x0 = tf.tracklets["x"][tf.truth_ids[ok, 0]].astype(np.float64)
+    np.testing.assert_array_equal(rf["x"][ok], x0)
+    y, z, f, t, k, good = G.truth_at_plane({key: v[ok] for key, v in tf.truth.items()}, rf["alpha"][ok], x0)
+    assert good.all()
+    sig = np.sqrt(rf["cov"][[0, 2, 5], :][:, ok])
+    assert np.all(np.abs(rf["par"][0][ok] - y) < 2e-3 * sig[0] + 1e-5)
+    assert np.all(np.abs(rf["par"][1][ok] - z) < 2e-3 * sig[1] + 1e-5)
+    assert np.all(np.abs(rf["par"][2][ok] - f) < 2e-3 * sig[2] + 1e-7)
+    # ignoring the radii, the refit is pulled off the truth
+    nox = {k_: v for k_, v in tf.tracklets.items() if k_ != "x"}
+    rf0 = O.refit(r, nox, p)
+    y0, *_ = G.truth_at_plane({key: v[ok] for key, v in tf.truth.items()}, rf0["alpha"][ok], np.full(ok.size, 300.0))
+    assert np.median(np.abs(rf0["par"][0][ok] - y0) / sig[0]) > 0.1

@@ -73,6 +73,8 @@ PINNED = [
      "    return field_at(P, hypot(st[1], st[2]), st[3]);"),
     ("field map axes swapped", "    return (1 - wz) * ((1 - wr) * F[j * nr + i] + wr * F[j * nr + i + 1]) +",
      "    return (1 - wr) * ((1 - wz) * F[j * nr + i] + wz * F[j * nr + i + 1]) +"),
+    ("refit at the nominal radius", "const double xl = (j >= 0 && T->x) ? (double)T->x[j] : layer_x(l);",
+     "const double xl = layer_x(l);"),
 ]
 
 UNPINNED = [
@@ -117,6 +119,7 @@ PINS = [
     lambda: M.test_nominal_radii_reproduce_the_aligned_follower(),
     lambda: M.test_uniform_field_map_is_the_homogeneous_field(),
     lambda: M.test_field_map_step_agrees_with_runge_kutta(),
+    lambda: M.test_refit_at_the_tracklet_radii_recovers_the_truth(),
 ]
 
 
