@@ -242,8 +242,10 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     ctx = trd.Context(local)
 
+    align = args.alignment
     tf = make_workload(WORKLOAD, seed=rank_workload_seed(rank),  # each rank: its own timeframe
-                       n_interactions=args.association)
+                       n_interactions=args.association, misalign=0.5 if align else 0.0,
+                       x_jitter=0.1 if align else 0.0)
     seeds = trd.to_device(tf.seeds, dev)
     trk = trd.to_device(tf.tracklets, dev)
     n = tf.n_seeds
@@ -259,16 +261,24 @@ def run_ours(args):
         bin_width = tuned["y_bin_width"]
     index = ctx.index_create(tf.n_tracklets, bin_width)
     res = trd.alloc_results(n, dev)
+    # misalignment and field map (Sec. 3): chamber radii and a Bz(r, z) map
+    # for trd_follow_aligned (the tracklets carry their radii)
+    akw = {}
+    if align:
+        from synth.timeframe import field_map
+        fm = field_map(tf.params["bz"])
+        akw = dict(chamber_x=torch.from_numpy(tf.chamber_x).to(dev),
+                   field=dict(fm, bz=torch.from_numpy(fm["bz"]).to(dev)))
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     def step():
         index.rebuild(trk, stream=stream)
-        ctx.follow(seeds, index, tf.params, results=res, stream=stream, **shape)
+        ctx.follow(seeds, index, tf.params, results=res, stream=stream, **shape, **akw)
 
     # the whole step (index rebuild + follow) as one CUDA-graph replay: the
     # library's single-timeframe batch
     graph = None
-    if not args.no_graph:
+    if not args.no_graph and not align:  # the graph batch takes no alignment table or map
         graph = ctx.batch_create(seeds, trk, [0, n], [0, tf.n_tracklets], tf.params, res,
                                  y_bin_width=bin_width, **shape)
 
@@ -291,7 +301,7 @@ def run_ours(args):
                 if split:
                     index.rebuild(trk, stream=stream)
                     ev[k][1].record(stream)
-                    ctx.follow(seeds, index, tf.params, results=res, stream=stream, **shape)
+                    ctx.follow(seeds, index, tf.params, results=res, stream=stream, **shape, **akw)
                 else:
                     run_step()
                     ev[k][1].record(stream)
@@ -383,6 +393,8 @@ def run_ours(args):
                                    f"N=1, 3-sigma road, chi2<15, <=2 missing",
                        "seeds_per_rank": n, "tracklets_per_rank": tf.n_tracklets,
                        "interactions": args.association or None,
+                       "alignment": "misaligned chambers (+-0.5 cm), tracklet radii (+-0.1 cm), Bz(r,z) map"
+                       if align else None,
                        "matched_per_rank_step": matched, "l2": "flushed (512 MB write) between steps",
                        "index_y_bin_cm": bin_width or 2.0, "launch": shape,
                        "autotuned": tuned is not None,
@@ -393,7 +405,9 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h),
                     "path": "trd_server_submit/wait with pinned host buffers, 4 requests in flight "
-                            "(copies in, index rebuild, follow, copies out per request)"},
+                            "(copies in, index rebuild, follow, copies out per request)" +
+                            (" (tracklet radii only: the server takes no chamber table or field map)"
+                             if align else "")},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
             "seeds_per_s": n * ws * args.steps / total_s,
@@ -816,6 +830,8 @@ def main():
     ap.add_argument("--min-count", type=int, default=50, help="clusters a voxel needs to be solved")
     ap.add_argument("--cpu-sample-tracks", type=int, default=60_000)
     ap.add_argument("--n-tf", type=int, default=64)
+    ap.add_argument("--alignment", action="store_true",
+                    help="misaligned chambers, per-tracklet radii and a field map (trd_follow_aligned)")
     ap.add_argument("--association", type=int, default=0,
                     help="interactions per timeframe (per-interaction association); 0 = off")
     ap.add_argument("--n-payloads", type=int, default=16)

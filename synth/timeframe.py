@@ -383,16 +383,28 @@ def make_timeframe(n_seeds: int, seed: int = 0, noise: float = 0.2, bz: float = 
 
 
 def make_workload(name: str, seed: int = 0, n_seeds: int | None = None,
-                  n_interactions: int = 0) -> Timeframe:
+                  n_interactions: int = 0, misalign: float = 0.0, x_jitter: float = 0.0) -> Timeframe:
     """One of the named workloads (tiny, timeframe, calibration), optionally
-    with a different seed count (same distributions) and with interaction ids
-    (n_interactions > 0: per-interaction association, Sec. 4)."""
+    with a different seed count (same distributions), with interaction ids
+    (n_interactions > 0: per-interaction association, Sec. 4) and with
+    misaligned chambers (misalign, x_jitter in cm: per-tracklet radii)."""
     w = WORKLOADS[name]
     params = default_params(0.5, n_sigma_road=w["road"], chi2_cut=w["chi2_cut"],
                             n_hyp=w["n_hyp"], max_missing=w["max_missing"])
     return make_timeframe(n_seeds or w["n_seeds"], seed=seed, noise=w["noise"],
                           distortion=w["distortion"], sys_y=2.0 if w["distortion"] else 0.0,
-                          name=name, params=params, n_interactions=n_interactions)
+                          name=name, params=params, n_interactions=n_interactions,
+                          misalign=misalign, x_jitter=x_jitter)
+
+
+def field_map(b0: float = 0.5) -> dict:
+    """A Bz(r, z) map for the misalignment/field-map workloads: b0 in the
+    middle, falling 15 % towards |z| = 400 cm, rising 5 % per metre in r, on
+    an 18 x 41 grid over r in [250, 420] cm and z in [-400, 400] cm."""
+    rs, zs = np.linspace(250.0, 420.0, 18), np.linspace(-400.0, 400.0, 41)
+    R, Z = np.meshgrid(rs, zs)
+    bz = (b0 * (1.0 - 0.15 * (Z / 400.0) ** 2) * (1.0 + 0.05 * (R - 300.0) / 100.0)).astype(np.float32)
+    return dict(bz=bz, r_min=250.0, r_max=420.0, z_min=-400.0, z_max=400.0)
 
 
 def batched_seed_counts(n_tf=64, lo=5_000, hi=400_000, seed=0):
