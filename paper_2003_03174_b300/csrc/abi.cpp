@@ -134,6 +134,16 @@ int trd_ctx_create(int device, trd_ctx_t **ctx)
     c->l2_bytes = static_cast<size_t>(prop.l2CacheSize);
     c->launch_seq = 0;
     c->counters = nullptr;
+    // the follower and the server take stream-ordered scratch from the
+    // device's default pool on every call: keep freed blocks in the pool
+    // (the default threshold of 0 returns them to the system at every
+    // synchronisation, and the next call maps fresh memory)
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t keep = ~0ull;
+        (void)cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    (void)cudaGetLastError();
     if (cudaMalloc(&c->counters, sizeof(int32_t) * kCounterSlots) != cudaSuccess) {
         (void)cudaGetLastError();
         delete c;
