@@ -96,25 +96,42 @@ int trd_batch_create(trd_ctx_t *ctx, int32_t n_tf, const int32_t *seed_offsets, 
         return TRD_EINVAL;
     }
 
-    cudaStream_t cs = nullptr;
-    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+    // the graph: the seeds' pre-pass on a branch beside the index build (it
+    // does not read the index), joined before the follower
+    cudaStream_t cs = nullptr, cs2 = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&cs2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess) {
+        if (cs) cudaStreamDestroy(cs);
+        if (cs2) cudaStreamDestroy(cs2);
+        if (fork) cudaEventDestroy(fork);
+        (void)cudaGetLastError();
         release(b);
         return TRD_ECUDA;
     }
     bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     if (ok) {
-        rc = trd_host::index_rebuild_launch(b->index, tracklets, cs);
-        if (!rc) {
+        ok = cudaEventRecord(fork, cs) == cudaSuccess && cudaStreamWaitEvent(cs2, fork, 0) == cudaSuccess;
+        if (ok) rc = trd_host::prepare_launch(seeds, params, results, cs2);
+        if (ok && !rc) ok = cudaEventRecord(join, cs2) == cudaSuccess;
+        if (ok && !rc) rc = trd_host::index_rebuild_launch(b->index, tracklets, cs);
+        if (ok && !rc) ok = cudaStreamWaitEvent(cs, join, 0) == cudaSuccess;
+        if (ok && !rc) {
             IndexView iv{b->index->offsets, b->index->rec, b->index->stats, b->index->nb, b->index->inv_w,
                          tracklets->x ? b->index->recx : nullptr};
             rc = trd_host::follow_launch(ctx, seeds, iv, params, results, cs, launch ? launch->lanes_per_track : 0,
                                          launch ? launch->block_threads : 0, launch ? launch->min_blocks_per_sm : 0,
-                                         b->counter, n_tf > 1 ? b->soff : nullptr, n_tf);
+                                         b->counter, n_tf > 1 ? b->soff : nullptr, n_tf, nullptr, false);
         }
         const bool ended = cudaStreamEndCapture(cs, &b->graph) == cudaSuccess;
-        ok = !rc && ended && cudaGraphInstantiate(&b->exec, b->graph, 0) == cudaSuccess;
+        ok = ok && !rc && ended && cudaGraphInstantiate(&b->exec, b->graph, 0) == cudaSuccess;
     }
     cudaStreamDestroy(cs);
+    cudaStreamDestroy(cs2);
+    cudaEventDestroy(fork);
+    cudaEventDestroy(join);
     if (!ok) {
         (void)cudaGetLastError();
         release(b);

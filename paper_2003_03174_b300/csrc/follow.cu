@@ -805,7 +805,7 @@ using namespace trd;
 
 template <int G, int NH, int MINB, bool EXT>
 static int launch(const trd_ctx *ctx, const SeedsView &sv, const IndexView &ix, const Params &P,
-                  const ResultsView &o, cudaStream_t s, int block, int *counter)
+                  const ResultsView &o, cudaStream_t s, int block, int *counter, bool prepare)
 {
     if (sv.n == 0) return TRD_OK;
     const int groups = block / G;
@@ -816,8 +816,10 @@ static int launch(const trd_ctx *ctx, const SeedsView &sv, const IndexView &ix, 
     const long long need = (static_cast<long long>(sv.n) + groups - 1) / groups;
     const int grid = static_cast<int>(std::min<long long>(need, static_cast<long long>(ctx->sm_count) * per_sm));
     TRD_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), s));
-    k_seed_prepare<<<(sv.n + 255) / 256, 256, 0, s>>>(sv, P, o);
-    TRD_CUDA_TRY(cudaGetLastError());
+    if (prepare) {
+        k_seed_prepare<<<(sv.n + 255) / 256, 256, 0, s>>>(sv, P, o);
+        TRD_CUDA_TRY(cudaGetLastError());
+    }
     k_follow<G, NH, MINB, EXT><<<grid, block, smem, s>>>(sv, ix, P, o, counter);
     TRD_CUDA_TRY(cudaGetLastError());
     return TRD_OK;
@@ -825,31 +827,28 @@ static int launch(const trd_ctx *ctx, const SeedsView &sv, const IndexView &ix, 
 
 template <bool EXT>
 static int dispatch(const trd_ctx *ctx, const SeedsView &sv, const IndexView &iv, const Params &P,
-                    const ResultsView &o, cudaStream_t s, int G, int mb, int block, int nhyp, int *counter)
+                    const ResultsView &o, cudaStream_t s, int G, int mb, int block, int nhyp, int *counter,
+                    bool prepare)
 {
     switch (G * 16 + mb) {
-    case 1 * 16 + 4: return nhyp == 1 ? launch<1, 1, 4, EXT>(ctx, sv, iv, P, o, s, block, counter) : TRD_EINVAL;
-    case 1 * 16 + 5: return nhyp == 1 ? launch<1, 1, 5, EXT>(ctx, sv, iv, P, o, s, block, counter) : TRD_EINVAL;
-    case 1 * 16 + 6: return nhyp == 1 ? launch<1, 1, 6, EXT>(ctx, sv, iv, P, o, s, block, counter) : TRD_EINVAL;
-    case 1 * 16 + 8: return nhyp == 1 ? launch<1, 1, 8, EXT>(ctx, sv, iv, P, o, s, block, counter) : TRD_EINVAL;
-    case 2 * 16 + 3: return launch<2, 2, 3, EXT>(ctx, sv, iv, P, o, s, block, counter);
-    case 2 * 16 + 4: return launch<2, 2, 4, EXT>(ctx, sv, iv, P, o, s, block, counter);
-    case 4 * 16 + 3: return launch<4, 4, 3, EXT>(ctx, sv, iv, P, o, s, block, counter);
-    case 4 * 16 + 4: return launch<4, 4, 4, EXT>(ctx, sv, iv, P, o, s, block, counter);
-    case 8 * 16 + 3: return launch<8, 8, 3, EXT>(ctx, sv, iv, P, o, s, block, counter);
-    case 8 * 16 + 4: return launch<8, 8, 4, EXT>(ctx, sv, iv, P, o, s, block, counter);
-    case 32 * 16 + 3: return launch<32, 8, 3, EXT>(ctx, sv, iv, P, o, s, block, counter);
-    case 32 * 16 + 4: return launch<32, 8, 4, EXT>(ctx, sv, iv, P, o, s, block, counter);
+    case 1 * 16 + 4: return nhyp == 1 ? launch<1, 1, 4, EXT>(ctx, sv, iv, P, o, s, block, counter, prepare) : TRD_EINVAL;
+    case 1 * 16 + 5: return nhyp == 1 ? launch<1, 1, 5, EXT>(ctx, sv, iv, P, o, s, block, counter, prepare) : TRD_EINVAL;
+    case 1 * 16 + 6: return nhyp == 1 ? launch<1, 1, 6, EXT>(ctx, sv, iv, P, o, s, block, counter, prepare) : TRD_EINVAL;
+    case 1 * 16 + 8: return nhyp == 1 ? launch<1, 1, 8, EXT>(ctx, sv, iv, P, o, s, block, counter, prepare) : TRD_EINVAL;
+    case 2 * 16 + 3: return launch<2, 2, 3, EXT>(ctx, sv, iv, P, o, s, block, counter, prepare);
+    case 2 * 16 + 4: return launch<2, 2, 4, EXT>(ctx, sv, iv, P, o, s, block, counter, prepare);
+    case 4 * 16 + 3: return launch<4, 4, 3, EXT>(ctx, sv, iv, P, o, s, block, counter, prepare);
+    case 4 * 16 + 4: return launch<4, 4, 4, EXT>(ctx, sv, iv, P, o, s, block, counter, prepare);
+    case 8 * 16 + 3: return launch<8, 8, 3, EXT>(ctx, sv, iv, P, o, s, block, counter, prepare);
+    case 8 * 16 + 4: return launch<8, 8, 4, EXT>(ctx, sv, iv, P, o, s, block, counter, prepare);
+    case 32 * 16 + 3: return launch<32, 8, 3, EXT>(ctx, sv, iv, P, o, s, block, counter, prepare);
+    case 32 * 16 + 4: return launch<32, 8, 4, EXT>(ctx, sv, iv, P, o, s, block, counter, prepare);
     default: return TRD_EINVAL;
     }
 }
 
-int follow_launch(const trd_ctx *ctx, const trd_seeds_t *seeds, const IndexView &iv, const trd_params_t *p,
-                  trd_results_t *out, cudaStream_t s, int lanes_per_track, int block_threads, int min_blocks,
-                  int *counter, const int32_t *seed_offsets, int n_tf, const trd_alignment_t *align)
+static Params make_params(const trd_params_t *p, const trd_alignment_t *align)
 {
-    SeedsView sv{seeds->alpha, seeds->x, seeds->y, seeds->z, seeds->snp, seeds->tgl, seeds->q2pt, seeds->cov,
-                 seeds->n, seed_offsets, n_tf, seeds->trigger};
     Params P{p->bz, p->n_sigma_road, p->chi2_cut, p->p_miss, p->dy_gate_sigma, p->n_hyp, p->max_missing,
              p->res_mode, p->material_on};
     if (align) {
@@ -864,6 +863,33 @@ int follow_launch(const trd_ctx *ctx, const trd_seeds_t *seeds, const IndexView 
             P.iz = static_cast<float>(align->nz - 1) / (align->z_max - align->z_min);
         }
     }
+    return P;
+}
+
+// The seeds' pre-pass alone (it does not read the index, so a captured step
+// can run it beside the index build).
+int prepare_launch(const trd_seeds_t *seeds, const trd_params_t *p, trd_results_t *out, cudaStream_t s,
+                   const trd_alignment_t *align)
+{
+    if (seeds->n == 0) return TRD_OK;
+    SeedsView sv{seeds->alpha, seeds->x, seeds->y, seeds->z, seeds->snp, seeds->tgl, seeds->q2pt, seeds->cov,
+                 seeds->n, nullptr, 1, seeds->trigger};
+    const Params P = make_params(p, align);
+    ResultsView o{out->alpha, out->x, out->par, out->cov, out->chi2, out->n_trk, out->n_miss, out->status,
+                  out->tracklet_id};
+    k_seed_prepare<<<(sv.n + 255) / 256, 256, 0, s>>>(sv, P, o);
+    TRD_CUDA_TRY(cudaGetLastError());
+    return TRD_OK;
+}
+
+int follow_launch(const trd_ctx *ctx, const trd_seeds_t *seeds, const IndexView &iv, const trd_params_t *p,
+                  trd_results_t *out, cudaStream_t s, int lanes_per_track, int block_threads, int min_blocks,
+                  int *counter, const int32_t *seed_offsets, int n_tf, const trd_alignment_t *align,
+                  bool prepare)
+{
+    SeedsView sv{seeds->alpha, seeds->x, seeds->y, seeds->z, seeds->snp, seeds->tgl, seeds->q2pt, seeds->cov,
+                 seeds->n, seed_offsets, n_tf, seeds->trigger};
+    const Params P = make_params(p, align);
     const bool ext = iv.recx || P.chamber_x || P.bzmap;
     ResultsView o{out->alpha, out->x, out->par, out->cov, out->chi2, out->n_trk, out->n_miss, out->status,
                   out->tracklet_id};
@@ -872,8 +898,8 @@ int follow_launch(const trd_ctx *ctx, const trd_seeds_t *seeds, const IndexView 
     if (G <= 0) G = p->n_hyp <= 1 ? 1 : (p->n_hyp <= 2 ? 2 : (p->n_hyp <= 4 ? 4 : 8));
     if (G < p->n_hyp) return TRD_EINVAL;
     const int mb = min_blocks > 0 ? min_blocks : 4;
-    return ext ? dispatch<true>(ctx, sv, iv, P, o, s, G, mb, block, p->n_hyp, counter)
-               : dispatch<false>(ctx, sv, iv, P, o, s, G, mb, block, p->n_hyp, counter);
+    return ext ? dispatch<true>(ctx, sv, iv, P, o, s, G, mb, block, p->n_hyp, counter, prepare)
+               : dispatch<false>(ctx, sv, iv, P, o, s, G, mb, block, p->n_hyp, counter, prepare);
 }
 
 }  // namespace trd_host
