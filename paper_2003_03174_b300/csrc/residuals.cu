@@ -2,7 +2,7 @@
 // refits, collected per TPC sub-volume, and the distortion vector of each
 // sub-volume (arXiv:2003.03174, Sec. 2, steps 4 and 5).
 //
-// k_residuals: one thread per track.  The ITS refit (inside the TPC) and the
+// k_residuals: two lanes per track (one per refit).  The ITS refit (inside the TPC) and the
 // TRD-only refit (outside) are carried along the track to every pad row that
 // holds a cluster of that track.  Each refit is transported to the row plane
 // (in one step from its state after the last rotation);
@@ -129,32 +129,38 @@ __device__ __forceinline__ long long fixed24(float v) { return __float2ll_rn(v *
 
 // Resident 128-thread blocks per SM the register budget is sized for.
 #ifndef TRD_RESIDUALS_MIN_BLOCKS
-#define TRD_RESIDUALS_MIN_BLOCKS 5
+#define TRD_RESIDUALS_MIN_BLOCKS 6
 #endif
 
-__global__ void __launch_bounds__(128, TRD_RESIDUALS_MIN_BLOCKS) k_residuals(StatesView I, StatesView Tr, ClustersView cl, int n, float bz,
-                                                   unsigned long long *sums, float *res_out)
+// Two lanes per track: the even lane carries the ITS refit, the odd lane the
+// TRD refit.  Both lanes of a pair walk the same rows (their control flow is
+// identical), exchange what the combination needs by shuffles, compute it
+// the same way, and split the eleven atomics.
+__global__ void __launch_bounds__(128, TRD_RESIDUALS_MIN_BLOCKS)
+k_residuals(StatesView I, StatesView Tr, ClustersView cl, int n, float bz, unsigned long long *sums, float *res_out)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = g >> 1;
+    if (i >= n) return;  // pair-uniform
+    const int role = g & 1;  // 0: ITS refit, 1: TRD refit
+    const unsigned pmask = 3u << ((threadIdx.x & 31) & ~1);
     const size_t plane = static_cast<size_t>(kRows) * n;
+    const float nan = __int_as_float(0x7fc00000);
     if (I.status[i] != 0 || Tr.status[i] != 0) {
         if (res_out)
             for (int r = 0; r < kRows; ++r)
 #pragma unroll
-                for (int k = 0; k < 4; ++k) res_out[k * plane + static_cast<size_t>(r) * n + i] = __int_as_float(0x7fc00000);
+                for (int k = 0; k < 2; ++k) res_out[(2 * role + k) * plane + static_cast<size_t>(r) * n + i] = nan;
         return;
     }
-    Carrier A, B;  // ITS refit, TRD refit
-    load_state(I, n, i, A.anchor);
-    load_state(Tr, n, i, B.anchor);
-    A.frame = {I.alpha[i], 0.0f};
-    B.frame = {Tr.alpha[i], 0.0f};
-    TrackState a, b;  // the two refits at the current row
+    const StatesView &V = role ? Tr : I;
+    Carrier C;
+    load_state(V, n, i, C.anchor);
+    C.frame = {V.alpha[i], 0.0f};
+    TrackState w;
 
-    // the ITS refit outward: only where the cluster sector changes does the
-    // path matter (the rotations); the anchor ends at the last of them
-    // (only the 1-byte sectors are read; y and z where a rotation is due)
+    // the ITS refit outward (even lane): only where the cluster sector
+    // changes does the path matter; both lanes find the last row
     int last = -1;
 #pragma unroll 4
     for (int r = 0; r < kRows; ++r) {
@@ -162,8 +168,8 @@ __global__ void __launch_bounds__(128, TRD_RESIDUALS_MIN_BLOCKS) k_residuals(Sta
         const int s = cl.sector[q];
         if (s < 0 || s >= kSectors) continue;
         last = r;
-        if (s != A.anchor.sector && isfinite(cl.y[q]) && isfinite(cl.z[q]))
-            (void)carry(A, s, df{c_rows.x[r], 0.0f}, bz, a);
+        if (role == 0 && s != C.anchor.sector && isfinite(cl.y[q]) && isfinite(cl.z[q]))
+            (void)carry(C, s, df{c_rows.x[r], 0.0f}, bz, w);
     }
 
     // both inward, row by row; the next row's cluster is loaded while this
@@ -174,7 +180,7 @@ __global__ void __launch_bounds__(128, TRD_RESIDUALS_MIN_BLOCKS) k_residuals(Sta
     if (res_out)
         for (int r = kRows - 1; r > last; --r)
 #pragma unroll
-            for (int k = 0; k < 4; ++k) res_out[k * plane + static_cast<size_t>(r) * n + i] = __int_as_float(0x7fc00000);
+            for (int k = 0; k < 2; ++k) res_out[(2 * role + k) * plane + static_cast<size_t>(r) * n + i] = nan;
 #pragma unroll 1
     for (int r = last; r >= 0; --r) {
         const size_t q = static_cast<size_t>(r) * n + i;
@@ -186,52 +192,49 @@ __global__ void __launch_bounds__(128, TRD_RESIDUALS_MIN_BLOCKS) k_residuals(Sta
             y_next = cl.y[qn];
             z_next = cl.z[qn];
         }
-        float dy = __int_as_float(0x7fc00000), dz = dy, t = dy, u = dy;
+        float o0 = nan, o1 = nan;  // this lane's outputs: (dy, dz) or (t, u)
         if (s >= 0 && s < kSectors && isfinite(ycl) && isfinite(zcl)) {
             const df xr = {c_rows.x[r], 0.0f};
-            const bool okb = carry(B, s, xr, bz, b);
-            const bool oka = carry(A, s, xr, bz, a);
-            if (oka && okb) {
-                // residuals to each refit (y carried as a double-float)
-                const float r1y = (__fsub_rn(ycl, a.y.hi) - a.y.lo), r1z = zcl - a.z;
-                const float r2y = (__fsub_rn(ycl, b.y.hi) - b.y.lo), r2z = zcl - b.z;
-                const float d1 = 1.0f / (a.c[0] * a.c[2] - a.c[1] * a.c[1]);
-                const float d2 = 1.0f / (b.c[0] * b.c[2] - b.c[1] * b.c[1]);
-                const float A00 = a.c[2] * d1, A01 = -a.c[1] * d1, A11 = a.c[0] * d1;  // V1^-1
-                const float B00 = b.c[2] * d2, B01 = -b.c[1] * d2, B11 = b.c[0] * d2;  // V2^-1
-                const float g0 = A00 * r1y + A01 * r1z + B00 * r2y + B01 * r2z;
-                const float g1 = A01 * r1y + A11 * r1z + B01 * r2y + B11 * r2z;
-                const float W00 = A00 + B00, W01 = A01 + B01, W11 = A11 + B11;
-                const float dw = 1.0f / (W00 * W11 - W01 * W01);
-                dy = (W11 * g0 - W01 * g1) * dw;
-                dz = (W00 * g1 - W01 * g0) * dw;
-                const float wa = 1.0f / a.c[5], wb = 1.0f / b.c[5];
-                const float f = (a.f * wa + b.f * wb) / (wa + wb);
-                const float va = 1.0f / a.c[9], vb = 1.0f / b.c[9];
-                const float tl = (a.t * va + b.t * vb) / (va + vb);
+            const bool ok = carry(C, s, xr, bz, w);
+            // this refit's share of the combination: V^-1, V^-1 (cluster - estimate),
+            // and the inverse-variance weighted angles (y carried as a double-float)
+            const float ry = __fsub_rn(ycl, w.y.hi) - w.y.lo, rz = zcl - w.z;
+            const float d = 1.0f / (w.c[0] * w.c[2] - w.c[1] * w.c[1]);
+            const float A00 = w.c[2] * d, A01 = -w.c[1] * d, A11 = w.c[0] * d;
+            const float wf = 1.0f / w.c[5], wt = 1.0f / w.c[9];
+            float v[9] = {A00, A01, A11, A00 * ry + A01 * rz, A01 * ry + A11 * rz, wf, w.f * wf, wt, w.t * wt};
+            const int both = __shfl_xor_sync(pmask, static_cast<int>(ok), 1) & static_cast<int>(ok);
+#pragma unroll
+            for (int k = 0; k < 9; ++k) v[k] += __shfl_xor_sync(pmask, v[k], 1);
+            if (both) {
+                const float dw = 1.0f / (v[0] * v[2] - v[1] * v[1]);
+                const float dy = (v[2] * v[3] - v[1] * v[4]) * dw;
+                const float dz = (v[0] * v[4] - v[1] * v[3]) * dw;
+                const float f = v[6] / v[5], tl = v[8] / v[7];
                 const float ir = rsqrtf((1.0f - f) * (1.0f + f));
-                t = f * ir;
-                u = tl * ir;
-                const int v = voxel_of(ycl, zcl, s, r, xr.hi);
-                unsigned long long *S = sums + static_cast<size_t>(v) * kVoxSums;
-                atomicAdd(S + 0, 1ull);
-                atomicAdd(S + 1, static_cast<unsigned long long>(fixed24(t)));
-                atomicAdd(S + 2, static_cast<unsigned long long>(fixed24(u)));
-                atomicAdd(S + 3, static_cast<unsigned long long>(fixed24(t * t)));
-                atomicAdd(S + 4, static_cast<unsigned long long>(fixed24(u * u)));
-                atomicAdd(S + 5, static_cast<unsigned long long>(fixed24(dy)));
-                atomicAdd(S + 6, static_cast<unsigned long long>(fixed24(dz)));
-                atomicAdd(S + 7, static_cast<unsigned long long>(fixed24(t * dy)));
-                atomicAdd(S + 8, static_cast<unsigned long long>(fixed24(u * dz)));
-                atomicAdd(S + 9, static_cast<unsigned long long>(fixed24(dy * dy)));
-                atomicAdd(S + 10, static_cast<unsigned long long>(fixed24(dz * dz)));
+                const float t = f * ir, u = tl * ir;
+                o0 = role ? t : dy;
+                o1 = role ? u : dz;
+                unsigned long long *S = sums + static_cast<size_t>(voxel_of(ycl, zcl, s, r, xr.hi)) * kVoxSums;
+                if (role == 0) {
+                    atomicAdd(S + 0, 1ull);
+                    atomicAdd(S + 1, static_cast<unsigned long long>(fixed24(t)));
+                    atomicAdd(S + 2, static_cast<unsigned long long>(fixed24(u)));
+                    atomicAdd(S + 3, static_cast<unsigned long long>(fixed24(t * t)));
+                    atomicAdd(S + 4, static_cast<unsigned long long>(fixed24(u * u)));
+                    atomicAdd(S + 5, static_cast<unsigned long long>(fixed24(dy)));
+                } else {
+                    atomicAdd(S + 6, static_cast<unsigned long long>(fixed24(dz)));
+                    atomicAdd(S + 7, static_cast<unsigned long long>(fixed24(t * dy)));
+                    atomicAdd(S + 8, static_cast<unsigned long long>(fixed24(u * dz)));
+                    atomicAdd(S + 9, static_cast<unsigned long long>(fixed24(dy * dy)));
+                    atomicAdd(S + 10, static_cast<unsigned long long>(fixed24(dz * dz)));
+                }
             }
         }
         if (res_out) {
-            res_out[0 * plane + q] = dy;
-            res_out[1 * plane + q] = dz;
-            res_out[2 * plane + q] = t;
-            res_out[3 * plane + q] = u;
+            res_out[(2 * role + 0) * plane + q] = o0;
+            res_out[(2 * role + 1) * plane + q] = o1;
         }
     }
 }
@@ -303,8 +306,10 @@ extern "C" int trd_residuals(trd_ctx_t *ctx, int32_t n, const trd_states_t *its,
     trd::StatesView I{its->alpha, its->x, its->par, its->cov, its->status};
     trd::StatesView T{trd_refit->alpha, trd_refit->x, trd_refit->par, trd_refit->cov, trd_refit->status};
     trd::ClustersView C{clusters->y, clusters->z, clusters->sector};
-    const int threads = 128;
-    trd::k_residuals<<<(n + threads - 1) / threads, threads, 0, static_cast<cudaStream_t>(stream)>>>(
+    const int threads = 128;  // 64 tracks, two lanes each
+    const long long lanes = 2LL * n;
+    trd::k_residuals<<<static_cast<int>((lanes + threads - 1) / threads), threads, 0,
+                        static_cast<cudaStream_t>(stream)>>>(
         I, T, C, n, bz, reinterpret_cast<unsigned long long *>(voxel_sums), cluster_res);
     TRD_CUDA_TRY(cudaGetLastError());
     return TRD_OK;
