@@ -64,10 +64,10 @@ REFIT_FLOPS_PER_LAYER = 460
 # is still in L2 when the kernel ends), valid only for the source measured.
 REFIT_TRAFFIC = {"source_sha256_16": "cdaab0d31a37f941", "bytes": 39.90e6}
 # DRAM bytes (read + write) of one trd_follow call (k_seed_prepare 17.62 MB +
-# k_follow 56.24 MB) on this workload from one ncu capture of each kernel, valid
+# k_follow 56.01 MB) on this workload from one ncu capture of each kernel, valid
 # only for the kernel source it was measured on: reported as null once
 # follow.cu, trd_device.cuh or track_model.cuh change.
-FOLLOW_TRAFFIC = {"source_sha256_16": "32ee53f02e0f8e2e", "bytes": 73.86e6}
+FOLLOW_TRAFFIC = {"source_sha256_16": "277fd7eea3810aab", "bytes": 73.63e6}
 
 
 def _source_hash(files=("follow.cu", "trd_device.cuh", "track_model.cuh")):

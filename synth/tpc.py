@@ -112,8 +112,25 @@ def make_residual_workload(n_tracks: int, seed: int = 0, distorted: bool = True,
     if keep.shape[0] < n_tracks:
         raise RuntimeError("not enough truth tracks reach the TRD")
     truth = dict(phi0=phi0[keep], kcurv=kc[keep], tgl=tgl[keep], q2pt=(q / pt)[keep])
-    n = n_tracks
+    its, trd, cl, app = _clusters_and_refits(rng, truth, bz, distorted, smear, eff, refit_smear, uniform)
+    # a few refits that failed upstream: their tracks must contribute nothing
+    for st in (its, trd):
+        st["status"][rng.uniform(0, 1, n_tracks) < fail_frac / 2] = 1
+    return ResidualWorkload(its=its, trd=trd, clusters=cl, truth=truth, bz=bz, applied=app)
 
+
+def clusters_for_truth(truth: dict, bz: float = 0.5, seed: int = 0, distorted: bool = True, smear: float = 0.1,
+                       eff: float = 0.9, uniform=None):
+    """TPC clusters and an ITS refit state for given truth tracks (e.g. a
+    timeframe's, to run the whole calibration chain on them): returns (its,
+    clusters, applied displacements).  truth: phi0, kcurv, tgl, q2pt."""
+    rng = np.random.Generator(np.random.Philox(key=seed + 6_000_000))
+    its, _, cl, app = _clusters_and_refits(rng, truth, bz, distorted, smear, eff, True, uniform)
+    return its, cl, app
+
+
+def _clusters_and_refits(rng, truth, bz, distorted, smear, eff, refit_smear, uniform):
+    n = truth["phi0"].shape[0]
     xr = row_x().astype(np.float64)
     cy = np.zeros((N_ROWS, n), np.float32)
     cz = np.zeros((N_ROWS, n), np.float32)
@@ -142,11 +159,7 @@ def make_residual_workload(n_tracks: int, seed: int = 0, distorted: bool = True,
         cs[r] = np.where(ok, sec, -1)
     its = _smeared_state(rng, truth, X_ITS, ITS_SIGMA, bz, refit_smear)
     trd = _smeared_state(rng, truth, X_TRD, TRD_SIGMA, bz, refit_smear)
-    # a few refits that failed upstream: their tracks must contribute nothing
-    for st in (its, trd):
-        st["status"][rng.uniform(0, 1, n) < fail_frac / 2] = 1
-    return ResidualWorkload(its=its, trd=trd, clusters=dict(y=cy, z=cz, sector=cs), truth=truth, bz=bz,
-                            applied=dict(dx=app[0], dy=app[1], dz=app[2]))
+    return its, trd, dict(y=cy, z=cz, sector=cs), dict(dx=app[0], dy=app[1], dz=app[2])
 
 
 def _chunk(args):
