@@ -63,11 +63,13 @@ REFIT_FLOPS_PER_LAYER = 460
 # from one ncu capture (39.05 MB read, 0.85 MB written: the 20 MB of output
 # is still in L2 when the kernel ends), valid only for the source measured.
 REFIT_TRAFFIC = {"source_sha256_16": "cdaab0d31a37f941", "bytes": 39.90e6}
-# DRAM bytes (read + write) of one trd_follow call (k_seed_prepare 17.62 MB +
-# k_follow 56.01 MB) on this workload from one ncu capture of each kernel, valid
-# only for the kernel source it was measured on: reported as null once
-# follow.cu, trd_device.cuh or track_model.cuh change.
-FOLLOW_TRAFFIC = {"source_sha256_16": "277fd7eea3810aab", "bytes": 73.63e6}
+# DRAM bytes (read + write) of one trd_follow call on this workload from one
+# ncu capture of its four kernels (k_seed_key 0.81 MB, k_seed_prepare 26.99 MB,
+# k_follow 59.90 MB, k_results_gather 26.41 MB; ncu empties the caches before
+# each kernel, so the gather's reads of the staged results, L2 hits in a
+# plain run, count here), valid only for the kernel source it was measured
+# on: reported as null once follow.cu, trd_device.cuh or track_model.cuh change.
+FOLLOW_TRAFFIC = {"source_sha256_16": "655825cab70fad42", "bytes": 114.11e6}
 # DRAM bytes (read 206.72 MB + write 16.63 MB) of one k_residuals launch on the
 # 100,000-track map from one ncu capture; the 450,000-track map holds ~3 GB on
 # the device and is not captured, so the figure is reported for the captured
@@ -386,7 +388,8 @@ def run_ours(args):
     hbm = peaks.get("hbm_gbs")
     follow_avg_s = statistics.mean(follow_ms) / 1e3
     achieved = n * FOLLOW_BYTES_PER_SEED / follow_avg_s / 1e9
-    roof = {"bound": "hbm", "kernel": "trd_follow (k_seed_prepare + k_follow)", "achieved": achieved,
+    roof = {"bound": "hbm", "kernel": "trd_follow (k_seed_key + k_seed_prepare + k_follow + k_results_gather)",
+            "achieved": achieved,
             "peak": hbm if hbm else 6400.0, "unit": "GB/s",
             "peak_source": "measured" if hbm else "fallback",
             "frac": achieved / (hbm if hbm else 6400.0),
@@ -401,7 +404,9 @@ def run_ours(args):
            "unit": "TFLOP/s", "peak_source": "measured by trd_measure_fp32_peak (FMA chains)"}
     alu["frac"] = alu["achieved"] / fp32_peak
     roof["alu_check"] = alu
-    launches_per_step = 7  # count, 3 scan kernels, scatter, seed prepare, follow (one graph)
+    # index: count, 3 scan kernels, scatter; follower: seed key, seed prepare,
+    # follow, results gather (one graph)
+    launches_per_step = 9
     clocks = clk.summary()
     refit = time_refit(ctx, res, trk, tf.params, stream, flush, args.steps, args.warmup, hbm, fp32_peak)
 
@@ -558,7 +563,7 @@ def run_batched(args):
                   "path": f"{len(tfs)} x (trd_index_rebuild + trd_follow) on one stream"},
         "speedup_batched_vs_plain": t_plain / t_batch,
         "results_identical": bool(same),
-        "gpu_launches_per_step": {"batched": 7, "plain": 7 * len(tfs)},
+        "gpu_launches_per_step": {"batched": 9, "plain": 9 * len(tfs)},
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)

@@ -204,8 +204,15 @@ TRD_API int trd_index_build_noalloc(const trd_tracklets_t *tracklets, float y_bi
  * All pointers are device pointers owned by the caller; results are written
  * asynchronously on `stream`.  The index must have been built on `stream` or
  * on a stream `stream` has synchronised with.
+ * Seeds are processed in order of decreasing |q/pT| (lanes that work together
+ * then have roads of similar width); results do not depend on the order and
+ * are written at the seeds' input positions.  The call's scratch (136 bytes
+ * per seed + 512: sorted seed states and staged results) is taken from the
+ * device's default memory pool, ordered on `stream` (cudaMallocAsync /
+ * cudaFreeAsync).
  * Errors: TRD_EINVAL (NULL pointers, n < 0, n_hyp outside 1..TRD_MAX_HYP,
- * non-positive road/cut), TRD_ECUDA (launch failure).                       */
+ * non-positive road/cut), TRD_ENOMEM (no scratch), TRD_ECUDA (launch
+ * failure).                                                                 */
 TRD_API int trd_follow(trd_ctx_t *ctx, const trd_seeds_t *seeds, const trd_index_t *index,
                const trd_params_t *params, trd_results_t *out, void *stream);
 

@@ -251,6 +251,18 @@ int trd_follow_aligned(trd_ctx_t *ctx, const trd_seeds_t *seeds, const trd_index
                        const trd_params_t *p, const trd_alignment_t *align, trd_results_t *out, void *stream,
                        const trd_launch_t *launch)
 {
+    return trd_host::follow_checked(ctx, seeds, index, p, align, out, stream, launch, nullptr);
+}
+
+}  // extern "C"
+
+// The follower's public entry points after validation; parked: the
+// pre-pass's scratch (trd_host::parked_bytes), or null to take it from the
+// device's pool on the stream.
+int trd_host::follow_checked(trd_ctx *ctx, const trd_seeds_t *seeds, const trd_index *index, const trd_params_t *p,
+                             const trd_alignment_t *align, trd_results_t *out, void *stream,
+                             const trd_launch_t *launch, void *parked)
+{
     if (align && align->bz_map &&
         (align->nr < 2 || align->nz < 2 || !(align->r_max > align->r_min) || !(align->z_max > align->z_min) ||
          !isfinite(align->r_min) || !isfinite(align->r_max) || !isfinite(align->z_min) || !isfinite(align->z_max)))
@@ -276,8 +288,11 @@ int trd_follow_aligned(trd_ctx_t *ctx, const trd_seeds_t *seeds, const trd_index
     IndexView iv{index->offsets, index->rec, index->stats, index->nb, index->inv_w,
                  index->has_x ? index->recx : nullptr};
     return trd_host::follow_launch(ctx, seeds, iv, p, out, static_cast<cudaStream_t>(stream), lanes_per_track,
-                                   block_threads, min_blocks, trd_host::next_counter(ctx), nullptr, 1, align);
+                                   block_threads, min_blocks, trd_host::next_counter(ctx), nullptr, 1, align, true,
+                                   parked);
 }
+
+extern "C" {
 
 int trd_follow(trd_ctx_t *ctx, const trd_seeds_t *seeds, const trd_index_t *index, const trd_params_t *p,
                trd_results_t *out, void *stream)

@@ -21,6 +21,7 @@ struct trd_batch {
     trd_index *index;
     int32_t *soff;      // [n_tf + 1] device seed offsets
     int32_t *counter;   // the follower's work counter (private to this batch)
+    void *parked;       // the seeds' pre-pass output (sorted, rotated states)
     cudaGraph_t graph;
     cudaGraphExec_t exec;
 };
@@ -43,6 +44,7 @@ void release(trd_batch *b)
     if (b->index) trd_host::index_release(b->index);
     cudaFree(b->soff);
     cudaFree(b->counter);
+    cudaFree(b->parked);
     (void)cudaGetLastError();
     delete b;
 }
@@ -72,7 +74,8 @@ int trd_batch_create(trd_ctx_t *ctx, int32_t n_tf, const int32_t *seed_offsets, 
         return rc;
     }
     if (cudaMalloc(&b->soff, sizeof(int32_t) * (n_tf + 1)) != cudaSuccess ||
-        cudaMalloc(&b->counter, sizeof(int32_t)) != cudaSuccess) {
+        cudaMalloc(&b->counter, sizeof(int32_t)) != cudaSuccess ||
+        (seeds->n > 0 && cudaMalloc(&b->parked, trd_host::parked_bytes(seeds->n)) != cudaSuccess)) {
         release(b);
         return TRD_ENOMEM;
     }
@@ -114,7 +117,7 @@ int trd_batch_create(trd_ctx_t *ctx, int32_t n_tf, const int32_t *seed_offsets, 
     bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     if (ok) {
         ok = cudaEventRecord(fork, cs) == cudaSuccess && cudaStreamWaitEvent(cs2, fork, 0) == cudaSuccess;
-        if (ok) rc = trd_host::prepare_launch(seeds, params, results, cs2);
+        if (ok) rc = trd_host::prepare_launch(seeds, params, results, cs2, b->parked);
         if (ok && !rc) ok = cudaEventRecord(join, cs2) == cudaSuccess;
         if (ok && !rc) rc = trd_host::index_rebuild_launch(b->index, tracklets, cs);
         if (ok && !rc) ok = cudaStreamWaitEvent(cs, join, 0) == cudaSuccess;
@@ -123,7 +126,8 @@ int trd_batch_create(trd_ctx_t *ctx, int32_t n_tf, const int32_t *seed_offsets, 
                          tracklets->x ? b->index->recx : nullptr};
             rc = trd_host::follow_launch(ctx, seeds, iv, params, results, cs, launch ? launch->lanes_per_track : 0,
                                          launch ? launch->block_threads : 0, launch ? launch->min_blocks_per_sm : 0,
-                                         b->counter, n_tf > 1 ? b->soff : nullptr, n_tf, nullptr, false);
+                                         b->counter, n_tf > 1 ? b->soff : nullptr, n_tf, nullptr, false,
+                                         b->parked);
         }
         const bool ended = cudaStreamEndCapture(cs, &b->graph) == cudaSuccess;
         ok = ok && !rc && ended && cudaGraphInstantiate(&b->exec, b->graph, 0) == cudaSuccess;

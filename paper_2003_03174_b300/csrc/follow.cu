@@ -468,24 +468,22 @@ __device__ __forceinline__ bool cov_pd(const float *c)
     return pd;
 }
 
-__device__ __forceinline__ void write_result(const ResultsView &o, int n, int i, const TrackState &s, float chi2,
-                                             int ntrk, int nmiss, int status, const int (&ids)[kLayers])
+// A finished seed's result as one 128-byte record at its sorted position
+// (8 vector stores); k_results_gather moves it to the seed's input position.
+// Words: alpha, x, par[5], cov[15], chi2, then n_trk, n_miss, status, ids[6].
+__device__ __forceinline__ void stage_result(float4 *res, int pos, const TrackState &s, float chi2, int ntrk,
+                                             int nmiss, int status, const int (&ids)[kLayers])
 {
-    o.alpha[i] = sector_alpha_df(s.sector).hi;
-    o.x[i] = df_to_f(s.x);
-    o.par[0 * n + i] = df_to_f(s.y);
-    o.par[1 * n + i] = s.z;
-    o.par[2 * n + i] = s.f;
-    o.par[3 * n + i] = s.t;
-    o.par[4 * n + i] = s.k;
-#pragma unroll
-    for (int k = 0; k < 15; ++k) o.cov[k * n + i] = s.c[k];
-    o.chi2[i] = chi2;
-    o.ntrk[i] = ntrk;
-    o.nmiss[i] = nmiss;
-    o.status[i] = status;
-#pragma unroll
-    for (int l = 0; l < kLayers; ++l) o.ids[l * n + i] = ids[l];
+    float4 *r = res + 8 * static_cast<size_t>(pos);
+    r[0] = make_float4(sector_alpha_df(s.sector).hi, df_to_f(s.x), df_to_f(s.y), s.z);
+    r[1] = make_float4(s.f, s.t, s.k, s.c[0]);
+    r[2] = make_float4(s.c[1], s.c[2], s.c[3], s.c[4]);
+    r[3] = make_float4(s.c[5], s.c[6], s.c[7], s.c[8]);
+    r[4] = make_float4(s.c[9], s.c[10], s.c[11], s.c[12]);
+    r[5] = make_float4(s.c[13], s.c[14], chi2, __int_as_float(ntrk));
+    r[6] = make_float4(__int_as_float(nmiss), __int_as_float(status), __int_as_float(ids[0]), __int_as_float(ids[1]));
+    r[7] = make_float4(__int_as_float(ids[2]), __int_as_float(ids[3]), __int_as_float(ids[4]),
+                       __int_as_float(ids[5]));
 }
 
 __device__ __forceinline__ void write_seed_result(const ResultsView &o, const SeedsView &sv, int n, int i,
@@ -550,76 +548,214 @@ struct Lane {
     bool alive;
 };
 
-// Seed preparation, one thread per seed (all seeds take the same path, so
-// this runs without divergence): load the seed, validate it, rotate it into
-// the sector of its position.  A seed that ends here gets its final result;
-// a live seed's rotated state is parked in its own result slots (which the
-// follower overwrites at the end) with status -1:
-//   alpha <- sector, x <- x.hi, chi2 <- x.lo, par <- (y.hi, z, snp, tgl, q2pt),
-//   cov <- cov, n_miss <- bits of y.lo.
-__global__ void __launch_bounds__(256) k_seed_prepare(SeedsView sv, Params P, ResultsView o)
+// ---- processing order ---------------------------------------------------------
+// The follower takes seeds in order of decreasing |q/pT| (bins of 1/28 c/GeV;
+// everything above 4.5 c/GeV shares the first bin): a low-momentum seed has a
+// wide road (scattering), a high-momentum one a narrow road, so lanes that
+// take seeds together scan roads of similar size and diverge less, and the
+// slow seeds start first instead of forming the launch's tail.  Results do
+// not depend on the order (every seed is followed on its own).  The rotated
+// seed state is parked at the seed's sorted position and the result is staged
+// there too, so the follower reads and writes consecutive addresses; a gather
+// kernel then writes the results at the input positions with full lines.
+constexpr int kSortBins = 128;
+constexpr float kSortBinsPerUnit = 28.0f;
+constexpr int kKeyThreads = 256;
+constexpr int kKeyItems = 8;
+constexpr int kParkedWords = 25;  // words of a parked record
+
+__device__ __forceinline__ int sort_bin(float q2pt)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int n = sv.n;
-    if (i >= n) return;
-    TrackState s;
-    const float alpha = sv.alpha[i];
-    const float sx = sv.x[i], sy = sv.y[i];
-    s.x = {sx, 0.0f};
-    s.y = {sy, 0.0f};
-    s.z = sv.z[i];
-    s.f = sv.snp[i];
-    s.t = sv.tgl[i];
-    s.k = sv.q2pt[i];
-#pragma unroll
-    for (int k = 0; k < 15; ++k) s.c[k] = sv.cov[k * n + i];
-    if (!(fabsf(s.f) < kMaxSnp) || !cov_pd(s.c)) {
-        write_seed_result(o, sv, n, i, TRD_ST_SEED_INVALID);
-        return;
-    }
-    const float phi = alpha + atan2f(sy, sx);
-    float u = phi - kTwoPiHi * floorf(phi * (1.0f / kTwoPiHi));
-    int sec = static_cast<int>(u * (1.0f / kSectorWidthHi));
-    sec = min(max(sec, 0), kSectors - 1);
-    df d = df_add_f(sector_alpha_df(sec), -alpha);
-    if (d.hi > 3.14159265f) d = df_add(d, df{-kTwoPiHi, -kTwoPiLo});
-    if (d.hi < -3.14159265f) d = df_add(d, df{kTwoPiHi, kTwoPiLo});
-    s.sector = sec;
-    if (!rotate(s, d, sec, P.bzmap ? field_at(P, hypotf(sx, sy), s.z) : P.bz)) {
-        write_seed_result(o, sv, n, i, TRD_ST_PROP_FAIL);
-        return;
-    }
-    o.alpha[i] = static_cast<float>(sec);
-    o.x[i] = s.x.hi;
-    o.chi2[i] = s.x.lo;
-    o.par[0 * n + i] = s.y.hi;
-    o.par[1 * n + i] = s.z;
-    o.par[2 * n + i] = s.f;
-    o.par[3 * n + i] = s.t;
-    o.par[4 * n + i] = s.k;
-#pragma unroll
-    for (int k = 0; k < 15; ++k) o.cov[k * n + i] = s.c[k];
-    o.nmiss[i] = __float_as_int(s.y.lo);
-    o.status[i] = -1;
+    const float a = fabsf(q2pt) * kSortBinsPerUnit;  // NaN fails the test: first bin
+    return a < static_cast<float>(kSortBins - 1) ? kSortBins - 1 - static_cast<int>(a) : 0;
 }
 
-// Pick up seed i as prepared by k_seed_prepare.  Returns false when the seed
-// already has its final result.
-template <int G>
-__device__ __forceinline__ bool start_seed(int i, int q, const SeedsView &sv, const ResultsView &o, Lane &L)
+// Scratch of one follower call (device, n seeds; the base 16-byte aligned):
+//   bin_count [kSortBins]     seeds per |q/pT| bin (zeroed before k_seed_key)
+//   rec       [n][8] float4   one 128-byte record per sorted position: first
+//                             the parked seed (k_seed_prepare), then the
+//                             staged result (stage_result)
+//   rank      [n]             a seed's rank inside its bin (input order)
+//   inv       [n]             the seed's sorted position, -1 when it ended in
+//                             k_seed_prepare (input order)
+// Parked record (words): sector (int bits; -1 = finished), x.hi, x.lo, y.hi,
+// y.lo, z, snp, tgl, q2pt, c0..c14, input index (int bits); words 25..31
+// unused until the result is staged.
+struct ParkedView {
+    int32_t *bin_count;
+    float4 *rec;
+    int32_t *rank, *inv;
+};
+
+__host__ __device__ inline size_t parked_words(int n)
 {
-    const int n = sv.n;
-    if (o.status[i] != -1) return false;
-    TrackState &s = L.s;
-    s.sector = static_cast<int>(o.alpha[i]);
-    s.x = {o.x[i], o.chi2[i]};
-    s.y = {o.par[0 * n + i], __int_as_float(o.nmiss[i])};
-    s.z = o.par[1 * n + i];
-    s.f = o.par[2 * n + i];
-    s.t = o.par[3 * n + i];
-    s.k = o.par[4 * n + i];
+    return static_cast<size_t>(kSortBins) + static_cast<size_t>(32 + 2) * static_cast<size_t>(n);
+}
+
+__host__ __device__ inline ParkedView parked_view(void *base, int n)
+{
+    int32_t *w = static_cast<int32_t *>(base);
+    ParkedView v;
+    v.bin_count = w;
+    v.rec = reinterpret_cast<float4 *>(w + kSortBins);  // 512 bytes in: still 16-byte aligned
+    v.rank = w + kSortBins + 32 * static_cast<size_t>(n);
+    v.inv = v.rank + n;
+    return v;
+}
+
+// Bin of every seed and its rank inside the bin: lanes of a warp with the
+// same bin share one shared-memory atomic, and each block takes its base in
+// every occupied bin with one global atomic.
+__global__ void __launch_bounds__(kKeyThreads) k_seed_key(const float *__restrict__ q2pt, int n, ParkedView pk)
+{
+    __shared__ int h[kSortBins], base[kSortBins];
+    for (int t = threadIdx.x; t < kSortBins; t += kKeyThreads) h[t] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int i0 = blockIdx.x * (kKeyThreads * kKeyItems) + threadIdx.x;
+    int b[kKeyItems], r[kKeyItems];
 #pragma unroll
-    for (int k = 0; k < 15; ++k) s.c[k] = o.cov[k * n + i];
+    for (int u = 0; u < kKeyItems; ++u) {
+        const int i = i0 + u * kKeyThreads;
+        b[u] = i < n ? sort_bin(__ldg(&q2pt[i])) : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, b[u]);
+        const int leader = __ffs(peers) - 1;
+        int first = 0;
+        if (b[u] >= 0 && lane == leader) first = atomicAdd(&h[b[u]], __popc(peers));
+        first = __shfl_sync(0xffffffffu, first, leader);
+        r[u] = first + __popc(peers & ((1u << lane) - 1u));
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < kSortBins; t += kKeyThreads) base[t] = h[t] ? atomicAdd(&pk.bin_count[t], h[t]) : 0;
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < kKeyItems; ++u) {
+        const int i = i0 + u * kKeyThreads;
+        if (b[u] >= 0) pk.rank[i] = base[b[u]] + r[u];
+    }
+}
+
+// Seed preparation, one thread per seed (all seeds take the same path, so
+// this runs without divergence): load the seed, validate it, rotate it into
+// the sector of its position.  A seed that ends here gets its final result
+// (and sector -1 at its sorted position); a live seed's rotated state is
+// parked at its sorted position.
+__global__ void __launch_bounds__(256) k_seed_prepare(SeedsView sv, Params P, ResultsView o, ParkedView pk)
+{
+    // first sorted position of every bin: exclusive scan of the bin counts
+    static_assert(kSortBins == 4 * 32, "one warp scans four bins per lane");
+    __shared__ int s_off[kSortBins];
+    static_assert(kParkedWords % 2 == 1, "an odd row length keeps the lanes' rows in distinct banks");
+    __shared__ float s_rec[256 / 32][32][kParkedWords];  // each warp's records
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        int c[4], sum = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            c[j] = pk.bin_count[4 * lane + j];
+            sum += c[j];
+        }
+        int x = sum;
+#pragma unroll
+        for (int o2 = 1; o2 < 32; o2 <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, x, o2);
+            if (lane >= o2) x += t;
+        }
+        int run = x - sum;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            s_off[4 * lane + j] = run;
+            run += c[j];
+        }
+    }
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = sv.n;
+    // 0: parked, 1: ended here, 2: beyond n (no early exits: the warp writes
+    // its seeds' records together below)
+    int state = 2, pos = -1;
+    float *t = s_rec[threadIdx.x >> 5][threadIdx.x & 31];
+    if (i < n) {
+        pos = s_off[sort_bin(sv.q2pt[i])] + pk.rank[i];
+        TrackState s;
+        const float alpha = sv.alpha[i];
+        const float sx = sv.x[i], sy = sv.y[i];
+        s.x = {sx, 0.0f};
+        s.y = {sy, 0.0f};
+        s.z = sv.z[i];
+        s.f = sv.snp[i];
+        s.t = sv.tgl[i];
+        s.k = sv.q2pt[i];
+#pragma unroll
+        for (int k = 0; k < 15; ++k) s.c[k] = sv.cov[k * n + i];
+        state = 1;
+        if (!(fabsf(s.f) < kMaxSnp) || !cov_pd(s.c)) {
+            write_seed_result(o, sv, n, i, TRD_ST_SEED_INVALID);
+        } else {
+            const float phi = alpha + atan2f(sy, sx);
+            float u = phi - kTwoPiHi * floorf(phi * (1.0f / kTwoPiHi));
+            int sec = static_cast<int>(u * (1.0f / kSectorWidthHi));
+            sec = min(max(sec, 0), kSectors - 1);
+            df d = df_add_f(sector_alpha_df(sec), -alpha);
+            if (d.hi > 3.14159265f) d = df_add(d, df{-kTwoPiHi, -kTwoPiLo});
+            if (d.hi < -3.14159265f) d = df_add(d, df{kTwoPiHi, kTwoPiLo});
+            s.sector = sec;
+            if (!rotate(s, d, sec, P.bzmap ? field_at(P, hypotf(sx, sy), s.z) : P.bz)) {
+                write_seed_result(o, sv, n, i, TRD_ST_PROP_FAIL);
+            } else {
+                state = 0;
+                t[0] = __int_as_float(sec);
+                t[1] = s.x.hi;
+                t[2] = s.x.lo;
+                t[3] = s.y.hi;
+                t[4] = s.y.lo;
+                t[5] = s.z;
+                t[6] = s.f;
+                t[7] = s.t;
+                t[8] = s.k;
+#pragma unroll
+                for (int k = 0; k < 15; ++k) t[9 + k] = s.c[k];
+                t[24] = __int_as_float(i);
+            }
+        }
+        pk.inv[i] = state == 0 ? pos : -1;
+    }
+    __syncwarp();
+    // the warp's records, one 100-byte record per store instruction
+    const int lane = threadIdx.x & 31;
+    float *recw = reinterpret_cast<float *>(pk.rec);
+    for (int j = 0; j < 32; ++j) {
+        const int pj = __shfl_sync(0xffffffffu, pos, j);
+        const int sj = __shfl_sync(0xffffffffu, state, j);
+        if (sj == 0 && lane < kParkedWords) recw[32 * static_cast<size_t>(pj) + lane] = s_rec[threadIdx.x >> 5][j][lane];
+        if (sj == 1 && lane == 0) reinterpret_cast<int *>(recw)[32 * static_cast<size_t>(pj)] = -1;
+    }
+}
+
+// Pick up the seed at sorted position pos as parked by k_seed_prepare; i is
+// its input index.  Returns false when the seed already has its final result.
+template <int G>
+__device__ __forceinline__ bool start_seed(int pos, int q, const SeedsView &sv, const ParkedView &pk, Lane &L,
+                                           int &i)
+{
+    // plain loads: the follower later stages the result in the same record
+    const float4 *rec = pk.rec + 8 * static_cast<size_t>(pos);
+    const float4 r0 = rec[0];
+    const int sec = __float_as_int(r0.x);
+    if (sec < 0) return false;
+    const float4 r1 = rec[1], r2 = rec[2], r3 = rec[3], r4 = rec[4], r5 = rec[5];
+    i = sv.soff || sv.trig ? __float_as_int(rec[6].x) : 0;  // the input index, for timeframe and interaction
+    TrackState &s = L.s;
+    s.sector = sec;
+    s.x = {r0.y, r0.z};
+    s.y = {r0.w, r1.x};
+    s.z = r1.y;
+    s.f = r1.z;
+    s.t = r1.w;
+    s.k = r2.x;
+    const float c[15] = {r2.y, r2.z, r2.w, r3.x, r3.y, r3.z, r3.w, r4.x, r4.y, r4.z, r4.w, r5.x, r5.y, r5.z, r5.w};
+#pragma unroll
+    for (int k = 0; k < 15; ++k) s.c[k] = c[k];
     L.cbase = tf_of(i, sv.soff, sv.n_tf) * kChambers;
     L.trig = sv.trig ? sv.trig[i] : -1;
     L.alive = q == 0;
@@ -635,9 +771,9 @@ __device__ __forceinline__ bool start_seed(int i, int q, const SeedsView &sv, co
 // One layer of seed i for the group.  Returns true when the seed is finished
 // (result written).
 template <int G, int NH, bool EXT>
-__device__ __forceinline__ bool layer_step(int i, int l, int q, unsigned gmask, const IndexView &ix, const Params &P,
-                                           const ResultsView &o, int n, float *sm, int stride, float vyy_max,
-                                           float vzz_max, float dx_max, Lane &H)
+__device__ __forceinline__ bool layer_step(int pos, int l, int q, unsigned gmask, const IndexView &ix, const Params &P,
+                                           float4 *res, float *sm, int stride, float vyy_max, float vzz_max,
+                                           float dx_max, Lane &H)
 {
     TrackState &s = H.s;
     if (q == 0) save_state(sm, stride, s);
@@ -706,7 +842,7 @@ __device__ __forceinline__ bool layer_step(int i, int l, int q, unsigned gmask, 
         if (q == 0) {
             TrackState b;
             load_state(sm, stride, b);
-            write_result(o, n, i, b, H.chisum, H.ntrk, H.nmiss, any_live ? TRD_ST_STOPPED : TRD_ST_PROP_FAIL, H.ids);
+            stage_result(res, pos, b, H.chisum, H.ntrk, H.nmiss, any_live ? TRD_ST_STOPPED : TRD_ST_PROP_FAIL, H.ids);
         }
         return true;
     }
@@ -759,7 +895,7 @@ __device__ __forceinline__ bool layer_step(int i, int l, int q, unsigned gmask, 
         for (int k = 0; k < kLayers; ++k) H.ids[k] = k == l ? idl : H.ids[k];
     }
     if (l == kLayers - 1) {
-        if (q == 0) write_result(o, n, i, s, H.chisum, H.ntrk, H.nmiss, TRD_ST_OK, H.ids);
+        if (q == 0) stage_result(res, pos, s, H.chisum, H.ntrk, H.nmiss, TRD_ST_OK, H.ids);
         return true;
     }
     return false;
@@ -769,7 +905,8 @@ __device__ __forceinline__ bool layer_step(int i, int l, int q, unsigned gmask, 
 // counter and over their layers in one flattened loop, so a lane whose seed
 // ends takes the next seed instead of idling while its warp finishes.
 template <int G, int NH, int MINB, bool EXT>
-__global__ void __launch_bounds__(128, MINB) k_follow(SeedsView sv, IndexView ix, Params P, ResultsView o, int *counter)
+__global__ void __launch_bounds__(128, MINB)
+k_follow(SeedsView sv, IndexView ix, Params P, ParkedView pk, int *counter)
 {
     extern __shared__ float smem[];
     const int groups = blockDim.x / G;
@@ -781,20 +918,53 @@ __global__ void __launch_bounds__(128, MINB) k_follow(SeedsView sv, IndexView ix
     const float vzz_max = __uint_as_float(__ldg(&ix.stats[1]));
     const float dx_max = EXT && ix.recx ? __uint_as_float(__ldg(&ix.stats[3])) : 0.0f;
     Lane H;
-    int i = 0, l = 0;
+    int pos = 0, l = 0;
     bool have = false;
     for (;;) {
         if (!have) {
-            i = fetch_seed<G>(counter, gmask, q);
-            if (i >= sv.n) break;
-            have = start_seed<G>(i, q, sv, o, H);
+            pos = fetch_seed<G>(counter, gmask, q);
+            if (pos >= sv.n) break;
+            int i;
+            have = start_seed<G>(pos, q, sv, pk, H, i);
             l = 0;
             if (!have) continue;
         }
-        if (layer_step<G, NH, EXT>(i, l, q, gmask, ix, P, o, sv.n, sm, groups, vyy_max, vzz_max, dx_max, H))
+        if (layer_step<G, NH, EXT>(pos, l, q, gmask, ix, P, pk.rec, sm, groups, vyy_max, vzz_max, dx_max, H))
             have = false;
         ++l;
     }
+}
+
+// The staged results to the seeds' input positions: thread i reads its
+// seed's 128-byte record and writes the result arrays with full lines.  Seeds
+// that ended in k_seed_prepare (inv -1) already have their results.
+__global__ void __launch_bounds__(256) k_results_gather(int n, ParkedView pk, ResultsView o)
+{
+    __shared__ float s_res[256 / 32][32][33];  // each warp's 32 records (odd row: no bank conflicts)
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int pos = i < n ? pk.inv[i] : -1;
+    // record j of the warp read by all lanes, one 128-byte line per load
+    const float *recw = reinterpret_cast<const float *>(pk.rec);
+    for (int j = 0; j < 32; ++j) {
+        const int pj = __shfl_sync(0xffffffffu, pos, j);
+        if (pj >= 0) s_res[w][j][lane] = recw[32 * static_cast<size_t>(pj) + lane];
+    }
+    __syncwarp();
+    if (pos < 0) return;
+    const float *r = s_res[w][lane];
+    o.alpha[i] = r[0];
+    o.x[i] = r[1];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) o.par[k * n + i] = r[2 + k];
+#pragma unroll
+    for (int k = 0; k < 15; ++k) o.cov[k * n + i] = r[7 + k];
+    o.chi2[i] = r[22];
+    o.ntrk[i] = __float_as_int(r[23]);
+    o.nmiss[i] = __float_as_int(r[24]);
+    o.status[i] = __float_as_int(r[25]);
+#pragma unroll
+    for (int l = 0; l < kLayers; ++l) o.ids[l * n + i] = __float_as_int(r[26 + l]);
 }
 
 }  // namespace trd
@@ -803,9 +973,23 @@ namespace trd_host {
 
 using namespace trd;
 
+// The seeds' pre-pass: bins and ranks, then the rotated states parked in
+// sorted order.
+static int prepare_kernels(const SeedsView &sv, const Params &P, const ResultsView &o, const ParkedView &pk,
+                           cudaStream_t s)
+{
+    TRD_CUDA_TRY(cudaMemsetAsync(pk.bin_count, 0, sizeof(int32_t) * kSortBins, s));
+    const int per_block = kKeyThreads * kKeyItems;
+    k_seed_key<<<(sv.n + per_block - 1) / per_block, kKeyThreads, 0, s>>>(sv.q2pt, sv.n, pk);
+    TRD_CUDA_TRY(cudaGetLastError());
+    k_seed_prepare<<<(sv.n + 255) / 256, 256, 0, s>>>(sv, P, o, pk);
+    TRD_CUDA_TRY(cudaGetLastError());
+    return TRD_OK;
+}
+
 template <int G, int NH, int MINB, bool EXT>
 static int launch(const trd_ctx *ctx, const SeedsView &sv, const IndexView &ix, const Params &P,
-                  const ResultsView &o, cudaStream_t s, int block, int *counter, bool prepare)
+                  const ResultsView &o, const ParkedView &pk, cudaStream_t s, int block, int *counter, bool prepare)
 {
     if (sv.n == 0) return TRD_OK;
     const int groups = block / G;
@@ -817,34 +1001,38 @@ static int launch(const trd_ctx *ctx, const SeedsView &sv, const IndexView &ix, 
     const int grid = static_cast<int>(std::min<long long>(need, static_cast<long long>(ctx->sm_count) * per_sm));
     TRD_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), s));
     if (prepare) {
-        k_seed_prepare<<<(sv.n + 255) / 256, 256, 0, s>>>(sv, P, o);
-        TRD_CUDA_TRY(cudaGetLastError());
+        const int rc = prepare_kernels(sv, P, o, pk, s);
+        if (rc) return rc;
     }
-    k_follow<G, NH, MINB, EXT><<<grid, block, smem, s>>>(sv, ix, P, o, counter);
+    k_follow<G, NH, MINB, EXT><<<grid, block, smem, s>>>(sv, ix, P, pk, counter);
+    TRD_CUDA_TRY(cudaGetLastError());
+    k_results_gather<<<(sv.n + 255) / 256, 256, 0, s>>>(sv.n, pk, o);
     TRD_CUDA_TRY(cudaGetLastError());
     return TRD_OK;
 }
 
 template <bool EXT>
 static int dispatch(const trd_ctx *ctx, const SeedsView &sv, const IndexView &iv, const Params &P,
-                    const ResultsView &o, cudaStream_t s, int G, int mb, int block, int nhyp, int *counter,
-                    bool prepare)
+                    const ResultsView &o, const ParkedView &pk, cudaStream_t s, int G, int mb, int block, int nhyp,
+                    int *counter, bool prepare)
 {
+#define TRD_LAUNCH(g, nh, m) launch<g, nh, m, EXT>(ctx, sv, iv, P, o, pk, s, block, counter, prepare)
     switch (G * 16 + mb) {
-    case 1 * 16 + 4: return nhyp == 1 ? launch<1, 1, 4, EXT>(ctx, sv, iv, P, o, s, block, counter, prepare) : TRD_EINVAL;
-    case 1 * 16 + 5: return nhyp == 1 ? launch<1, 1, 5, EXT>(ctx, sv, iv, P, o, s, block, counter, prepare) : TRD_EINVAL;
-    case 1 * 16 + 6: return nhyp == 1 ? launch<1, 1, 6, EXT>(ctx, sv, iv, P, o, s, block, counter, prepare) : TRD_EINVAL;
-    case 1 * 16 + 8: return nhyp == 1 ? launch<1, 1, 8, EXT>(ctx, sv, iv, P, o, s, block, counter, prepare) : TRD_EINVAL;
-    case 2 * 16 + 3: return launch<2, 2, 3, EXT>(ctx, sv, iv, P, o, s, block, counter, prepare);
-    case 2 * 16 + 4: return launch<2, 2, 4, EXT>(ctx, sv, iv, P, o, s, block, counter, prepare);
-    case 4 * 16 + 3: return launch<4, 4, 3, EXT>(ctx, sv, iv, P, o, s, block, counter, prepare);
-    case 4 * 16 + 4: return launch<4, 4, 4, EXT>(ctx, sv, iv, P, o, s, block, counter, prepare);
-    case 8 * 16 + 3: return launch<8, 8, 3, EXT>(ctx, sv, iv, P, o, s, block, counter, prepare);
-    case 8 * 16 + 4: return launch<8, 8, 4, EXT>(ctx, sv, iv, P, o, s, block, counter, prepare);
-    case 32 * 16 + 3: return launch<32, 8, 3, EXT>(ctx, sv, iv, P, o, s, block, counter, prepare);
-    case 32 * 16 + 4: return launch<32, 8, 4, EXT>(ctx, sv, iv, P, o, s, block, counter, prepare);
+    case 1 * 16 + 4: return nhyp == 1 ? TRD_LAUNCH(1, 1, 4) : TRD_EINVAL;
+    case 1 * 16 + 5: return nhyp == 1 ? TRD_LAUNCH(1, 1, 5) : TRD_EINVAL;
+    case 1 * 16 + 6: return nhyp == 1 ? TRD_LAUNCH(1, 1, 6) : TRD_EINVAL;
+    case 1 * 16 + 8: return nhyp == 1 ? TRD_LAUNCH(1, 1, 8) : TRD_EINVAL;
+    case 2 * 16 + 3: return TRD_LAUNCH(2, 2, 3);
+    case 2 * 16 + 4: return TRD_LAUNCH(2, 2, 4);
+    case 4 * 16 + 3: return TRD_LAUNCH(4, 4, 3);
+    case 4 * 16 + 4: return TRD_LAUNCH(4, 4, 4);
+    case 8 * 16 + 3: return TRD_LAUNCH(8, 8, 3);
+    case 8 * 16 + 4: return TRD_LAUNCH(8, 8, 4);
+    case 32 * 16 + 3: return TRD_LAUNCH(32, 8, 3);
+    case 32 * 16 + 4: return TRD_LAUNCH(32, 8, 4);
     default: return TRD_EINVAL;
     }
+#undef TRD_LAUNCH
 }
 
 static Params make_params(const trd_params_t *p, const trd_alignment_t *align)
@@ -866,26 +1054,27 @@ static Params make_params(const trd_params_t *p, const trd_alignment_t *align)
     return P;
 }
 
+size_t parked_bytes(int32_t n) { return n > 0 ? sizeof(int32_t) * parked_words(n) : 0; }
+
 // The seeds' pre-pass alone (it does not read the index, so a captured step
-// can run it beside the index build).
+// can run it beside the index build).  parked: parked_bytes(n) of device memory.
 int prepare_launch(const trd_seeds_t *seeds, const trd_params_t *p, trd_results_t *out, cudaStream_t s,
-                   const trd_alignment_t *align)
+                   void *parked, const trd_alignment_t *align)
 {
     if (seeds->n == 0) return TRD_OK;
+    if (!parked) return TRD_EINVAL;
     SeedsView sv{seeds->alpha, seeds->x, seeds->y, seeds->z, seeds->snp, seeds->tgl, seeds->q2pt, seeds->cov,
                  seeds->n, nullptr, 1, seeds->trigger};
     const Params P = make_params(p, align);
     ResultsView o{out->alpha, out->x, out->par, out->cov, out->chi2, out->n_trk, out->n_miss, out->status,
                   out->tracklet_id};
-    k_seed_prepare<<<(sv.n + 255) / 256, 256, 0, s>>>(sv, P, o);
-    TRD_CUDA_TRY(cudaGetLastError());
-    return TRD_OK;
+    return prepare_kernels(sv, P, o, parked_view(parked, seeds->n), s);
 }
 
 int follow_launch(const trd_ctx *ctx, const trd_seeds_t *seeds, const IndexView &iv, const trd_params_t *p,
                   trd_results_t *out, cudaStream_t s, int lanes_per_track, int block_threads, int min_blocks,
                   int *counter, const int32_t *seed_offsets, int n_tf, const trd_alignment_t *align,
-                  bool prepare)
+                  bool prepare, void *parked)
 {
     SeedsView sv{seeds->alpha, seeds->x, seeds->y, seeds->z, seeds->snp, seeds->tgl, seeds->q2pt, seeds->cov,
                  seeds->n, seed_offsets, n_tf, seeds->trigger};
@@ -898,8 +1087,24 @@ int follow_launch(const trd_ctx *ctx, const trd_seeds_t *seeds, const IndexView 
     if (G <= 0) G = p->n_hyp <= 1 ? 1 : (p->n_hyp <= 2 ? 2 : (p->n_hyp <= 4 ? 4 : 8));
     if (G < p->n_hyp) return TRD_EINVAL;
     const int mb = min_blocks > 0 ? min_blocks : 4;
-    return ext ? dispatch<true>(ctx, sv, iv, P, o, s, G, mb, block, p->n_hyp, counter, prepare)
-               : dispatch<false>(ctx, sv, iv, P, o, s, G, mb, block, p->n_hyp, counter, prepare);
+    // without a caller scratch: one from the device's pool, ordered on s
+    void *own = nullptr;
+    if (sv.n > 0 && !parked) {
+        if (!prepare) return TRD_EINVAL;  // the pre-pass's output is needed
+        if (cudaMallocAsync(&own, parked_bytes(sv.n), s) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return TRD_ENOMEM;
+        }
+        parked = own;
+    }
+    const ParkedView pk = sv.n > 0 ? parked_view(parked, sv.n) : ParkedView{};
+    const int rc = ext ? dispatch<true>(ctx, sv, iv, P, o, pk, s, G, mb, block, p->n_hyp, counter, prepare)
+                       : dispatch<false>(ctx, sv, iv, P, o, pk, s, G, mb, block, p->n_hyp, counter, prepare);
+    if (own && cudaFreeAsync(own, s) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return rc ? rc : TRD_ECUDA;
+    }
+    return rc;
 }
 
 }  // namespace trd_host

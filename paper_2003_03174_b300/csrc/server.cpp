@@ -68,7 +68,8 @@ size_t io_bytes(int n_seeds, int n_trk)
            align_up(28 * static_cast<size_t>(n_trk)) +                     // tracklets
            align_up(sizeof(int32_t) * static_cast<size_t>(n_seeds)) +      // seed interaction ids
            align_up(sizeof(int32_t) * static_cast<size_t>(n_trk)) +        // tracklet interaction ids
-           align_up(sizeof(float) * static_cast<size_t>(n_trk));           // tracklet radii
+           align_up(sizeof(float) * static_cast<size_t>(n_trk)) +          // tracklet radii
+           align_up(trd_host::parked_bytes(n_seeds));                       // the follower's pre-pass scratch
 }
 
 // bytes of an index for n_trk tracklets (records + build scratch + buckets)
@@ -128,6 +129,8 @@ int start_request(trd_server *S, Slot &slot, Request *r)
     int32_t *dtrig_t = reinterpret_cast<int32_t *>(p);
     p += align_up(sizeof(int32_t) * static_cast<size_t>(m));
     float *dx_t = reinterpret_cast<float *>(p);
+    p += align_up(sizeof(float) * static_cast<size_t>(m));
+    void *parked = n ? p : nullptr;
     // seeds: alpha x y z snp tgl q2pt cov[15] (22 rows of n)
     const float *hs[7] = {r->seeds.alpha, r->seeds.x, r->seeds.y, r->seeds.z, r->seeds.snp, r->seeds.tgl,
                           r->seeds.q2pt};
@@ -162,7 +165,8 @@ int start_request(trd_server *S, Slot &slot, Request *r)
                        di + 3 * static_cast<size_t>(n)};
     int rc = trd_index_rebuild(slot.index, &dtrk, st);
     if (rc) return rc;
-    rc = trd_follow_tuned(S->ctx, &dseeds, slot.index, &S->cfg.params, &dres, st, &S->cfg.launch);
+    rc = trd_host::follow_checked(S->ctx, &dseeds, slot.index, &S->cfg.params, nullptr, &dres, st, &S->cfg.launch,
+                                  parked);
     if (rc) return rc;
     // results back: alpha x par[5] cov[15] chi2 (23 float rows), then 9 int rows
     float *hf[5] = {r->out.alpha, r->out.x, r->out.par, r->out.cov, r->out.chi2};
