@@ -355,15 +355,22 @@ def run_ours(args):
     # end to end through the library's host-buffer entry point (the server):
     # pinned host inputs -> device, index + follow, results -> host, with the
     # copies of one timeframe overlapping the kernels of another
-    host_in = {k: torch.from_numpy(v).pin_memory() for k, v in tf.seeds.items()}
-    host_trk = {k: torch.from_numpy(v).pin_memory() for k, v in tf.tracklets.items()}
+    # one pinned block per timeframe in the server's copy order (one copy each way)
+    host_in, host_trk = trd.pinned_inputs(tf.seeds, tf.tracklets)
     h2d = sum(v.numel() * v.element_size() for v in list(host_in.values()) + list(host_trk.values()))
     slots = 4
     host_outs = [trd.host_results(n, pinned=True) for _ in range(slots)]
     d2h = sum(v.numel() * v.element_size() for v in host_outs[0].values())
     srv = trd.Server(ctx, tf.params, max_slots=slots, y_bin_width=bin_width, **shape)
-    for o in host_outs:  # warm: every slot's resident index
-        srv.wait(srv.submit(host_in, host_trk, o))
+    # warm-up with every slot busy, at least W rounds and 1 s: each slot's
+    # resident index, the device pool at its steady size for `slots` requests
+    # in flight, and the host link out of its idle state (after the kernel-only
+    # timing the first ~0.3 s of transfers run up to a third slower)
+    w0, rounds = time.monotonic(), 0
+    while rounds < max(1, args.warmup) or time.monotonic() - w0 < 1.0:
+        for t in [srv.submit(host_in, host_trk, o) for o in host_outs]:
+            srv.wait(t, 60_000)
+        rounds += 1
     e_steps = max(8, args.steps)
     t0 = time.monotonic()
     tickets = [srv.submit(host_in, host_trk, host_outs[k % slots]) for k in range(min(slots, e_steps))]
@@ -732,8 +739,7 @@ def run_served(args):
     dev = torch.device("cuda", 0)
     ctx = trd.Context(0)
     params = payloads[0].params
-    pin = [({k: torch.from_numpy(v).pin_memory() for k, v in tf.seeds.items()},
-            {k: torch.from_numpy(v).pin_memory() for k, v in tf.tracklets.items()}) for tf in payloads]
+    pin = [trd.pinned_inputs(tf.seeds, tf.tracklets) for tf in payloads]
     outs = [trd.host_results(tf.n_seeds, pinned=True) for tf in payloads]
     big = max(tf.n_tracklets for tf in payloads)
     nmax = max(tf.n_seeds for tf in payloads)
@@ -773,8 +779,14 @@ def run_served(args):
 
     srv = trd.Server(ctx, params, max_slots=args.slots, mem_budget_bytes=60 << 30)
     srv_outs = [trd.host_results(tf.n_seeds, pinned=True) for tf in payloads]
-    for j in range(len(payloads)):  # warm: grow every slot's resident index
+    # warm-up: grow every slot's resident index, then W rounds with every
+    # payload in flight (the device pool at its steady size, the pinned
+    # blocks' first transfers)
+    for j in range(len(payloads)):
         srv.wait(srv.submit(pin[j][0], pin[j][1], srv_outs[j]))
+    for _ in range(max(1, args.warmup)):
+        for t in [srv.submit(pin[j][0], pin[j][1], srv_outs[j]) for j in range(len(payloads))]:
+            srv.wait(t, 60_000)
     rng = np.random.Generator(np.random.Philox(key=99))
     points = []
     for mult in args.rates:

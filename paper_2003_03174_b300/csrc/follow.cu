@@ -946,6 +946,7 @@ __global__ void __launch_bounds__(256) k_results_gather(int n, ParkedView pk, Re
     const int pos = i < n ? pk.inv[i] : -1;
     // record j of the warp read by all lanes, one 128-byte line per load
     const float *recw = reinterpret_cast<const float *>(pk.rec);
+#pragma unroll 8
     for (int j = 0; j < 32; ++j) {
         const int pj = __shfl_sync(0xffffffffu, pos, j);
         if (pj >= 0) s_res[w][j][lane] = recw[32 * static_cast<size_t>(pj) + lane];

@@ -59,17 +59,16 @@ struct Slot {
 
 size_t align_up(size_t v) { return (v + 255) & ~static_cast<size_t>(255); }
 
-// bytes of one request's device inputs and outputs
+// bytes of one request's device buffer: inputs (seeds 22 rows of n,
+// tracklets 7 rows of m, interaction ids of seeds and tracklets, tracklet
+// radii) and outputs (23 float rows and 9 int rows of n), each packed without
+// gaps (4-byte elements) so that a caller's packed host block moves in one
+// copy, then the follower's scratch
 size_t io_bytes(int n_seeds, int n_trk)
 {
-    return align_up(sizeof(float) * 22 * static_cast<size_t>(n_seeds)) +   // seeds
-           align_up(sizeof(float) * 23 * static_cast<size_t>(n_seeds)) +   // float results
-           align_up(sizeof(int32_t) * 9 * static_cast<size_t>(n_seeds)) +  // int results
-           align_up(28 * static_cast<size_t>(n_trk)) +                     // tracklets
-           align_up(sizeof(int32_t) * static_cast<size_t>(n_seeds)) +      // seed interaction ids
-           align_up(sizeof(int32_t) * static_cast<size_t>(n_trk)) +        // tracklet interaction ids
-           align_up(sizeof(float) * static_cast<size_t>(n_trk)) +          // tracklet radii
-           align_up(trd_host::parked_bytes(n_seeds));                       // the follower's pre-pass scratch
+    const size_t n = static_cast<size_t>(n_seeds), m = static_cast<size_t>(n_trk);
+    return align_up(sizeof(float) * (22 * n + 7 * m + n + m + m)) + align_up(sizeof(float) * 32 * n) +
+           align_up(trd_host::parked_bytes(n_seeds));
 }
 
 // bytes of an index for n_trk tracklets (records + build scratch + buckets)
@@ -108,6 +107,36 @@ struct trd_server {
 
 namespace {
 
+// One request's copies in one direction, merged where both the host and the
+// device ranges continue the previous copy: a caller that keeps its arrays in
+// one block in the library's order gets one copy per block instead of one per
+// array (every copy costs the copy engine a fixed set-up time).
+struct CopyList {
+    struct Copy {
+        char *dst;
+        const char *src;
+        size_t bytes;
+    };
+    Copy c[32];
+    int k = 0;
+    void add(void *dst, const void *src, size_t bytes)
+    {
+        if (!bytes) return;
+        char *d = static_cast<char *>(dst);
+        const char *s = static_cast<const char *>(src);
+        if (k && c[k - 1].dst + c[k - 1].bytes == d && c[k - 1].src + c[k - 1].bytes == s) {
+            c[k - 1].bytes += bytes;
+            return;
+        }
+        c[k++] = {d, s, bytes};
+    }
+    int issue(cudaMemcpyKind kind, cudaStream_t st) const
+    {
+        for (int j = 0; j < k; ++j) TRD_CUDA_TRY(cudaMemcpyAsync(c[j].dst, c[j].src, c[j].bytes, kind, st));
+        return TRD_OK;
+    }
+};
+
 // enqueue one admitted request on its slot (scheduler thread, lock held)
 int start_request(trd_server *S, Slot &slot, Request *r)
 {
@@ -116,54 +145,50 @@ int start_request(trd_server *S, Slot &slot, Request *r)
     const size_t need = io_bytes(n, m);
     TRD_CUDA_TRY(cudaMallocAsync(&r->dbuf, std::max<size_t>(need, 256), st));
     char *p = static_cast<char *>(r->dbuf);
-    float *ds = reinterpret_cast<float *>(p);
-    p += align_up(sizeof(float) * 22 * static_cast<size_t>(n));
-    float *dr = reinterpret_cast<float *>(p);
-    p += align_up(sizeof(float) * 23 * static_cast<size_t>(n));
-    int32_t *di = reinterpret_cast<int32_t *>(p);
-    p += align_up(sizeof(int32_t) * 9 * static_cast<size_t>(n));
-    char *dt = p;
-    p += align_up(28 * static_cast<size_t>(m));
-    int32_t *dtrig_s = reinterpret_cast<int32_t *>(p);
-    p += align_up(sizeof(int32_t) * static_cast<size_t>(n));
-    int32_t *dtrig_t = reinterpret_cast<int32_t *>(p);
-    p += align_up(sizeof(int32_t) * static_cast<size_t>(m));
-    float *dx_t = reinterpret_cast<float *>(p);
-    p += align_up(sizeof(float) * static_cast<size_t>(m));
-    void *parked = n ? p : nullptr;
-    // seeds: alpha x y z snp tgl q2pt cov[15] (22 rows of n)
+    float *ds = reinterpret_cast<float *>(p);                  // seeds [22][n]
+    char *dt = reinterpret_cast<char *>(ds + 22 * static_cast<size_t>(n));  // tracklets [7][m]
+    int32_t *dtrig_s = reinterpret_cast<int32_t *>(dt) + 7 * static_cast<size_t>(m);
+    int32_t *dtrig_t = dtrig_s + n;
+    float *dx_t = reinterpret_cast<float *>(dtrig_t + m);
+    p += align_up(sizeof(float) * (22 * static_cast<size_t>(n) + 9 * static_cast<size_t>(m) + n));
+    float *dr = reinterpret_cast<float *>(p);                  // float results [23][n]
+    int32_t *di = reinterpret_cast<int32_t *>(dr + 23 * static_cast<size_t>(n));  // int results [9][n]
+    p += align_up(sizeof(float) * 32 * static_cast<size_t>(n));
+    void *parked = n ? p : nullptr;                            // 256-byte aligned
+    // inputs in device order: seeds alpha x y z snp tgl q2pt cov[15] (22 rows
+    // of n), tracklets chamber y z dy vyy vzz vyz (7 rows of m), interaction
+    // ids of seeds and tracklets, tracklet radii
     const float *hs[7] = {r->seeds.alpha, r->seeds.x, r->seeds.y, r->seeds.z, r->seeds.snp, r->seeds.tgl,
                           r->seeds.q2pt};
+    int32_t *dch = reinterpret_cast<int32_t *>(dt);
+    float *dtf = reinterpret_cast<float *>(dt) + m;
+    const float *ht[6] = {r->trk.y, r->trk.z, r->trk.dy, r->trk.vyy, r->trk.vzz, r->trk.vyz};
+    CopyList in;
+    if (n) {
+        for (int k = 0; k < 7; ++k) in.add(ds + static_cast<size_t>(k) * n, hs[k], sizeof(float) * n);
+        in.add(ds + 7 * static_cast<size_t>(n), r->seeds.cov, sizeof(float) * 15 * n);
+    }
+    if (m) {
+        in.add(dch, r->trk.chamber, sizeof(int32_t) * m);
+        for (int k = 0; k < 6; ++k) in.add(dtf + static_cast<size_t>(k) * m, ht[k], sizeof(float) * m);
+    }
+    if (n && r->seeds.trigger) in.add(dtrig_s, r->seeds.trigger, sizeof(int32_t) * n);
+    if (m && r->trk.trigger) in.add(dtrig_t, r->trk.trigger, sizeof(int32_t) * m);
+    if (m && r->trk.x) in.add(dx_t, r->trk.x, sizeof(float) * m);
     TRD_CUDA_TRY(cudaEventRecord(r->ev0, st));
-    for (int k = 0; k < 7; ++k)
-        if (n) TRD_CUDA_TRY(cudaMemcpyAsync(ds + static_cast<size_t>(k) * n, hs[k], sizeof(float) * n,
-                                            cudaMemcpyHostToDevice, st));
-    if (n) TRD_CUDA_TRY(cudaMemcpyAsync(ds + 7 * static_cast<size_t>(n), r->seeds.cov, sizeof(float) * 15 * n,
-                                        cudaMemcpyHostToDevice, st));
-    if (n && r->seeds.trigger)
-        TRD_CUDA_TRY(cudaMemcpyAsync(dtrig_s, r->seeds.trigger, sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
-    if (m && r->trk.trigger)
-        TRD_CUDA_TRY(cudaMemcpyAsync(dtrig_t, r->trk.trigger, sizeof(int32_t) * m, cudaMemcpyHostToDevice, st));
-    if (m && r->trk.x)
-        TRD_CUDA_TRY(cudaMemcpyAsync(dx_t, r->trk.x, sizeof(float) * m, cudaMemcpyHostToDevice, st));
+    int rc = in.issue(cudaMemcpyHostToDevice, st);
+    if (rc) return rc;
     trd_seeds_t dseeds{ds, ds + n, ds + 2 * static_cast<size_t>(n), ds + 3 * static_cast<size_t>(n),
                        ds + 4 * static_cast<size_t>(n), ds + 5 * static_cast<size_t>(n),
                        ds + 6 * static_cast<size_t>(n), ds + 7 * static_cast<size_t>(n), n,
                        r->seeds.trigger ? dtrig_s : nullptr};
-    int32_t *dch = reinterpret_cast<int32_t *>(dt);
-    float *dtf = reinterpret_cast<float *>(dt) + m;
-    if (m) TRD_CUDA_TRY(cudaMemcpyAsync(dch, r->trk.chamber, sizeof(int32_t) * m, cudaMemcpyHostToDevice, st));
-    const float *ht[6] = {r->trk.y, r->trk.z, r->trk.dy, r->trk.vyy, r->trk.vzz, r->trk.vyz};
-    for (int k = 0; k < 6; ++k)
-        if (m) TRD_CUDA_TRY(cudaMemcpyAsync(dtf + static_cast<size_t>(k) * m, ht[k], sizeof(float) * m,
-                                            cudaMemcpyHostToDevice, st));
     trd_tracklets_t dtrk{dch, dtf, dtf + m, dtf + 2 * static_cast<size_t>(m), dtf + 3 * static_cast<size_t>(m),
                          dtf + 4 * static_cast<size_t>(m), dtf + 5 * static_cast<size_t>(m), m,
                          r->trk.trigger ? dtrig_t : nullptr, r->trk.x ? dx_t : nullptr};
     trd_results_t dres{dr, dr + n, dr + 2 * static_cast<size_t>(n), dr + 7 * static_cast<size_t>(n),
                        dr + 22 * static_cast<size_t>(n), di, di + n, di + 2 * static_cast<size_t>(n),
                        di + 3 * static_cast<size_t>(n)};
-    int rc = trd_index_rebuild(slot.index, &dtrk, st);
+    rc = trd_index_rebuild(slot.index, &dtrk, st);
     if (rc) return rc;
     rc = trd_host::follow_checked(S->ctx, &dseeds, slot.index, &S->cfg.params, nullptr, &dres, st, &S->cfg.launch,
                                   parked);
@@ -171,18 +196,23 @@ int start_request(trd_server *S, Slot &slot, Request *r)
     // results back: alpha x par[5] cov[15] chi2 (23 float rows), then 9 int rows
     float *hf[5] = {r->out.alpha, r->out.x, r->out.par, r->out.cov, r->out.chi2};
     const int rows_f[5] = {1, 1, 5, 15, 1};
-    size_t off = 0;
-    for (int k = 0; k < 5; ++k) {
-        if (n) TRD_CUDA_TRY(cudaMemcpyAsync(hf[k], dr + off, sizeof(float) * rows_f[k] * n, cudaMemcpyDeviceToHost, st));
-        off += static_cast<size_t>(rows_f[k]) * n;
-    }
     int32_t *hi[4] = {r->out.n_trk, r->out.n_miss, r->out.status, r->out.tracklet_id};
     const int rows_i[4] = {1, 1, 1, 6};
-    off = 0;
-    for (int k = 0; k < 4; ++k) {
-        if (n) TRD_CUDA_TRY(cudaMemcpyAsync(hi[k], di + off, sizeof(int32_t) * rows_i[k] * n, cudaMemcpyDeviceToHost, st));
-        off += static_cast<size_t>(rows_i[k]) * n;
+    CopyList out;
+    if (n) {
+        size_t off = 0;
+        for (int k = 0; k < 5; ++k) {
+            out.add(hf[k], dr + off, sizeof(float) * rows_f[k] * n);
+            off += static_cast<size_t>(rows_f[k]) * n;
+        }
+        off = 0;
+        for (int k = 0; k < 4; ++k) {
+            out.add(hi[k], di + off, sizeof(int32_t) * rows_i[k] * n);
+            off += static_cast<size_t>(rows_i[k]) * n;
+        }
     }
+    rc = out.issue(cudaMemcpyDeviceToHost, st);
+    if (rc) return rc;
     TRD_CUDA_TRY(cudaEventRecord(r->ev1, st));
     TRD_CUDA_TRY(cudaFreeAsync(r->dbuf, st));
     r->dbuf = nullptr;

@@ -279,21 +279,65 @@ def _hptr(a):
     return C.c_void_p(a.ctypes.data)
 
 
+_RESULT_ROWS = (("alpha", 1, "f"), ("x", 1, "f"), ("par", 5, "f"), ("cov", 15, "f"), ("chi2", 1, "f"),
+                ("n_trk", 1, "i"), ("n_miss", 1, "i"), ("status", 1, "i"), ("tracklet_id", 6, "i"))
+
+
+def _pinned_views(block, rows, n):
+    """Views of one pinned int32 block: (name, rows, 'f' | 'i') in order."""
+    import torch
+    out, o = {}, 0
+    for name, r, kind in rows:
+        v = block[o:o + r * n]
+        v = v.view(torch.float32) if kind == "f" else v
+        out[name] = v.view(r, n) if r > 1 else v
+        o += r * n
+    return out
+
+
 def host_results(n: int, pinned: bool = False):
-    """Host result arrays (numpy, or pinned torch CPU tensors)."""
+    """Host result arrays (numpy, or views of one pinned block in the order
+    the server copies them back, so each request's results come in one copy)."""
     if pinned:
         import torch
-        f = dict(dtype=torch.float32, pin_memory=True)
-        i = dict(dtype=torch.int32, pin_memory=True)
-        return dict(alpha=torch.empty(n, **f), x=torch.empty(n, **f), par=torch.empty(5, n, **f),
-                    cov=torch.empty(15, n, **f), chi2=torch.empty(n, **f), n_trk=torch.empty(n, **i),
-                    n_miss=torch.empty(n, **i), status=torch.empty(n, **i),
-                    tracklet_id=torch.empty(6, n, **i))
+        block = torch.empty(32 * n, dtype=torch.int32, pin_memory=True)
+        return _pinned_views(block, _RESULT_ROWS, n)
     import numpy as np
     f, i = np.float32, np.int32
     return dict(alpha=np.empty(n, f), x=np.empty(n, f), par=np.empty((5, n), f), cov=np.empty((15, n), f),
                 chi2=np.empty(n, f), n_trk=np.empty(n, i), n_miss=np.empty(n, i), status=np.empty(n, i),
                 tracklet_id=np.empty((6, n), i))
+
+
+def pinned_inputs(seeds: dict, tracklets: dict, pin: bool = True):
+    """A timeframe's host inputs copied into one (pinned) block in the order
+    the server copies them to the device (seeds, tracklets, interaction ids of
+    seeds and tracklets, tracklet radii), so each request's inputs go in one
+    copy.  Returns (seeds, tracklets) dicts of views into the block."""
+    import numpy as np
+    import torch
+    n, m = len(seeds["alpha"]), len(tracklets["chamber"])
+    srows = [(k, 1, "f") for k in ("alpha", "x", "y", "z", "snp", "tgl", "q2pt")] + [("cov", 15, "f")]
+    trows = [("chamber", 1, "i")] + [(k, 1, "f") for k in ("y", "z", "dy", "vyy", "vzz", "vyz")]
+    words = 22 * n + 7 * m + (n if "trigger" in seeds else 0) + \
+        (m if "trigger" in tracklets else 0) + (m if "x" in tracklets else 0)
+    block = torch.empty(words, dtype=torch.int32, pin_memory=pin)
+    hs = _pinned_views(block[:22 * n], srows, n)
+    ht = _pinned_views(block[22 * n:22 * n + 7 * m], trows, m)
+    o = 22 * n + 7 * m
+    if "trigger" in seeds:
+        hs["trigger"] = block[o:o + n]
+        o += n
+    if "trigger" in tracklets:
+        ht["trigger"] = block[o:o + m]
+        o += m
+    if "x" in tracklets:
+        ht["x"] = block[o:o + m].view(torch.float32)
+        o += m
+    for src, dst in ((seeds, hs), (tracklets, ht)):
+        for k, v in dst.items():
+            v.copy_(torch.from_numpy(np.ascontiguousarray(src[k])).reshape(v.shape))
+    return hs, ht
 
 
 class Server:
