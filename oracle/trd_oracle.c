@@ -166,7 +166,8 @@ static double asin_over_deriv(double w)
  * between the end points has slope tan((phi0+phi1)/2) = (f0+f1)/(r0+r1); the
  * arc is the chord times asin(w)/w with w = rho * chord / 2; z advances by
  * tgl times the transverse arc.
- * Returns 0, or -1 when |snp| reaches kMaxSnp at either end (state untouched).
+ * Returns 0, or -1 when |snp| reaches kMaxSnp at either end or is not a
+ * number (state untouched).
  * J (25 doubles, row major, optional) receives d(p1)/d(p0).                */
 int ora_propagate(double st[7], double c[15], double xk, double bz, double *jac_out,
                   double *snp_slack)
@@ -180,7 +181,8 @@ int ora_propagate(double st[7], double c[15], double xk, double bz, double *jac_
         double s = kMaxSnp - fmax(fabs(f0), fabs(f1));
         *snp_slack = fmin(*snp_slack, fabs(s));
     }
-    if (fabs(f0) >= kMaxSnp || fabs(f1) >= kMaxSnp) return -1;
+    /* a sin(phi) that is not a number has no place below the limit either */
+    if (!(fabs(f0) < kMaxSnp) || !(fabs(f1) < kMaxSnp)) return -1;
     const double r0 = sqrt((1.0 - f0) * (1.0 + f0));
     const double r1 = sqrt((1.0 - f1) * (1.0 + f1));
     const double rs = r0 + r1;
@@ -233,7 +235,7 @@ int ora_rotate(double st[7], double c[15], double alpha_new, double bz, double *
     const double fn = f * cd - r * sd;
     const double rn = r * cd + f * sd;
     if (snp_slack) *snp_slack = fmin(*snp_slack, fabs(kMaxSnp - fabs(fn)));
-    if (fabs(fn) >= kMaxSnp || rn <= 0) return -1;
+    if (!(fabs(fn) < kMaxSnp) || !(rn > 0)) return -1;  /* NaN fails too */
     const double rho = -kCLight * bz * st[6];
     double J[5][5];
     eye5(J);

@@ -244,3 +244,49 @@ def test_association_parity(ctx, n_hyp):
     ids = g["tracklet_id"]
     ok = ids >= 0
     assert np.all(tf.tracklets["trigger"][ids[ok]] == np.broadcast_to(tf.seeds["trigger"], ids.shape)[ok])
+
+
+@pytest.mark.parametrize("n_hyp", [1, 3])
+def test_seed_order_does_not_change_results(ctx, n_hyp):
+    """The follower takes seeds in order of |q/pT|; a seed's result does not
+    depend on where it sits in the input: permuted seeds give the permuted
+    results, bit for bit."""
+    p = G.default_params(n_hyp=n_hyp)
+    tf = make_timeframe(6000, seed=41 + n_hyp, noise=0.3, params=p)
+    base, _ = run_gpu(ctx, tf, params=p)
+    perm = np.random.default_rng(7).permutation(tf.n_seeds)
+    s = {k: np.ascontiguousarray(v[..., perm]) for k, v in tf.seeds.items()}
+    g, _ = run_gpu(ctx, tf, params=p, seeds=s)
+    for k in base:
+        np.testing.assert_array_equal(g[k], base[k][..., perm], err_msg=k)
+
+
+def test_momentum_order_edge_cases(ctx):
+    """Seeds at the ends of the |q/pT| order against the oracle: NaN q/pT
+    (first bin; the transport fails), |q/pT| = 40 c/GeV (first bin; the
+    helix cannot reach the layers), q/pT = 0 (last bin; a straight line)."""
+    tf = make_workload("tiny", seed=16)
+    s = {k: v.copy() for k, v in tf.seeds.items()}
+    s["q2pt"][:4] = np.nan
+    s["q2pt"][4:8] = 0.0
+    s["q2pt"][8:12] = 40.0
+    s["q2pt"][12:16] = -40.0
+    g, _ = run_gpu(ctx, tf, seeds=s)
+    o = O.follow(s, tf.tracklets, tf.params)
+    np.testing.assert_array_equal(g["status"][:16], o["status"][:16])
+    np.testing.assert_array_equal(g["tracklet_id"][:, :16], o["tracklet_id"][:, :16])
+    assert np.all(g["status"][:4] == O.STATUS_PROP_FAIL) and np.all(g["status"][8:16] == O.STATUS_PROP_FAIL)
+    fin = np.arange(4, tf.n_seeds)
+    compare(g, {k: v[..., fin] for k, v in o.items()}, sel=fin)
+
+
+@pytest.mark.parametrize("n", [1, 2049])
+def test_one_momentum_bin(ctx, n):
+    """Every seed with the same q/pT: one bin holds them all (the key kernel's
+    atomics all on one counter), a single seed, and a ragged second block."""
+    tf = make_timeframe(n, seed=17 + n, noise=0.3)
+    s = {k: v.copy() for k, v in tf.seeds.items()}
+    s["q2pt"][:] = np.float32(0.8)
+    g, _ = run_gpu(ctx, tf, seeds=s)
+    o = O.follow(s, tf.tracklets, tf.params)
+    compare(g, o)
