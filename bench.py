@@ -60,9 +60,9 @@ REFIT_BYTES_PER_TRACKLET = 24
 # ~250, material ~60)
 REFIT_FLOPS_PER_LAYER = 460
 # DRAM bytes (read + write) of one k_refit launch on the 200k-seed timeframe
-# from one ncu capture (39.05 MB read, 0.85 MB written: the 20 MB of output
+# from one ncu capture (39.05 MB read, 0.76 MB written: the 20 MB of output
 # is still in L2 when the kernel ends), valid only for the source measured.
-REFIT_TRAFFIC = {"source_sha256_16": "cdaab0d31a37f941", "bytes": 39.90e6}
+REFIT_TRAFFIC = {"source_sha256_16": "d0afd33335175e46", "bytes": 39.81e6}
 # DRAM bytes (read + write) of one trd_follow call on this workload from one
 # ncu capture of its four kernels (k_seed_key 0.81 MB, k_seed_prepare 20.93 MB,
 # k_follow 59.91 MB, k_results_gather 26.41 MB; ncu empties the caches before
