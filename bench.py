@@ -212,7 +212,8 @@ def cpu_baseline(tf, sample_seeds: int, reps: int = 1, align=None):
     dt_rf = (time.perf_counter() - t1) / rf_reps
     refitted = int((rf["status"] == 0).sum())
     return dict(value=matched / dt, unit=UNIT, cores=os.cpu_count(), kind="oracle",
-                sample=f"{len(sel)} of {n} seeds (every {n // len(sel)}th) against all "
+                sample=(f"all {n} seeds" if len(sel) == n else
+                        f"{len(sel)} of {n} seeds (every {n // len(sel)}th)") + " against all "
                        f"{tf.n_tracklets} tracklets; chamber bucketing included; {dt:.2f} s",
                 seconds=dt, seeds=len(sel), matched=matched,
                 refit=dict(value=refitted / dt_rf, unit="refitted tracks/s", cores=os.cpu_count(),
@@ -400,8 +401,9 @@ def run_ours(args):
             "peak": hbm if hbm else 6400.0, "unit": "GB/s",
             "peak_source": "measured" if hbm else "fallback",
             "frac": achieved / (hbm if hbm else 6400.0),
+            # captured for the default instance only (the aligned one: profiles/k_follow_aligned_timeframe.md)
             "traffic": FOLLOW_TRAFFIC["bytes"] if _follow_source_hash() == FOLLOW_TRAFFIC["source_sha256_16"]
-            and tf.n_seeds == 200_000 else None,
+            and tf.n_seeds == 200_000 and not align else None,
             "traffic_unit": "bytes per launch (ncu dram read+write)",
             "algorithmic_bytes_per_launch": n * FOLLOW_BYTES_PER_SEED,
             "follow_ms": statistics.mean(follow_ms), "index_ms": statistics.mean(index_ms),
@@ -715,7 +717,8 @@ def residual_cpu_baseline(w, sample_tracks):
     dt = time.perf_counter() - t0
     n_cl = int(r["sums"][:, 0].sum())
     return {"value": n_cl / dt, "unit": "clusters/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"first {m} of {w.n_tracks} tracks ({n_cl} clusters); {dt:.2f} s"}
+            "sample": (f"all {m} tracks" if m == w.n_tracks else f"first {m} of {w.n_tracks} tracks") +
+                      f" ({n_cl} clusters); {dt:.2f} s"}
 
 
 def _pct(v, q):
@@ -867,7 +870,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--bin-width", type=float, default=0.0)
-    ap.add_argument("--cpu-sample", type=int, default=40_000)
+    ap.add_argument("--cpu-sample", type=int, default=200_000, help="seeds the CPU baseline follows")
     ap.add_argument("--ref-sample", type=int, default=20_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
@@ -875,7 +878,7 @@ def main():
     ap.add_argument("--workload", choices=["timeframe", "batched", "served", "residuals"], default="timeframe")
     ap.add_argument("--map-tracks", type=int, default=450_000, help="tracks of the residual workload")
     ap.add_argument("--min-count", type=int, default=50, help="clusters a voxel needs to be solved")
-    ap.add_argument("--cpu-sample-tracks", type=int, default=60_000)
+    ap.add_argument("--cpu-sample-tracks", type=int, default=450_000, help="tracks of the residual CPU baseline")
     ap.add_argument("--n-tf", type=int, default=64)
     ap.add_argument("--alignment", action="store_true",
                     help="misaligned chambers, per-tracklet radii and a field map (trd_follow_aligned)")
