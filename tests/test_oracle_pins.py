@@ -179,6 +179,24 @@ def test_snp_limit_fails_transport():
     assert not ok
 
 
+def test_undefined_snp_fails_transport_and_rotation():
+    """A sin(phi) that is not a number (a NaN q/pT after one step) cannot lie
+    below the limit: the transport and the rotation fail, and a seed with a
+    NaN q/pT ends with PROP_FAIL at its first layer, no tracklet attached."""
+    st = np.array([0.0, 300.0, 0.0, 0.0, 0.2, 0.1, np.nan])
+    ok, _, _, _ = O.propagate(st, _random_cov(), 310.0, 0.5)
+    assert not ok
+    st = np.array([0.0, 300.0, 0.0, 0.0, np.nan, 0.1, 1.0])
+    ok, _, _, _ = O.rotate(st, _random_cov(), math.radians(20.0), 0.5)
+    assert not ok
+    tf = make_workload("tiny")
+    s2 = {k: v.copy() for k, v in tf.seeds.items()}
+    s2["q2pt"][:6] = np.nan
+    r = O.follow(s2, tf.tracklets, tf.params, seed_index=np.arange(8))
+    assert np.all(r["status"][:6] == O.STATUS_PROP_FAIL)
+    assert np.all(r["tracklet_id"][:, :6] == -1) and np.all(r["n_trk"][:6] == 0)
+
+
 # ---------------------------------------------------------------- rotation
 def test_rotation_round_trip_is_identity():
     for _ in range(30):
