@@ -211,6 +211,13 @@ def cpu_baseline(tf, sample_seeds: int, reps: int = 1, align=None):
             break
     dt_rf = (time.perf_counter() - t1) / rf_reps
     refitted = int((rf["status"] == 0).sum())
+    # one host thread on every 20th seed of the sample, then all threads again
+    sel1 = sel[::20]
+    t2 = time.perf_counter()
+    r1 = O.follow(tf.seeds, tf.tracklets, tf.params, seed_index=sel1, n_threads=1, **akw)
+    dt1 = time.perf_counter() - t2
+    O.follow(tf.seeds, tf.tracklets, tf.params, seed_index=sel[:64], n_threads=os.cpu_count(), **akw)
+    matched1 = int((r1["n_trk"] >= 2).sum())
     return dict(value=matched / dt, unit=UNIT, cores=os.cpu_count(), kind="oracle",
                 sample=(f"all {n} seeds" if len(sel) == n else
                         f"{len(sel)} of {n} seeds (every {n // len(sel)}th)") + " against all "
@@ -219,7 +226,10 @@ def cpu_baseline(tf, sample_seeds: int, reps: int = 1, align=None):
                 refit=dict(value=refitted / dt_rf, unit="refitted tracks/s", cores=os.cpu_count(),
                            kind="oracle", sample=f"the {len(sel)} sampled tracks' refit ({refitted} "
                                                  f"refitted); {1e3 * dt_rf:.1f} ms each, "
-                                                 f"{rf_reps} repeats"))
+                                                 f"{rf_reps} repeats"),
+                one_thread=dict(value=matched1 / dt1, unit=UNIT, cores=1, kind="oracle",
+                                sample=f"{len(sel1)} seeds (every 20th of the sample) against all "
+                                       f"tracklets; {dt1:.2f} s"))
 
 
 def run_reference(args):
@@ -448,12 +458,17 @@ def run_ours(args):
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
             "seeds_per_s": n * ws * args.steps / total_s,
+            # the resident-index serving case: the follower call alone (index
+            # already built), separate launches
+            "without_index": {"value": matched_all * args.steps / (sum(follow_ms) / 1e3), "unit": UNIT,
+                              "ms_per_step": statistics.mean(follow_ms)},
             "refit": refit,
         }
         if ws == 1 and not args.no_cpu_baseline:
             cb = cpu_baseline(tf, args.cpu_sample,
                               align=dict(chamber_x=tf.chamber_x, field=fm) if align else None)
             line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+            line["cpu_baseline"]["one_thread"] = cb["one_thread"]
             line["refit"]["cpu_baseline"] = cb["refit"]
         print(json.dumps(line), flush=True)
     if ws > 1:
