@@ -48,6 +48,13 @@ FOLLOW_BYTES_PER_SEED = SEED_BYTES + RESULT_BYTES + RECORD_BYTES * IN_ROAD_PER_S
 # candidates x 10, 2.6 in-road candidates x 25, Joseph update ~240 on ~80 % of
 # layers; six layers.
 FOLLOW_FLOPS_PER_SEED = 3700
+# The calibration pass (450k seeds, N = 6, 5-sigma road, 2 cm systematic
+# error): 590.4 in-road tracklets per seed over its layers and hypotheses
+# (the oracle on 2,000 sampled seeds); FP32 model: 6 layers x 6 hypotheses x
+# ~550 (transport, material, road set-up, update) + 590 candidates x ~35.
+CAL_IN_ROAD_PER_SEED = 590.4
+CAL_FOLLOW_BYTES_PER_SEED = SEED_BYTES + RESULT_BYTES + RECORD_BYTES * CAL_IN_ROAD_PER_SEED
+CAL_FOLLOW_FLOPS_PER_SEED = 6 * 6 * 550 + 590 * 35
 L2_FLUSH_BYTES = 512 << 20
 # TRD-only refit (trd_refit), algorithmic bytes: per track the follower
 # result fields it reads (alpha, x, 5 parameters, 5 covariance diagonal
@@ -279,7 +286,10 @@ def run_ours(args):
     ctx = trd.Context(local)
 
     align = args.alignment
-    tf = make_workload(WORKLOAD, seed=rank_workload_seed(rank),  # each rank: its own timeframe
+    wl = "calibration" if args.workload == "calibration" else WORKLOAD
+    bytes_per_seed = CAL_FOLLOW_BYTES_PER_SEED if wl == "calibration" else FOLLOW_BYTES_PER_SEED
+    flops_per_seed = CAL_FOLLOW_FLOPS_PER_SEED if wl == "calibration" else FOLLOW_FLOPS_PER_SEED
+    tf = make_workload(wl, seed=rank_workload_seed(rank),  # each rank: its own timeframe
                        n_interactions=args.association, misalign=0.5 if align else 0.0,
                        x_jitter=0.1 if align else 0.0)
     seeds = trd.to_device(tf.seeds, dev)
@@ -405,7 +415,7 @@ def run_ours(args):
     peaks = _peaks()
     hbm = peaks.get("hbm_gbs")
     follow_avg_s = statistics.mean(follow_ms) / 1e3
-    achieved = n * FOLLOW_BYTES_PER_SEED / follow_avg_s / 1e9
+    achieved = n * bytes_per_seed / follow_avg_s / 1e9
     roof = {"bound": "hbm", "kernel": "trd_follow (k_seed_key + k_seed_prepare + k_follow + k_results_gather)",
             "achieved": achieved,
             "peak": hbm if hbm else 6400.0, "unit": "GB/s",
@@ -413,13 +423,13 @@ def run_ours(args):
             "frac": achieved / (hbm if hbm else 6400.0),
             # captured for the default instance only (the aligned one: profiles/k_follow_aligned_timeframe.md)
             "traffic": FOLLOW_TRAFFIC["bytes"] if _follow_source_hash() == FOLLOW_TRAFFIC["source_sha256_16"]
-            and tf.n_seeds == 200_000 and not align else None,
+            and tf.n_seeds == 200_000 and wl == WORKLOAD and not align else None,
             "traffic_unit": "bytes per launch (ncu dram read+write)",
-            "algorithmic_bytes_per_launch": n * FOLLOW_BYTES_PER_SEED,
+            "algorithmic_bytes_per_launch": n * bytes_per_seed,
             "follow_ms": statistics.mean(follow_ms), "index_ms": statistics.mean(index_ms),
             "step_ms_separate_launches": statistics.mean(split_ms)}
     fp32_peak = ctx.fp32_peak_tflops()
-    alu = {"bound": "alu", "achieved": n * FOLLOW_FLOPS_PER_SEED / follow_avg_s / 1e12, "peak": fp32_peak,
+    alu = {"bound": "alu", "achieved": n * flops_per_seed / follow_avg_s / 1e12, "peak": fp32_peak,
            "unit": "TFLOP/s", "peak_source": "measured by trd_measure_fp32_peak (FMA chains)"}
     alu["frac"] = alu["achieved"] / fp32_peak
     roof["alu_check"] = alu
@@ -436,8 +446,9 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded Pb-Pb-like timeframe: truth helices, 90% efficient "
                     "tracklets, 30% noise)",
-            "config": {"workload": f"{WORKLOAD}: {n} seeds, {tf.n_tracklets} tracklets per rank, "
-                                   f"N=1, 3-sigma road, chi2<15, <=2 missing",
+            "config": {"workload": f"{wl}: {n} seeds, {tf.n_tracklets} tracklets per rank, "
+                                   f"N={tf.params['n_hyp']}, {tf.params['n_sigma_road']:g}-sigma road, "
+                                   f"chi2<{tf.params['chi2_cut']:g}, <={tf.params['max_missing']} missing",
                        "seeds_per_rank": n, "tracklets_per_rank": tf.n_tracklets,
                        "interactions": args.association or None,
                        "alignment": "misaligned chambers (+-0.5 cm), tracklet radii (+-0.1 cm), Bz(r,z) map"
@@ -465,7 +476,8 @@ def run_ours(args):
             "refit": refit,
         }
         if ws == 1 and not args.no_cpu_baseline:
-            cb = cpu_baseline(tf, args.cpu_sample,
+            # the calibration pass's oracle runs ~50x longer per seed: 10,000 of them
+            cb = cpu_baseline(tf, args.cpu_sample if wl == WORKLOAD else min(args.cpu_sample, 10_000),
                               align=dict(chamber_x=tf.chamber_x, field=fm) if align else None)
             line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
             line["cpu_baseline"]["one_thread"] = cb["one_thread"]
@@ -890,7 +902,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="time separate launches instead of the graph")
-    ap.add_argument("--workload", choices=["timeframe", "batched", "served", "residuals"], default="timeframe")
+    ap.add_argument("--workload", choices=["timeframe", "calibration", "batched", "served", "residuals"],
+                    default="timeframe")
     ap.add_argument("--map-tracks", type=int, default=450_000, help="tracks of the residual workload")
     ap.add_argument("--min-count", type=int, default=50, help="clusters a voxel needs to be solved")
     ap.add_argument("--cpu-sample-tracks", type=int, default=450_000, help="tracks of the residual CPU baseline")
