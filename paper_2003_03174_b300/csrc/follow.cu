@@ -1025,10 +1025,12 @@ static int dispatch(const trd_ctx *ctx, const SeedsView &sv, const IndexView &iv
     case 1 * 16 + 8: return nhyp == 1 ? TRD_LAUNCH(1, 1, 8) : TRD_EINVAL;
     case 2 * 16 + 3: return TRD_LAUNCH(2, 2, 3);
     case 2 * 16 + 4: return TRD_LAUNCH(2, 2, 4);
-    case 4 * 16 + 3: return TRD_LAUNCH(4, 4, 3);
-    case 4 * 16 + 4: return TRD_LAUNCH(4, 4, 4);
-    case 8 * 16 + 3: return TRD_LAUNCH(8, 8, 3);
-    case 8 * 16 + 4: return TRD_LAUNCH(8, 8, 4);
+    // up to three hypotheses in a group of 4: lists of 3
+    case 4 * 16 + 3: return nhyp <= 3 ? TRD_LAUNCH(4, 3, 3) : TRD_LAUNCH(4, 4, 3);
+    case 4 * 16 + 4: return nhyp <= 3 ? TRD_LAUNCH(4, 3, 4) : TRD_LAUNCH(4, 4, 4);
+    // up to six hypotheses in a group of 8: lists of 6 (fewer registers)
+    case 8 * 16 + 3: return nhyp <= 6 ? TRD_LAUNCH(8, 6, 3) : TRD_LAUNCH(8, 8, 3);
+    case 8 * 16 + 4: return nhyp <= 6 ? TRD_LAUNCH(8, 6, 4) : TRD_LAUNCH(8, 8, 4);
     case 32 * 16 + 3: return TRD_LAUNCH(32, 8, 3);
     case 32 * 16 + 4: return TRD_LAUNCH(32, 8, 4);
     default: return TRD_EINVAL;
