@@ -217,16 +217,20 @@ def test_full_calibration_sampled_parity(ctx):
     compare(g, o, sel=sel)
 
 
-def test_lane_groups_do_not_change_multi_hypothesis_results(ctx):
-    """N = 6 with 8 lanes per seed (four seeds per warp) and with a whole warp
-    per seed: the same candidates, arithmetic and order, so identical results."""
+@pytest.mark.parametrize("n_hyp,shapes", [(6, ((8, 3), (32, 3), (32, 4), (8, 4))),
+                                          (3, ((4, 3), (4, 4), (8, 3), (32, 4)))])
+def test_lane_groups_do_not_change_multi_hypothesis_results(ctx, n_hyp, shapes):
+    """N hypotheses with 4 or 8 lanes per seed (lists sized to N or to the
+    group), and with a whole warp per seed: the same candidates, arithmetic
+    and order, so identical results."""
     from paper_2003_03174_b300 import trd
     tf = make_workload("calibration", seed=9, n_seeds=4000)
+    params = dict(tf.params, n_hyp=n_hyp)
     s, t = trd.to_device(tf.seeds), trd.to_device(tf.tracklets)
     idx = ctx.index_build(t)
     outs = []
-    for lanes, mb in ((8, 3), (32, 3), (32, 4), (8, 4)):
-        outs.append(to_numpy(ctx.follow(s, idx, tf.params, lanes_per_track=lanes, min_blocks_per_sm=mb)))
+    for lanes, mb in shapes:
+        outs.append(to_numpy(ctx.follow(s, idx, params, lanes_per_track=lanes, min_blocks_per_sm=mb)))
     torch.cuda.synchronize()
     for o in outs[1:]:
         for k in outs[0]:
