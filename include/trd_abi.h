@@ -178,7 +178,7 @@ TRD_API int trd_index_copy_out(const trd_index_t *index, int32_t *offsets, int32
  *            the tracklets carry none)}, in bucket order; the first
  *            offsets[n_buckets] records are written
  *   stats    4 uint32: largest vyy and vzz (float bits), rejected count, 0
- * Its scratch is a fixed device array inside the library (about 13.5 MB on
+ * Its scratch is a fixed device array inside the library (about 9.3 MB on
  * every GPU that loads it, kept until exit), so it accepts at most 1,048,576
  * tracklets and y bins of at least 1 cm (w = 0 selects 2 cm); anything larger
  * returns TRD_EINVAL.  All calls on a device share that scratch: calls that

@@ -34,7 +34,6 @@ void free_index_buffers(trd_index *x)
     cudaFree(x->recx);
     cudaFree(x->stats);
     cudaFree(x->bucket);
-    cudaFree(x->rank);
     cudaFree(x->counts);
     cudaFree(x->partials);
     cudaFree(x->toff);
@@ -82,7 +81,6 @@ int index_alloc(trd_ctx *ctx, int32_t capacity, float y_bin_width, int32_t n_tf,
               cudaMalloc(&x->recx, sizeof(float) * cap) == cudaSuccess &&
               cudaMalloc(&x->stats, sizeof(uint32_t) * 4) == cudaSuccess &&
               cudaMalloc(&x->bucket, sizeof(int32_t) * cap) == cudaSuccess &&
-              cudaMalloc(&x->rank, sizeof(int32_t) * cap) == cudaSuccess &&
               cudaMalloc(&x->counts, sizeof(int32_t) * x->n_buckets) == cudaSuccess &&
               cudaMalloc(&x->partials, sizeof(int32_t) * (x->n_partials + 1)) == cudaSuccess &&
               (n_tf == 1 || cudaMalloc(&x->toff, sizeof(int32_t) * (n_tf + 1)) == cudaSuccess) &&

@@ -2,11 +2,16 @@
 // based on the covariance matrices of the tracks are considered").
 //
 // Tracklets are bucketed by (chamber, y bin, pad row) with a counting sort:
-//   1. count: bucket of each tracklet; atomicAdd on the bucket's counter
-//      returns the tracklet's rank inside its bucket (no second atomic pass);
-//      block-reduced maxima of vyy and vzz bound the road width.
-//   2. exclusive scan of the bucket counters (reduce / scan partials / apply).
-//   3. scatter: a 32-byte record at offsets[bucket] + rank.
+//   1. count: bucket of each tracklet; a fire-and-forget atomic add on the
+//      bucket's counter (nothing waits for its return); block-reduced maxima
+//      of vyy and vzz bound the road width.
+//   2. exclusive scan of the bucket counters (reduce / scan partials / apply),
+//      written one slot late: offsets[b + 1] = first position of bucket b,
+//      offsets[0] = 0.
+//   3. scatter: atomicAdd on offsets[bucket + 1] returns the tracklet's
+//      position, where its 32-byte record goes; when every tracklet is placed,
+//      offsets[b + 1] holds the end of bucket b, i.e. the start of bucket
+//      b + 1, so offsets[b] is the first position of bucket b for every b.
 // The pad rows of one (chamber, y bin) are adjacent, so the follower reads
 // one contiguous range per y bin.  Order inside a bucket is not defined;
 // the follower's selection does not depend on it (ties break on tracklet id).
@@ -31,7 +36,7 @@ __global__ void __launch_bounds__(kCountThreads)
 k_index_count(const int32_t *__restrict__ ch, const float *__restrict__ y, const float *__restrict__ z,
               const float *__restrict__ dy, const float *__restrict__ vyy, const float *__restrict__ vzz,
               const float *__restrict__ vyz, int n, float inv_w, int nb, int32_t *__restrict__ bucket,
-              int32_t *__restrict__ rank, int32_t *__restrict__ counts, uint32_t *__restrict__ stats,
+              int32_t *__restrict__ counts, uint32_t *__restrict__ stats,
               const int32_t *__restrict__ toff, int n_tf, const float *__restrict__ xs)
 {
     float myy = 0.0f, mzz = 0.0f, mdx = 0.0f;
@@ -63,7 +68,6 @@ k_index_count(const int32_t *__restrict__ ch, const float *__restrict__ y, const
                             a[u] >= 0.0f && b[u] >= 0.0f && isfinite(xt);
             if (!ok) {
                 bucket[i] = -1;
-                rank[i] = 0;
                 ++rejected;
                 continue;
             }
@@ -71,7 +75,7 @@ k_index_count(const int32_t *__restrict__ ch, const float *__restrict__ y, const
             const int yb = trd::ybin_of(yy[u], inv_w, nb);
             const int bk = trd::bucket_of(trd::tf_of(i, toff, n_tf) * trd::kChambers + c[u], yb, row, nb);
             bucket[i] = bk;
-            rank[i] = atomicAdd(&counts[bk], 1);
+            atomicAdd(&counts[bk], 1);  // return value unused: a reduction, no round trip
             myy = fmaxf(myy, a[u]);
             mzz = fmaxf(mzz, b[u]);
             if (xs) {
@@ -177,6 +181,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_partials(int32_t *partial
     if (threadIdx.x == 0) partials[m] = carry;
 }
 
+// out[b + 1] = exclusive prefix of the counters at b (the scatter's cursor for
+// bucket b), out[0] = 0.
 __global__ void __launch_bounds__(kScanThreads)
 k_scan_apply(const int32_t *__restrict__ in, int n, const int32_t *__restrict__ partials, int32_t *__restrict__ out)
 {
@@ -193,35 +199,34 @@ k_scan_apply(const int32_t *__restrict__ in, int n, const int32_t *__restrict__ 
     int run = partials[blockIdx.x] + block_exclusive_scan(s, s_w, &total);
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-        if (base + k < n) out[base + k] = run;
+        if (base + k < n) out[base + k + 1] = run;
         run += v[k];
     }
-    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = partials[gridDim.x];
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[0] = 0;
 }
 
 __global__ void __launch_bounds__(kCountThreads)
 k_index_scatter(const float *__restrict__ y, const float *__restrict__ z, const float *__restrict__ dy,
                 const float *__restrict__ vyy, const float *__restrict__ vzz, const float *__restrict__ vyz,
-                int n, const int32_t *__restrict__ bucket, const int32_t *__restrict__ rank,
-                const int32_t *__restrict__ offsets, float4 *__restrict__ rec, const int32_t *__restrict__ toff,
+                int n, const int32_t *__restrict__ bucket, int32_t *__restrict__ offsets,
+                float4 *__restrict__ rec, const int32_t *__restrict__ toff,
                 int n_tf, const int32_t *__restrict__ trig, const float *__restrict__ xs, float *__restrict__ recx)
 {
     const int stride = gridDim.x * blockDim.x;
     for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += stride * kIlp) {
-        int bk[kIlp], rk[kIlp], base[kIlp];
+        int bk[kIlp], at[kIlp];
 #pragma unroll
         for (int u = 0; u < kIlp; ++u) {
             const int i = i0 + u * stride;
             bk[u] = i < n ? __ldg(&bucket[i]) : -1;
-            rk[u] = i < n ? __ldg(&rank[i]) : 0;
         }
 #pragma unroll
-        for (int u = 0; u < kIlp; ++u) base[u] = bk[u] >= 0 ? __ldg(&offsets[bk[u]]) : 0;
+        for (int u = 0; u < kIlp; ++u) at[u] = bk[u] >= 0 ? atomicAdd(&offsets[bk[u] + 1], 1) : 0;
 #pragma unroll
         for (int u = 0; u < kIlp; ++u) {
             const int i = i0 + u * stride;
             if (bk[u] < 0) continue;
-            const int pos = base[u] + rk[u];
+            const int pos = at[u];
             // ids are local to the tracklet's timeframe
             const int local = toff ? i - __ldg(&toff[trd::tf_of(i, toff, n_tf)]) : i;
             rec[2 * pos] = make_float4(__ldg(&y[i]), __ldg(&z[i]), __ldg(&dy[i]), __int_as_float(local));
@@ -247,7 +252,7 @@ int index_rebuild_launch(trd_index *idx, const trd_tracklets_t *t, cudaStream_t 
         n > 0 ? std::min((n + kCountThreads * kIlp - 1) / (kCountThreads * kIlp), idx->ctx->sm_count * 8) : 0;
     if (n > 0) {
         k_index_count<<<grid_n, kCountThreads, 0, s>>>(t->chamber, t->y, t->z, t->dy, t->vyy, t->vzz, t->vyz, n,
-                                                       idx->inv_w, idx->nb, idx->bucket, idx->rank, idx->counts,
+                                                       idx->inv_w, idx->nb, idx->bucket, idx->counts,
                                                        idx->stats, idx->toff, idx->n_tf, t->x);
         TRD_CUDA_TRY(cudaGetLastError());
     }
@@ -260,7 +265,7 @@ int index_rebuild_launch(trd_index *idx, const trd_tracklets_t *t, cudaStream_t 
     TRD_CUDA_TRY(cudaGetLastError());
     if (n > 0) {
         k_index_scatter<<<grid_n, kCountThreads, 0, s>>>(t->y, t->z, t->dy, t->vyy, t->vzz, t->vyz, n, idx->bucket,
-                                                         idx->rank, idx->offsets, idx->rec, idx->toff, idx->n_tf,
+                                                         idx->offsets, idx->rec, idx->toff, idx->n_tf,
                                                          t->trigger, t->x, idx->recx);
         TRD_CUDA_TRY(cudaGetLastError());
     }
@@ -274,11 +279,11 @@ int index_rebuild_launch(trd_index *idx, const trd_tracklets_t *t, cudaStream_t 
 // Some callers cannot allocate device memory at the point where they build an
 // index: code running inside a framework that owns every device allocation
 // through its own pool, or a real-time loop that must not call cudaMalloc
-// because it may synchronise the device.  For them the build's scratch (bucket
-// and rank of every tracklet, one counter per bucket, scan partials) lives in
+// because it may synchronise the device.  For them the build's scratch (the
+// bucket of every tracklet, one counter per bucket, scan partials) lives in
 // the file-scope array below, sized for kNoAllocMaxTracklets tracklets and
 // y bins of at least kNoAllocMinBinWidth cm.  Every GPU that loads the library
-// holds it (about 13.5 MB) until the process exits, and all calls on a device
+// holds it (about 9.3 MB) until the process exits, and all calls on a device
 // share it.
 namespace {
 
@@ -288,7 +293,7 @@ constexpr int kNoAllocMaxBins = 132;  // ceil(2 * 66 cm / 1 cm)
 constexpr int kNoAllocMaxBuckets = trd::kChambers * trd::kRowsPerStack * kNoAllocMaxBins;
 constexpr int kNoAllocMaxPartials = (kNoAllocMaxBuckets + kScanTile - 1) / kScanTile + 1;
 constexpr size_t kNoAllocWords =
-    2 * static_cast<size_t>(kNoAllocMaxTracklets) + kNoAllocMaxBuckets + kNoAllocMaxPartials;
+    static_cast<size_t>(kNoAllocMaxTracklets) + kNoAllocMaxBuckets + kNoAllocMaxPartials;
 
 static __device__ __align__(256) int32_t g_noalloc_scratch[kNoAllocWords];
 
@@ -350,8 +355,7 @@ extern "C" int trd_index_build_noalloc(const trd_tracklets_t *t, float y_bin_wid
     const int n_buckets = trd::kChambers * trd::kRowsPerStack * nb;
     const int m = (n_buckets + kScanTile - 1) / kScanTile;
     int32_t *bucket = d.scratch;
-    int32_t *rank = bucket + kNoAllocMaxTracklets;
-    int32_t *counts = rank + kNoAllocMaxTracklets;
+    int32_t *counts = bucket + kNoAllocMaxTracklets;
     int32_t *partials = counts + kNoAllocMaxBuckets;
     float4 *rec = reinterpret_cast<float4 *>(records);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -363,7 +367,7 @@ extern "C" int trd_index_build_noalloc(const trd_tracklets_t *t, float y_bin_wid
     const int grid_n = n > 0 ? std::min((n + kCountThreads * kIlp - 1) / (kCountThreads * kIlp), d.sm_count * 8) : 0;
     if (n > 0) {
         k_index_count<<<grid_n, kCountThreads, 0, s>>>(t->chamber, t->y, t->z, t->dy, t->vyy, t->vzz, t->vyz, n,
-                                                       inv_w, nb, bucket, rank, counts, stats, nullptr, 1, nullptr);
+                                                       inv_w, nb, bucket, counts, stats, nullptr, 1, nullptr);
         TRD_CUDA_TRY(cudaGetLastError());
     }
     k_scan_reduce<<<m, kScanThreads, 0, s>>>(counts, n_buckets, partials);
@@ -373,7 +377,7 @@ extern "C" int trd_index_build_noalloc(const trd_tracklets_t *t, float y_bin_wid
     k_scan_apply<<<m, kScanThreads, 0, s>>>(counts, n_buckets, partials, offsets);
     TRD_CUDA_TRY(cudaGetLastError());
     if (n > 0) {
-        k_index_scatter<<<grid_n, kCountThreads, 0, s>>>(t->y, t->z, t->dy, t->vyy, t->vzz, t->vyz, n, bucket, rank,
+        k_index_scatter<<<grid_n, kCountThreads, 0, s>>>(t->y, t->z, t->dy, t->vyy, t->vzz, t->vyz, n, bucket,
                                                          offsets, rec, nullptr, 1, t->trigger, nullptr, nullptr);
         TRD_CUDA_TRY(cudaGetLastError());
     }

@@ -76,7 +76,7 @@ size_t index_bytes(int n_trk, float w)
 {
     const size_t nb = static_cast<size_t>(ceilf(2.0f * 66.0f / w));
     const size_t buckets = static_cast<size_t>(TRD_N_CHAMBERS) * 18 * nb;
-    return 44 * static_cast<size_t>(n_trk) + 8 * buckets + 4096;  // records, radii, bucket, rank
+    return 40 * static_cast<size_t>(n_trk) + 8 * buckets + 4096;  // records, radii, bucket
 }
 
 void CUDART_CB on_done(void *p)

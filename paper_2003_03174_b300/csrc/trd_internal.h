@@ -38,7 +38,6 @@ struct trd_index {
     int has_x;          // the last build's tracklets carried radii
     // build scratch
     int32_t *bucket;    // [capacity] bucket of each input tracklet (-1: rejected)
-    int32_t *rank;      // [capacity] position inside its bucket
     int32_t *counts;    // [n_buckets]
     int32_t *partials;  // [scan blocks + 1]
     int32_t n_partials;

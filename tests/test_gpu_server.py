@@ -69,7 +69,7 @@ def test_budget_admits_one_request_at_a_time(ctx, tfs):
     # leave room for the index and one and a half requests, never for two
     # (with the follower's scratch: 136 B per seed + 512 B)
     io = 220 * big.n_seeds + 36 * big.n_tracklets + 7 * 256 + 136 * big.n_seeds + 512 + 256
-    index = 44 * big.n_tracklets + 8 * 540 * 18 * 66 + 4096
+    index = 40 * big.n_tracklets + 8 * 540 * 18 * 66 + 4096
     one = index + io + io // 2
     srv = trd.Server(ctx, big.params, max_slots=4, mem_budget_bytes=one)
     outs = [trd.host_results(big.n_seeds) for _ in range(3)]
