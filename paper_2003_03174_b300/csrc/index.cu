@@ -214,25 +214,34 @@ k_index_scatter(const float *__restrict__ y, const float *__restrict__ z, const 
 {
     const int stride = gridDim.x * blockDim.x;
     for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += stride * kIlp) {
+        // the records' contents are loaded before the position atomics, so
+        // the two latencies overlap
         int bk[kIlp], at[kIlp];
+        float4 ra[kIlp], rb[kIlp];
+        float rx[kIlp];
 #pragma unroll
         for (int u = 0; u < kIlp; ++u) {
             const int i = i0 + u * stride;
             bk[u] = i < n ? __ldg(&bucket[i]) : -1;
+            const bool in = i < n;
+            // ids are local to the tracklet's timeframe
+            const int local = in && toff ? i - __ldg(&toff[trd::tf_of(i, toff, n_tf)]) : i;
+            ra[u] = in ? make_float4(__ldg(&y[i]), __ldg(&z[i]), __ldg(&dy[i]), __int_as_float(local))
+                       : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            rb[u] = in ? make_float4(__ldg(&vyy[i]), __ldg(&vzz[i]), __ldg(&vyz[i]),
+                                     __int_as_float(trig ? __ldg(&trig[i]) : -1))
+                       : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            rx[u] = in && xs ? __ldg(&xs[i]) : 0.0f;
         }
 #pragma unroll
         for (int u = 0; u < kIlp; ++u) at[u] = bk[u] >= 0 ? atomicAdd(&offsets[bk[u] + 1], 1) : 0;
 #pragma unroll
         for (int u = 0; u < kIlp; ++u) {
-            const int i = i0 + u * stride;
             if (bk[u] < 0) continue;
             const int pos = at[u];
-            // ids are local to the tracklet's timeframe
-            const int local = toff ? i - __ldg(&toff[trd::tf_of(i, toff, n_tf)]) : i;
-            rec[2 * pos] = make_float4(__ldg(&y[i]), __ldg(&z[i]), __ldg(&dy[i]), __int_as_float(local));
-            rec[2 * pos + 1] = make_float4(__ldg(&vyy[i]), __ldg(&vzz[i]), __ldg(&vyz[i]),
-                                           __int_as_float(trig ? __ldg(&trig[i]) : -1));
-            if (xs) recx[pos] = __ldg(&xs[i]);
+            rec[2 * pos] = ra[u];
+            rec[2 * pos + 1] = rb[u];
+            if (xs) recx[pos] = rx[u];
         }
     }
 }
