@@ -85,6 +85,14 @@ int trd_batch_create(trd_ctx_t *ctx, int32_t n_tf, const int32_t *seed_offsets, 
         release(b);
         return TRD_ECUDA;
     }
+    // the index's bucket counters zeroed before the capture, so that the
+    // captured build does not repeat that memset on every replay
+    if (cudaMemset(b->index->counts, 0, sizeof(int32_t) * b->index->n_buckets) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess) {
+        release(b);
+        return TRD_ECUDA;
+    }
+    b->index->counts_zero = true;
     // validate the follower's arguments once, with the plain entry point's rules
     trd_seeds_t none = *seeds;
     none.n = 0;
@@ -117,7 +125,7 @@ int trd_batch_create(trd_ctx_t *ctx, int32_t n_tf, const int32_t *seed_offsets, 
     bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     if (ok) {
         ok = cudaEventRecord(fork, cs) == cudaSuccess && cudaStreamWaitEvent(cs2, fork, 0) == cudaSuccess;
-        if (ok) rc = trd_host::prepare_launch(seeds, params, results, cs2, b->parked);
+        if (ok) rc = trd_host::prepare_launch(seeds, params, results, cs2, b->parked, b->counter);
         if (ok && !rc) ok = cudaEventRecord(join, cs2) == cudaSuccess;
         if (ok && !rc) rc = trd_host::index_rebuild_launch(b->index, tracklets, cs);
         if (ok && !rc) ok = cudaStreamWaitEvent(cs, join, 0) == cudaSuccess;

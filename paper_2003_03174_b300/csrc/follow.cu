@@ -605,9 +605,12 @@ __host__ __device__ inline ParkedView parked_view(void *base, int n)
 
 // Bin of every seed and its rank inside the bin: lanes of a warp with the
 // same bin share one shared-memory atomic, and each block takes its base in
-// every occupied bin with one global atomic.
-__global__ void __launch_bounds__(kKeyThreads) k_seed_key(const float *__restrict__ q2pt, int n, ParkedView pk)
+// every occupied bin with one global atomic.  Also zeroes the follower's work
+// counter (the follower starts after this kernel).
+__global__ void __launch_bounds__(kKeyThreads)
+k_seed_key(const float *__restrict__ q2pt, int n, ParkedView pk, int *__restrict__ counter)
 {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *counter = 0;
     __shared__ int h[kSortBins], base[kSortBins];
     for (int t = threadIdx.x; t < kSortBins; t += kKeyThreads) h[t] = 0;
     __syncthreads();
@@ -977,11 +980,11 @@ using namespace trd;
 // The seeds' pre-pass: bins and ranks, then the rotated states parked in
 // sorted order.
 static int prepare_kernels(const SeedsView &sv, const Params &P, const ResultsView &o, const ParkedView &pk,
-                           cudaStream_t s)
+                           int *counter, cudaStream_t s)
 {
     TRD_CUDA_TRY(cudaMemsetAsync(pk.bin_count, 0, sizeof(int32_t) * kSortBins, s));
     const int per_block = kKeyThreads * kKeyItems;
-    k_seed_key<<<(sv.n + per_block - 1) / per_block, kKeyThreads, 0, s>>>(sv.q2pt, sv.n, pk);
+    k_seed_key<<<(sv.n + per_block - 1) / per_block, kKeyThreads, 0, s>>>(sv.q2pt, sv.n, pk, counter);
     TRD_CUDA_TRY(cudaGetLastError());
     k_seed_prepare<<<(sv.n + 255) / 256, 256, 0, s>>>(sv, P, o, pk);
     TRD_CUDA_TRY(cudaGetLastError());
@@ -1000,9 +1003,10 @@ static int launch(const trd_ctx *ctx, const SeedsView &sv, const IndexView &ix, 
     per_sm = per_sm > 0 ? per_sm : 1;
     const long long need = (static_cast<long long>(sv.n) + groups - 1) / groups;
     const int grid = static_cast<int>(std::min<long long>(need, static_cast<long long>(ctx->sm_count) * per_sm));
-    TRD_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), s));
+    // the work counter is zeroed by the pre-pass (here, or on the caller's
+    // branch when prepare is false)
     if (prepare) {
-        const int rc = prepare_kernels(sv, P, o, pk, s);
+        const int rc = prepare_kernels(sv, P, o, pk, counter, s);
         if (rc) return rc;
     }
     k_follow<G, NH, MINB, EXT><<<grid, block, smem, s>>>(sv, ix, P, pk, counter);
@@ -1060,18 +1064,19 @@ static Params make_params(const trd_params_t *p, const trd_alignment_t *align)
 size_t parked_bytes(int32_t n) { return n > 0 ? sizeof(int32_t) * parked_words(n) : 0; }
 
 // The seeds' pre-pass alone (it does not read the index, so a captured step
-// can run it beside the index build).  parked: parked_bytes(n) of device memory.
+// can run it beside the index build).  parked: parked_bytes(n) of device
+// memory; counter: the work counter of the follower launch that follows.
 int prepare_launch(const trd_seeds_t *seeds, const trd_params_t *p, trd_results_t *out, cudaStream_t s,
-                   void *parked, const trd_alignment_t *align)
+                   void *parked, int *counter, const trd_alignment_t *align)
 {
     if (seeds->n == 0) return TRD_OK;
-    if (!parked) return TRD_EINVAL;
+    if (!parked || !counter) return TRD_EINVAL;
     SeedsView sv{seeds->alpha, seeds->x, seeds->y, seeds->z, seeds->snp, seeds->tgl, seeds->q2pt, seeds->cov,
                  seeds->n, nullptr, 1, seeds->trigger};
     const Params P = make_params(p, align);
     ResultsView o{out->alpha, out->x, out->par, out->cov, out->chi2, out->n_trk, out->n_miss, out->status,
                   out->tracklet_id};
-    return prepare_kernels(sv, P, o, parked_view(parked, seeds->n), s);
+    return prepare_kernels(sv, P, o, parked_view(parked, seeds->n), counter, s);
 }
 
 int follow_launch(const trd_ctx *ctx, const trd_seeds_t *seeds, const IndexView &iv, const trd_params_t *p,

@@ -182,9 +182,10 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_partials(int32_t *partial
 }
 
 // out[b + 1] = exclusive prefix of the counters at b (the scatter's cursor for
-// bucket b), out[0] = 0.
+// bucket b), out[0] = 0.  The counters are zeroed after they are read, so
+// every build leaves them ready for the next one (they start zeroed).
 __global__ void __launch_bounds__(kScanThreads)
-k_scan_apply(const int32_t *__restrict__ in, int n, const int32_t *__restrict__ partials, int32_t *__restrict__ out)
+k_scan_apply(int32_t *__restrict__ in, int n, const int32_t *__restrict__ partials, int32_t *__restrict__ out)
 {
     __shared__ int s_w[kScanThreads / 32];
     const int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
@@ -195,6 +196,9 @@ k_scan_apply(const int32_t *__restrict__ in, int n, const int32_t *__restrict__ 
         v[k] = base + k < n ? in[base + k] : 0;
         s += v[k];
     }
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+        if (base + k < n) in[base + k] = 0;
     int total;
     int run = partials[blockIdx.x] + block_exclusive_scan(s, s_w, &total);
 #pragma unroll
@@ -255,7 +259,12 @@ int scan_blocks_for(int n) { return (n + kScanTile - 1) / kScanTile; }
 int index_rebuild_launch(trd_index *idx, const trd_tracklets_t *t, cudaStream_t s)
 {
     const int n = t->n;
-    TRD_CUDA_TRY(cudaMemsetAsync(idx->counts, 0, sizeof(int32_t) * idx->n_buckets, s));
+    // the bucket counters are zero between builds: zeroed once here, then by
+    // every build's scan after it has read them
+    if (!idx->counts_zero) {
+        TRD_CUDA_TRY(cudaMemsetAsync(idx->counts, 0, sizeof(int32_t) * idx->n_buckets, s));
+        idx->counts_zero = true;
+    }
     TRD_CUDA_TRY(cudaMemsetAsync(idx->stats, 0, sizeof(uint32_t) * 4, s));
     const int grid_n =
         n > 0 ? std::min((n + kCountThreads * kIlp - 1) / (kCountThreads * kIlp), idx->ctx->sm_count * 8) : 0;
@@ -371,7 +380,8 @@ extern "C" int trd_index_build_noalloc(const trd_tracklets_t *t, float y_bin_wid
 
     // the counters and the caller's stats must start at zero; the rest of the
     // scratch is fully written before it is read
-    TRD_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(int32_t) * n_buckets, s));
+    // the counters are zero here: the static array starts zeroed and every
+    // build's scan zeroes the ones it used
     TRD_CUDA_TRY(cudaMemsetAsync(stats, 0, sizeof(uint32_t) * 4, s));
     const int grid_n = n > 0 ? std::min((n + kCountThreads * kIlp - 1) / (kCountThreads * kIlp), d.sm_count * 8) : 0;
     if (n > 0) {

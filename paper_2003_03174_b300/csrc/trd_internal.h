@@ -38,7 +38,8 @@ struct trd_index {
     int has_x;          // the last build's tracklets carried radii
     // build scratch
     int32_t *bucket;    // [capacity] bucket of each input tracklet (-1: rejected)
-    int32_t *counts;    // [n_buckets]
+    int32_t *counts;    // [n_buckets], zero between builds (each build's scan re-zeroes them)
+    bool counts_zero;   // zeroed once (at the first build, or by the batch before capture)
     int32_t *partials;  // [scan blocks + 1]
     int32_t n_partials;
     cudaStream_t stream;  // stream of the last build
@@ -65,7 +66,7 @@ int follow_launch(const trd_ctx *ctx, const trd_seeds_t *seeds, const IndexView 
 // Device scratch of the seeds' pre-pass for n seeds (sorted, rotated states).
 size_t parked_bytes(int32_t n);
 int prepare_launch(const trd_seeds_t *seeds, const trd_params_t *p, trd_results_t *out, cudaStream_t s,
-                   void *parked, const trd_alignment_t *align = nullptr);
+                   void *parked, int *counter, const trd_alignment_t *align = nullptr);
 int follow_checked(trd_ctx *ctx, const trd_seeds_t *seeds, const trd_index *index, const trd_params_t *p,
                    const trd_alignment_t *align, trd_results_t *out, void *stream, const trd_launch_t *launch,
                    void *parked);
