@@ -433,9 +433,9 @@ def run_ours(args):
            "unit": "TFLOP/s", "peak_source": "measured by trd_measure_fp32_peak (FMA chains)"}
     alu["frac"] = alu["achieved"] / fp32_peak
     roof["alu_check"] = alu
-    # index: count, 3 scan kernels, scatter; follower: seed key, seed prepare,
+    # index: count, 2 scan kernels, scatter; follower: seed key, seed prepare,
     # follow, results gather (one graph)
-    launches_per_step = 9
+    launches_per_step = 8
     clocks = clk.summary()
     refit = time_refit(ctx, res, trk, tf.params, stream, flush, args.steps, args.warmup, hbm, fp32_peak)
 
@@ -599,7 +599,7 @@ def run_batched(args):
                   "path": f"{len(tfs)} x (trd_index_rebuild + trd_follow) on one stream"},
         "speedup_batched_vs_plain": t_plain / t_batch,
         "results_identical": bool(same),
-        "gpu_launches_per_step": {"batched": 9, "plain": 9 * len(tfs)},
+        "gpu_launches_per_step": {"batched": 8, "plain": 8 * len(tfs)},
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)

@@ -5,7 +5,7 @@
 //   1. count: bucket of each tracklet; a fire-and-forget atomic add on the
 //      bucket's counter (nothing waits for its return); block-reduced maxima
 //      of vyy and vzz bound the road width.
-//   2. exclusive scan of the bucket counters (reduce / scan partials / apply),
+//   2. exclusive scan of the bucket counters (tile sums, then apply),
 //      written one slot late: offsets[b + 1] = first position of bucket b,
 //      offsets[0] = 0.
 //   3. scatter: atomicAdd on offsets[bucket + 1] returns the tracklet's
@@ -165,29 +165,22 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int32_t *__r
     }
 }
 
-// Single block: exclusive scan of the partial sums in place; partials[m] = total.
-__global__ void __launch_bounds__(kScanThreads) k_scan_partials(int32_t *partials, int m)
-{
-    __shared__ int s_w[kScanThreads / 32];
-    int carry = 0;
-    for (int base = 0; base < m; base += kScanThreads) {
-        const int i = base + threadIdx.x;
-        const int v = i < m ? partials[i] : 0;
-        int total;
-        const int ex = block_exclusive_scan(v, s_w, &total);
-        if (i < m) partials[i] = carry + ex;
-        carry += total;
-    }
-    if (threadIdx.x == 0) partials[m] = carry;
-}
-
 // out[b + 1] = exclusive prefix of the counters at b (the scatter's cursor for
-// bucket b), out[0] = 0.  The counters are zeroed after they are read, so
-// every build leaves them ready for the next one (they start zeroed).
+// bucket b), out[0] = 0.  A block's base is the sum of the partial sums of the
+// tiles before it (a few hundred at most; one warp adds them), so no separate
+// scan of the partials is launched.  The counters are zeroed after they are
+// read, so every build leaves them ready for the next one (they start zeroed).
 __global__ void __launch_bounds__(kScanThreads)
 k_scan_apply(int32_t *__restrict__ in, int n, const int32_t *__restrict__ partials, int32_t *__restrict__ out)
 {
     __shared__ int s_w[kScanThreads / 32];
+    __shared__ int s_base;
+    if (threadIdx.x < 32) {
+        int b = 0;
+        for (int j = threadIdx.x; j < static_cast<int>(blockIdx.x); j += 32) b += partials[j];
+        for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
+        if (threadIdx.x == 0) s_base = b;
+    }
     const int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
     int v[kScanItems];
     int s = 0;
@@ -200,7 +193,8 @@ k_scan_apply(int32_t *__restrict__ in, int n, const int32_t *__restrict__ partia
     for (int k = 0; k < kScanItems; ++k)
         if (base + k < n) in[base + k] = 0;
     int total;
-    int run = partials[blockIdx.x] + block_exclusive_scan(s, s_w, &total);
+    const int ex = block_exclusive_scan(s, s_w, &total);  // its barriers also publish s_base
+    int run = s_base + ex;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
         if (base + k < n) out[base + k + 1] = run;
@@ -276,8 +270,6 @@ int index_rebuild_launch(trd_index *idx, const trd_tracklets_t *t, cudaStream_t 
     }
     const int m = scan_blocks_for(idx->n_buckets);
     k_scan_reduce<<<m, kScanThreads, 0, s>>>(idx->counts, idx->n_buckets, idx->partials);
-    TRD_CUDA_TRY(cudaGetLastError());
-    k_scan_partials<<<1, kScanThreads, 0, s>>>(idx->partials, m);
     TRD_CUDA_TRY(cudaGetLastError());
     k_scan_apply<<<m, kScanThreads, 0, s>>>(idx->counts, idx->n_buckets, idx->partials, idx->offsets);
     TRD_CUDA_TRY(cudaGetLastError());
@@ -390,8 +382,6 @@ extern "C" int trd_index_build_noalloc(const trd_tracklets_t *t, float y_bin_wid
         TRD_CUDA_TRY(cudaGetLastError());
     }
     k_scan_reduce<<<m, kScanThreads, 0, s>>>(counts, n_buckets, partials);
-    TRD_CUDA_TRY(cudaGetLastError());
-    k_scan_partials<<<1, kScanThreads, 0, s>>>(partials, m);
     TRD_CUDA_TRY(cudaGetLastError());
     k_scan_apply<<<m, kScanThreads, 0, s>>>(counts, n_buckets, partials, offsets);
     TRD_CUDA_TRY(cudaGetLastError());
