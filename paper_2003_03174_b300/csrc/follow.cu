@@ -645,6 +645,7 @@ k_seed_key(const float *__restrict__ q2pt, int n, ParkedView pk, int *__restrict
 // parked at its sorted position.
 __global__ void __launch_bounds__(256) k_seed_prepare(SeedsView sv, Params P, ResultsView o, ParkedView pk)
 {
+    wait_prior_grid();
     // first sorted position of every bin: exclusive scan of the bin counts
     static_assert(kSortBins == 4 * 32, "one warp scans four bins per lane");
     __shared__ int s_off[kSortBins];
@@ -911,6 +912,7 @@ template <int G, int NH, int MINB, bool EXT>
 __global__ void __launch_bounds__(128, MINB)
 k_follow(SeedsView sv, IndexView ix, Params P, ParkedView pk, int *counter)
 {
+    wait_prior_grid();
     extern __shared__ float smem[];
     const int groups = blockDim.x / G;
     const int g = threadIdx.x / G;
@@ -943,6 +945,7 @@ k_follow(SeedsView sv, IndexView ix, Params P, ParkedView pk, int *counter)
 // that ended in k_seed_prepare (inv -1) already have their results.
 __global__ void __launch_bounds__(256) k_results_gather(int n, ParkedView pk, ResultsView o)
 {
+    wait_prior_grid();
     __shared__ float s_res[256 / 32][32][33];  // each warp's 32 records (odd row: no bank conflicts)
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -986,8 +989,7 @@ static int prepare_kernels(const SeedsView &sv, const Params &P, const ResultsVi
     const int per_block = kKeyThreads * kKeyItems;
     k_seed_key<<<(sv.n + per_block - 1) / per_block, kKeyThreads, 0, s>>>(sv.q2pt, sv.n, pk, counter);
     TRD_CUDA_TRY(cudaGetLastError());
-    k_seed_prepare<<<(sv.n + 255) / 256, 256, 0, s>>>(sv, P, o, pk);
-    TRD_CUDA_TRY(cudaGetLastError());
+    TRD_CUDA_TRY(launch_after(k_seed_prepare, dim3((sv.n + 255) / 256), dim3(256), 0, s, sv, P, o, pk));
     return TRD_OK;
 }
 
@@ -1009,10 +1011,9 @@ static int launch(const trd_ctx *ctx, const SeedsView &sv, const IndexView &ix, 
         const int rc = prepare_kernels(sv, P, o, pk, counter, s);
         if (rc) return rc;
     }
-    k_follow<G, NH, MINB, EXT><<<grid, block, smem, s>>>(sv, ix, P, pk, counter);
-    TRD_CUDA_TRY(cudaGetLastError());
-    k_results_gather<<<(sv.n + 255) / 256, 256, 0, s>>>(sv.n, pk, o);
-    TRD_CUDA_TRY(cudaGetLastError());
+    // the follower and the gather start while their predecessor drains
+    TRD_CUDA_TRY(launch_after(k_follow<G, NH, MINB, EXT>, dim3(grid), dim3(block), smem, s, sv, ix, P, pk, counter));
+    TRD_CUDA_TRY(launch_after(k_results_gather, dim3((sv.n + 255) / 256), dim3(256), 0, s, sv.n, pk, o));
     return TRD_OK;
 }
 

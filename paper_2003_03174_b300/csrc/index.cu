@@ -147,6 +147,7 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *s_warp, int *tot
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int32_t *__restrict__ in, int n, int32_t *__restrict__ partials)
 {
+    trd::wait_prior_grid();
     const int base = blockIdx.x * kScanTile;
     int s = 0;
 #pragma unroll
@@ -173,6 +174,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int32_t *__r
 __global__ void __launch_bounds__(kScanThreads)
 k_scan_apply(int32_t *__restrict__ in, int n, const int32_t *__restrict__ partials, int32_t *__restrict__ out)
 {
+    trd::wait_prior_grid();
     __shared__ int s_w[kScanThreads / 32];
     __shared__ int s_base;
     if (threadIdx.x < 32) {
@@ -210,6 +212,7 @@ k_index_scatter(const float *__restrict__ y, const float *__restrict__ z, const 
                 float4 *__restrict__ rec, const int32_t *__restrict__ toff,
                 int n_tf, const int32_t *__restrict__ trig, const float *__restrict__ xs, float *__restrict__ recx)
 {
+    trd::wait_prior_grid();
     const int stride = gridDim.x * blockDim.x;
     for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += stride * kIlp) {
         // the records' contents are loaded before the position atomics, so
@@ -269,15 +272,15 @@ int index_rebuild_launch(trd_index *idx, const trd_tracklets_t *t, cudaStream_t 
         TRD_CUDA_TRY(cudaGetLastError());
     }
     const int m = scan_blocks_for(idx->n_buckets);
-    k_scan_reduce<<<m, kScanThreads, 0, s>>>(idx->counts, idx->n_buckets, idx->partials);
-    TRD_CUDA_TRY(cudaGetLastError());
-    k_scan_apply<<<m, kScanThreads, 0, s>>>(idx->counts, idx->n_buckets, idx->partials, idx->offsets);
-    TRD_CUDA_TRY(cudaGetLastError());
+    // the scan and the scatter start while their predecessor drains
+    TRD_CUDA_TRY(launch_after(k_scan_reduce, dim3(m), dim3(kScanThreads), 0, s, idx->counts, idx->n_buckets,
+                              idx->partials));
+    TRD_CUDA_TRY(launch_after(k_scan_apply, dim3(m), dim3(kScanThreads), 0, s, idx->counts, idx->n_buckets,
+                              idx->partials, idx->offsets));
     if (n > 0) {
-        k_index_scatter<<<grid_n, kCountThreads, 0, s>>>(t->y, t->z, t->dy, t->vyy, t->vzz, t->vyz, n, idx->bucket,
-                                                         idx->offsets, idx->rec, idx->toff, idx->n_tf,
-                                                         t->trigger, t->x, idx->recx);
-        TRD_CUDA_TRY(cudaGetLastError());
+        TRD_CUDA_TRY(launch_after(k_index_scatter, dim3(grid_n), dim3(kCountThreads), 0, s, t->y, t->z, t->dy,
+                                  t->vyy, t->vzz, t->vyz, n, idx->bucket, idx->offsets, idx->rec, idx->toff,
+                                  idx->n_tf, t->trigger, t->x, idx->recx));
     }
     idx->has_x = t->x != nullptr;
     return TRD_OK;

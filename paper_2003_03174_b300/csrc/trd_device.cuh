@@ -12,6 +12,15 @@
 
 namespace trd {
 
+// Programmatic dependent launch: a kernel launched after another in the same
+// stream with the programmatic-serialization attribute (trd_host::launch_after)
+// may have its blocks start while its predecessor is still running; it calls
+// wait_prior_grid() before touching any memory the predecessor reads or
+// writes, and that returns once the predecessor has completed and its writes
+// are visible.  In a kernel launched the ordinary way it returns at once.
+__device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+
 // ---- geometry (Sec. 3: 18 sectors x 5 stacks x 6 layers; radii, pad rows
 // and material are readings) ------------------------------------------------
 constexpr int kLayers = 6;

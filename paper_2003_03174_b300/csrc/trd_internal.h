@@ -76,6 +76,29 @@ void index_release(trd_index *x);
 int scan_blocks_for(int n);
 }  // namespace trd_host
 
+namespace trd_host {
+// Launch `kernel` after the previous kernel in stream s with programmatic
+// serialization: its blocks may be scheduled before that kernel has finished
+// (hiding the launch latency), and they wait in trd::wait_prior_grid(), which
+// every kernel launched this way calls first.
+template <typename... K, typename... A>
+inline cudaError_t launch_after(void (*kernel)(K...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                                A &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<A &&>(args)...);
+}
+}  // namespace trd_host
+
 #define TRD_CUDA_TRY(expr)                                   \
     do {                                                     \
         cudaError_t e_ = (expr);                             \
