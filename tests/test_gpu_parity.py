@@ -294,3 +294,24 @@ def test_one_momentum_bin(ctx, n):
     g, _ = run_gpu(ctx, tf, seeds=s)
     o = O.follow(s, tf.tracklets, tf.params)
     compare(g, o)
+
+
+def test_resident_index_rebuilds_stay_exact(ctx):
+    """A resident index rebuilt with different tracklet sets in turn (the
+    bucket counters return to zero after every build): each build's offsets
+    and bucket contents equal the counting-sort reference of its own set."""
+    from paper_2003_03174_b300 import trd
+    a = make_workload("timeframe", seed=12, n_seeds=30_000).tracklets
+    b = make_workload("timeframe", seed=13, n_seeds=20_000).tracklets
+    w = 2.0
+    idx = ctx.index_create(max(len(a["chamber"]), len(b["chamber"])), w)
+    for trk in (a, b, a, b):
+        idx.rebuild(trd.to_device(trk))
+        torch.cuda.synchronize()
+        off, ids = idx.copy_out()
+        bk, nb = _bucket_reference(trk, w)
+        counts = np.bincount(bk, minlength=540 * 18 * nb)
+        np.testing.assert_array_equal(off, np.concatenate([[0], np.cumsum(counts)]).astype(np.int32))
+        n = len(trk["chamber"])
+        assert np.array_equal(np.sort(ids[:n]), np.arange(n))
+        np.testing.assert_array_equal(bk[ids[:n]], np.repeat(np.arange(counts.shape[0]), counts))
