@@ -125,7 +125,9 @@ int trd_batch_create(trd_ctx_t *ctx, int32_t n_tf, const int32_t *seed_offsets, 
     bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     if (ok) {
         ok = cudaEventRecord(fork, cs) == cudaSuccess && cudaStreamWaitEvent(cs2, fork, 0) == cudaSuccess;
-        if (ok) rc = trd_host::prepare_launch(seeds, params, results, cs2, b->parked, b->counter);
+        if (ok)
+            rc = trd_host::prepare_launch(seeds, params, results, cs2, b->parked, b->counter,
+                                          n_tf > 1 ? b->soff : nullptr, n_tf);
         if (ok && !rc) ok = cudaEventRecord(join, cs2) == cudaSuccess;
         if (ok && !rc) rc = trd_host::index_rebuild_launch(b->index, tracklets, cs);
         if (ok && !rc) ok = cudaStreamWaitEvent(cs, join, 0) == cudaSuccess;

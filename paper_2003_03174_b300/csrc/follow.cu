@@ -564,10 +564,15 @@ constexpr int kKeyThreads = 256;
 constexpr int kKeyItems = 8;
 constexpr int kParkedWords = 25;  // words of a parked record
 
-__device__ __forceinline__ int sort_bin(float q2pt)
+// A batch of timeframes is taken timeframe by timeframe (each one's tracklet
+// records then stay in L2 while its seeds are followed), each in momentum
+// order at the resolution the 128 bins leave: bin = (timeframe * 128 +
+// momentum bin) / n_tf (two momentum bins per timeframe at 64 timeframes).
+__device__ __forceinline__ int sort_bin(float q2pt, int tf, int n_tf)
 {
     const float a = fabsf(q2pt) * kSortBinsPerUnit;  // NaN fails the test: first bin
-    return a < static_cast<float>(kSortBins - 1) ? kSortBins - 1 - static_cast<int>(a) : 0;
+    const int local = a < static_cast<float>(kSortBins - 1) ? kSortBins - 1 - static_cast<int>(a) : 0;
+    return n_tf == 1 ? local : (tf * kSortBins + local) / n_tf;
 }
 
 // Scratch of one follower call (device, n seeds; the base 16-byte aligned):
@@ -608,7 +613,8 @@ __host__ __device__ inline ParkedView parked_view(void *base, int n)
 // every occupied bin with one global atomic.  Also zeroes the follower's work
 // counter (the follower starts after this kernel).
 __global__ void __launch_bounds__(kKeyThreads)
-k_seed_key(const float *__restrict__ q2pt, int n, ParkedView pk, int *__restrict__ counter)
+k_seed_key(const float *__restrict__ q2pt, int n, const int32_t *__restrict__ soff, int n_tf, ParkedView pk,
+           int *__restrict__ counter)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0) *counter = 0;
     __shared__ int h[kSortBins], base[kSortBins];
@@ -620,7 +626,7 @@ k_seed_key(const float *__restrict__ q2pt, int n, ParkedView pk, int *__restrict
 #pragma unroll
     for (int u = 0; u < kKeyItems; ++u) {
         const int i = i0 + u * kKeyThreads;
-        b[u] = i < n ? sort_bin(__ldg(&q2pt[i])) : -1;
+        b[u] = i < n ? sort_bin(__ldg(&q2pt[i]), tf_of(i, soff, n_tf), n_tf) : -1;
         const unsigned peers = __match_any_sync(0xffffffffu, b[u]);
         const int leader = __ffs(peers) - 1;
         int first = 0;
@@ -680,7 +686,7 @@ __global__ void __launch_bounds__(256) k_seed_prepare(SeedsView sv, Params P, Re
     int state = 2, pos = -1;
     float *t = s_rec[threadIdx.x >> 5][threadIdx.x & 31];
     if (i < n) {
-        pos = s_off[sort_bin(sv.q2pt[i])] + pk.rank[i];
+        pos = s_off[sort_bin(sv.q2pt[i], tf_of(i, sv.soff, sv.n_tf), sv.n_tf)] + pk.rank[i];
         TrackState s;
         const float alpha = sv.alpha[i];
         const float sx = sv.x[i], sy = sv.y[i];
@@ -987,7 +993,8 @@ static int prepare_kernels(const SeedsView &sv, const Params &P, const ResultsVi
 {
     TRD_CUDA_TRY(cudaMemsetAsync(pk.bin_count, 0, sizeof(int32_t) * kSortBins, s));
     const int per_block = kKeyThreads * kKeyItems;
-    k_seed_key<<<(sv.n + per_block - 1) / per_block, kKeyThreads, 0, s>>>(sv.q2pt, sv.n, pk, counter);
+    k_seed_key<<<(sv.n + per_block - 1) / per_block, kKeyThreads, 0, s>>>(sv.q2pt, sv.n, sv.soff, sv.n_tf, pk,
+                                                                           counter);
     TRD_CUDA_TRY(cudaGetLastError());
     TRD_CUDA_TRY(launch_after(k_seed_prepare, dim3((sv.n + 255) / 256), dim3(256), 0, s, sv, P, o, pk));
     return TRD_OK;
@@ -1068,12 +1075,12 @@ size_t parked_bytes(int32_t n) { return n > 0 ? sizeof(int32_t) * parked_words(n
 // can run it beside the index build).  parked: parked_bytes(n) of device
 // memory; counter: the work counter of the follower launch that follows.
 int prepare_launch(const trd_seeds_t *seeds, const trd_params_t *p, trd_results_t *out, cudaStream_t s,
-                   void *parked, int *counter, const trd_alignment_t *align)
+                   void *parked, int *counter, const int32_t *seed_offsets, int n_tf, const trd_alignment_t *align)
 {
     if (seeds->n == 0) return TRD_OK;
     if (!parked || !counter) return TRD_EINVAL;
     SeedsView sv{seeds->alpha, seeds->x, seeds->y, seeds->z, seeds->snp, seeds->tgl, seeds->q2pt, seeds->cov,
-                 seeds->n, nullptr, 1, seeds->trigger};
+                 seeds->n, seed_offsets, seed_offsets ? n_tf : 1, seeds->trigger};
     const Params P = make_params(p, align);
     ResultsView o{out->alpha, out->x, out->par, out->cov, out->chi2, out->n_trk, out->n_miss, out->status,
                   out->tracklet_id};

@@ -66,7 +66,8 @@ int follow_launch(const trd_ctx *ctx, const trd_seeds_t *seeds, const IndexView 
 // Device scratch of the seeds' pre-pass for n seeds (sorted, rotated states).
 size_t parked_bytes(int32_t n);
 int prepare_launch(const trd_seeds_t *seeds, const trd_params_t *p, trd_results_t *out, cudaStream_t s,
-                   void *parked, int *counter, const trd_alignment_t *align = nullptr);
+                   void *parked, int *counter, const int32_t *seed_offsets = nullptr, int n_tf = 1,
+                   const trd_alignment_t *align = nullptr);
 int follow_checked(trd_ctx *ctx, const trd_seeds_t *seeds, const trd_index *index, const trd_params_t *p,
                    const trd_alignment_t *align, trd_results_t *out, void *stream, const trd_launch_t *launch,
                    void *parked);
