@@ -71,12 +71,12 @@ REFIT_FLOPS_PER_LAYER = 460
 # is still in L2 when the kernel ends), valid only for the source measured.
 REFIT_TRAFFIC = {"source_sha256_16": "d0afd33335175e46", "bytes": 39.81e6}
 # DRAM bytes (read + write) of one trd_follow call on this workload from one
-# ncu capture of its four kernels (k_seed_key 0.81 MB, k_seed_prepare 21.04 MB,
-# k_follow 60.05 MB, k_results_gather 26.41 MB; ncu empties the caches before
+# ncu capture of its four kernels (k_seed_key 0.82 MB, k_seed_prepare 20.97 MB,
+# k_follow 60.07 MB, k_results_gather 26.41 MB; ncu empties the caches before
 # each kernel, so the gather's reads of the staged results, L2 hits in a
 # plain run, count here), valid only for the kernel source it was measured
 # on: reported as null once follow.cu, trd_device.cuh or track_model.cuh change.
-FOLLOW_TRAFFIC = {"source_sha256_16": "585b8ab9b23a647b", "bytes": 108.31e6}
+FOLLOW_TRAFFIC = {"source_sha256_16": "590f2d96086b25c1", "bytes": 108.27e6}
 # DRAM bytes (read 206.72 MB + write 16.63 MB) of one k_residuals launch on the
 # 100,000-track map from one ncu capture; the 450,000-track map holds ~3 GB on
 # the device and is not captured, so the figure is reported for the captured
