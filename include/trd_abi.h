@@ -394,8 +394,10 @@ TRD_API int trd_voxel_solve(trd_ctx_t *ctx, const int64_t *voxel_sums, int32_t m
  *       Result tracklet ids are local to each seed's timeframe.
  *   params, y_bin_width, launch: as for trd_index_build / trd_follow_tuned.
  * The library owns the batch (index, offsets, the follower's scratch of 136
- * bytes per seed + 512, graph); free with trd_batch_free.  Each seed's arithmetic is the same as in trd_follow on
- * its timeframe alone, so results are identical.
+ * bytes per seed + 512, graph); free with trd_batch_free.  Seeds are taken
+ * timeframe by timeframe, each timeframe's in decreasing-|q/pT| order; each
+ * seed's arithmetic is the same as in trd_follow on its timeframe alone, so
+ * results are identical.
  * trd_batch_run replays the graph on `stream` (asynchronous).  A batch must
  * not be run concurrently with itself.
  * Errors: TRD_EINVAL (bad offsets, parameters or shape), TRD_ENOMEM,
