@@ -77,11 +77,11 @@ REFIT_TRAFFIC = {"source_sha256_16": "d0afd33335175e46", "bytes": 39.81e6}
 # plain run, count here), valid only for the kernel source it was measured
 # on: reported as null once follow.cu, trd_device.cuh or track_model.cuh change.
 FOLLOW_TRAFFIC = {"source_sha256_16": "590f2d96086b25c1", "bytes": 108.27e6}
-# DRAM bytes (read 206.72 MB + write 16.63 MB) of one k_residuals launch on the
+# DRAM bytes (read 207.63 MB + write 13.23 MB) of one k_residuals launch on the
 # 100,000-track map from one ncu capture; the 450,000-track map holds ~3 GB on
 # the device and is not captured, so the figure is reported for the captured
 # size only (the voxel array's write-back does not grow with the tracks).
-RES_TRAFFIC = {"source_sha256_16": "ce8c0e7a789fed23", "bytes": 223.35e6, "tracks": 100_000}
+RES_TRAFFIC = {"source_sha256_16": "3fa7da3ab857720a", "bytes": 220.86e6, "tracks": 100_000}
 RES_SOURCES = ("residuals.cu", "trd_device.cuh", "track_model.cuh")
 
 
