@@ -373,10 +373,11 @@ extern "C" int trd_index_build_noalloc(const trd_tracklets_t *t, float y_bin_wid
     float4 *rec = reinterpret_cast<float4 *>(records);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
 
-    // the counters and the caller's stats must start at zero; the rest of the
-    // scratch is fully written before it is read
-    // the counters are zero here: the static array starts zeroed and every
-    // build's scan zeroes the ones it used
+    // the counters and the caller's stats must start at zero: the shared array
+    // keeps whatever the last call left (its scan re-zeroes the counters, but
+    // a call that did not complete would not), so they are cleared here; the
+    // rest of the scratch is fully written before it is read
+    TRD_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(int32_t) * n_buckets, s));
     TRD_CUDA_TRY(cudaMemsetAsync(stats, 0, sizeof(uint32_t) * 4, s));
     const int grid_n = n > 0 ? std::min((n + kCountThreads * kIlp - 1) / (kCountThreads * kIlp), d.sm_count * 8) : 0;
     if (n > 0) {
