@@ -256,12 +256,13 @@ int scan_blocks_for(int n) { return (n + kScanTile - 1) / kScanTile; }
 int index_rebuild_launch(trd_index *idx, const trd_tracklets_t *t, cudaStream_t s)
 {
     const int n = t->n;
-    // the bucket counters are zero between builds: zeroed once here, then by
-    // every build's scan after it has read them
-    if (!idx->counts_zero) {
-        TRD_CUDA_TRY(cudaMemsetAsync(idx->counts, 0, sizeof(int32_t) * idx->n_buckets, s));
-        idx->counts_zero = true;
-    }
+    // the bucket counters are zero between builds: cleared here when no
+    // complete build has run since they were (first build, or a build that
+    // stopped on an error), otherwise by the previous build's scan after it
+    // read them; the flag is set again once this build's scan is enqueued
+    const bool clear = !idx->counts_zero;
+    idx->counts_zero = false;
+    if (clear) TRD_CUDA_TRY(cudaMemsetAsync(idx->counts, 0, sizeof(int32_t) * idx->n_buckets, s));
     TRD_CUDA_TRY(cudaMemsetAsync(idx->stats, 0, sizeof(uint32_t) * 4, s));
     const int grid_n =
         n > 0 ? std::min((n + kCountThreads * kIlp - 1) / (kCountThreads * kIlp), idx->ctx->sm_count * 8) : 0;
@@ -277,6 +278,7 @@ int index_rebuild_launch(trd_index *idx, const trd_tracklets_t *t, cudaStream_t 
                               idx->partials));
     TRD_CUDA_TRY(launch_after(k_scan_apply, dim3(m), dim3(kScanThreads), 0, s, idx->counts, idx->n_buckets,
                               idx->partials, idx->offsets));
+    idx->counts_zero = true;  // the scan just enqueued leaves them zero
     if (n > 0) {
         TRD_CUDA_TRY(launch_after(k_index_scatter, dim3(grid_n), dim3(kCountThreads), 0, s, t->y, t->z, t->dy,
                                   t->vyy, t->vzz, t->vyz, n, idx->bucket, idx->offsets, idx->rec, idx->toff,

@@ -39,7 +39,8 @@ struct trd_index {
     // build scratch
     int32_t *bucket;    // [capacity] bucket of each input tracklet (-1: rejected)
     int32_t *counts;    // [n_buckets], zero between builds (each build's scan re-zeroes them)
-    bool counts_zero;   // zeroed once (at the first build, or by the batch before capture)
+    bool counts_zero;   // the counters are zero for the next build (set by a build whose scan
+                        // was enqueued, or by the batch before its capture)
     int32_t *partials;  // [scan blocks + 1]
     int32_t n_partials;
     cudaStream_t stream;  // stream of the last build
