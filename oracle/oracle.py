@@ -55,6 +55,8 @@ def _load(path):
         L.ora_material.restype = C.c_int
         L.ora_bethe.argtypes = [C.c_double]
         L.ora_bethe.restype = C.c_double
+        L.ora_bethe_dbg.argtypes = [C.c_double]
+        L.ora_bethe_dbg.restype = C.c_double
         L.ora_highland.argtypes = [C.c_double, C.c_double, C.c_double]
         L.ora_highland.restype = C.c_double
         L.ora_update.argtypes = [_d, _d, C.c_int, _d, C.c_int]
@@ -133,6 +135,11 @@ def propagate_map(st, cov, x_to, bz, field=None):
 
 def bethe(bg: float) -> float:
     return lib().ora_bethe(float(bg))
+
+
+def bethe_dbg(bg: float) -> float:
+    """Slope of the Bethe curve, d(dE/dx)/d(beta gamma), MeV cm^2/g."""
+    return lib().ora_bethe_dbg(float(bg))
 
 
 def highland(p: float, beta: float, xx0: float) -> float:
@@ -350,6 +357,6 @@ def _params_arrays(params):
     return pd, pi
 
 
-__all__ = ["use_library", "propagate", "rotate", "material", "bethe", "highland", "update", "chi2",
+__all__ = ["use_library", "propagate", "rotate", "material", "bethe", "bethe_dbg", "highland", "update", "chi2",
            "cov_is_pd", "constants", "follow", "refit", "to_layer", "candidates", "lib",
            "material_inward", "propagate_map", "residuals", "voxel_solve", "voxel_of", "N_VOXELS", "N_TPC_ROWS"]

@@ -19,11 +19,13 @@
  *   signed curvature rho = d(phi)/ds = -C_LIGHT * Bz * q2pt
  *       (Lorentz force: +q in +Bz bends towards -y)
  *
- * Parity unpinned: the material step (Highland + Bethe with the constants of
- * the reading) has no counterpart in the paper beyond "energy loss" (Sec. 3);
- * only its invariants are pinned (material off gives the pure helix, the
- * Bethe curve has its minimum near beta*gamma = 3.5, scattering only widens
- * the angular/curvature block).
+ * The material step (Highland + Bethe with the constants of the reading) has
+ * no counterpart in the paper beyond "energy loss" (Sec. 3).  Its constants
+ * are a reading; its action on the state and covariance is pinned: the
+ * scattering increments against a Monte-Carlo of two projected angles
+ * carried through the exact direction geometry, the energy taken out against
+ * the Bethe curve over the geometric path, and the covariance transport
+ * against finite differences of the state map.
  *
  * Build: gcc -O2 -fopenmp -shared -fPIC trd_oracle.c -o libtrd_oracle.so -lm
  */
@@ -262,6 +264,20 @@ double ora_bethe(double bg)
            (log(2.0 * kMassElectron * bg * bg / kIExcitation) - b2);
 }
 
+/* d(ora_bethe)/d(beta gamma): with 1/beta^2 = 1 + 1/bg^2 the curve is
+ * K Z/A (1 + 1/bg^2) (ln(2 m_e bg^2 / I) - beta^2), differentiated term by
+ * term (d beta^2 / d bg = 2 bg / (1 + bg^2)^2).                             */
+double ora_bethe_dbg(double bg)
+{
+    const double bg2 = bg * bg;
+    const double inv_b2 = 1.0 + 1.0 / bg2;
+    const double b2 = bg2 / (1.0 + bg2);
+    const double bracket = log(2.0 * kMassElectron * bg2 / kIExcitation) - b2;
+    const double d_inv_b2 = -2.0 / (bg2 * bg);
+    const double d_bracket = 2.0 / bg - 2.0 * bg / ((1.0 + bg2) * (1.0 + bg2));
+    return kBetheK * kZOverA * (d_inv_b2 * bracket + inv_b2 * d_bracket);
+}
+
 /* Highland: variance of the projected scattering angle (rad^2). */
 double ora_highland(double p, double beta, double xx0)
 {
@@ -270,14 +286,17 @@ double ora_highland(double p, double beta, double xx0)
     return t0 * t0 * xx0 * f * f;
 }
 
-/* One material step: multiple scattering widens snp, tgl, q2pt; the mean
- * energy loss of a pion reduces |p| and scales q2pt and its covariance row
- * by p/p'.  Returns -1 when the particle stops.                            */
 /* One material step at the current position.  dir = +1 for a track moving
  * outward (the mean loss is subtracted), -1 for a track moving inward (the
- * refit of Sec. 2, step 3: the loss is added back).  The scattering term is
- * the same in both directions; the loss is evaluated at the momentum on
- * entering the step.                                                       */
+ * refit of Sec. 2, step 3: the loss is added back).
+ *   1. multiple scattering at the entry momentum widens snp, tgl and q2pt
+ *      (two projected angles of variance theta0^2 carried onto the state);
+ *   2. the mean energy loss of a pion over the path through the layer
+ *      changes |p| to p', so q2pt becomes q2pt p / p' = sign(q) sqrt(1 + tgl^2) / p';
+ *   3. the covariance is carried through step 2 by its Jacobian, as through
+ *      a transport: q2pt' depends on snp (path length), on tgl (path length
+ *      and p) and on q2pt (p, and through p the Bethe curve).
+ * Returns -1 when the particle stops.                                      */
 static int material_dir(double st[7], double c[15], double dir)
 {
     const double f = st[4], t = st[5], k = st[6];
@@ -295,14 +314,27 @@ static int material_dir(double st[7], double c[15], double dir)
     c[ci(3, 3)] += th2 * t2 * t2;
     c[ci(4, 3)] += th2 * t * t2 * k;
     c[ci(4, 4)] += th2 * t * t * k * k;
-    const double de = ora_bethe(p / kMassPion) * xrho * 1e-3;
+    const double bg = p / kMassPion;
+    const double de = ora_bethe(bg) * xrho * 1e-3;
     const double e1 = e - dir * de;
     if (e1 <= kMassPion) return -1;
     const double p1 = sqrt(e1 * e1 - kMassPion * kMassPion);
-    const double sc = p / p1;
-    st[6] = k * sc;
-    for (int i = 0; i < 4; ++i) c[ci(4, i)] *= sc;
-    c[ci(4, 4)] *= sc * sc;
+    const double k1 = k * p / p1;
+    /* derivatives with respect to (snp, tgl, q2pt) */
+    const double dp[3] = {0.0, p * t / t2, -p / k};
+    const double dpath[3] = {path * f / (r * r), path * t / t2, 0.0};
+    const double dlns[3] = {0.0, t / t2, 0.0}; /* d ln sqrt(1 + tgl^2) */
+    double J[5][5];
+    eye5(J);
+    for (int a = 0; a < 3; ++a) {
+        const double dde = 1e-3 * kXRho *
+                           (ora_bethe_dbg(bg) * dp[a] / kMassPion * path + ora_bethe(bg) * dpath[a]);
+        const double de1 = (p / e) * dp[a] - dir * dde;
+        const double dp1 = (e1 / p1) * de1;
+        J[4][2 + a] = k1 * (dlns[a] - dp1 / p1);
+    }
+    st[6] = k1;
+    cov_transport(J, c);
     return 0;
 }
 

@@ -183,12 +183,18 @@ static __device__ bool rotate(TrackState &s, df delta, int new_sector, float bz)
 // ---- material step (reading: Highland scattering + Bethe loss of a pion) ----
 // INWARD = false: a track moving outward, the mean loss is subtracted;
 // INWARD = true: a track moving inward (the refit), the loss is added back.
+// Scattering at the entry momentum widens the sin(phi), tan(lambda), q/pT
+// block; the loss changes |p| to p', so q/pT becomes sign(q) sqrt(1+tgl^2)/p'
+// and the covariance is carried through that change by its Jacobian (the
+// loss depends on q/pT through p and the slope of the Bethe curve, on sin(phi)
+// and tan(lambda) through the path length, and tan(lambda) also enters p).
 template <bool INWARD>
 static __device__ bool material(TrackState &s)
 {
     const float f = s.f, t = s.t, k = s.k;
     if (k == 0.0f) return true;
-    const float r = sqrtf((1.0f - f) * (1.0f + f));
+    const float r2 = (1.0f - f) * (1.0f + f);
+    const float r = sqrtf(r2);
     const float t2 = fmaf(t, t, 1.0f);
     const float st2 = sqrtf(t2);
     const float path = st2 / r;
@@ -201,25 +207,46 @@ static __device__ bool material(TrackState &s)
     const float lg = fmaf(0.038f, __logf(xx0), 1.0f);
     const float th2 = t0 * t0 * xx0 * lg * lg;
     float *C = s.c;
-    C[5] += th2 * r * r * t2;
+    C[5] += th2 * r2 * t2;
     C[9] += th2 * t2 * t2;
     C[13] += th2 * t * t2 * k;
     C[14] += th2 * t * t * k * k;
     const float bg = p / kMassPion;
     const float bg2 = bg * bg;
     const float b2 = bg2 / (1.0f + bg2);
-    const float dedx = kBetheKZA / b2 * (__logf(kTwoMeOverI * bg2) - b2);  // GeV cm^2/g
+    const float ib2 = 1.0f + 1.0f / bg2;  // 1 / beta^2
+    const float brk = __logf(kTwoMeOverI * bg2) - b2;
+    const float dedx = kBetheKZA * ib2 * brk;  // GeV cm^2/g
+    // d(dedx)/d(bg) = K Z/A (d(1/beta^2)/dbg * brk + 1/beta^2 * d(brk)/dbg)
+    const float ddedx = kBetheKZA * (-2.0f / (bg2 * bg) * brk + ib2 * (2.0f / bg - 2.0f * b2 * (1.0f - b2) / bg));
     const float de = dedx * kXRho * path;
     const float e1 = INWARD ? e + de : e - de;
     if (!(e1 > kMassPion)) return false;
     const float p1 = sqrtf((e1 - kMassPion) * (e1 + kMassPion));
-    const float sc = p / p1;
-    s.k = k * sc;
-    C[10] *= sc;
-    C[11] *= sc;
-    C[12] *= sc;
-    C[13] *= sc;
-    C[14] *= sc * sc;
+    const float k1 = k * (p / p1);
+    // d q2pt' / d(snp, tgl, q2pt) = q2pt' (d ln sqrt(1+tgl^2) - e1/p1^2 d e1), with
+    // d e1 = (p/e) dp -+ d de, dp = (0, p tgl/t2, -p/q2pt), dpath = (path snp/r^2, path tgl/t2, 0)
+    const float tt2 = t / t2;
+    const float sgn = INWARD ? -1.0f : 1.0f;                    // e1 = e - sgn de
+    const float slope = ddedx * kXRho * path * (1.0f / kMassPion);  // d de / dp
+    const float w = k1 * e1 / (p1 * p1);
+    const float de1_df = -sgn * dedx * kXRho * path * f / r2;
+    const float dp_dt = p * tt2;
+    const float de1_dt = (p / e) * dp_dt - sgn * (slope * dp_dt + de * tt2);
+    const float dp_dk = -p / k;
+    const float de1_dk = (p / e - sgn * slope) * dp_dk;
+    const float ja = -w * de1_df;             // d q2pt' / d snp
+    const float jb = k1 * tt2 - w * de1_dt;   // d q2pt' / d tgl
+    const float jc = -w * de1_dk;             // d q2pt' / d q2pt
+    s.k = k1;
+    // C <- J C J^T with J = I except row 4 = (0, 0, ja, jb, jc)
+    const float C20 = C[3], C21 = C[4], C22 = C[5], C30 = C[6], C31 = C[7], C32 = C[8], C33 = C[9];
+    const float C40 = C[10], C41 = C[11], C42 = C[12], C43 = C[13], C44 = C[14];
+    C[10] = ja * C20 + jb * C30 + jc * C40;
+    C[11] = ja * C21 + jb * C31 + jc * C41;
+    C[12] = ja * C22 + jb * C32 + jc * C42;
+    C[13] = ja * C32 + jb * C33 + jc * C43;
+    C[14] = ja * (ja * C22 + 2.0f * (jb * C32 + jc * C42)) + jb * (jb * C33 + 2.0f * jc * C43) + jc * jc * C44;
     return true;
 }
 

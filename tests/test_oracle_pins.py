@@ -277,6 +277,151 @@ def test_material_widens_angles_and_lowers_momentum():
         assert O.cov_is_pd(c1)
 
 
+
+# The material reading's constants (not the paper's): one step per layer of
+# x/X0 = 0.04 and 1 g/cm^2 at normal incidence, a pion.
+MAT_X0 = 0.04
+MAT_RHO = 1.0
+M_PION = 0.13957039
+
+
+def _direction(f, t):
+    """Unit direction of a track with sin(phi) = f, tan(lambda) = t in the
+    local frame (x along the layer normal)."""
+    lam = math.atan(t)
+    phi = math.asin(f)
+    return np.array([math.cos(lam) * math.cos(phi), math.cos(lam) * math.sin(phi), math.sin(lam)])
+
+
+def _path_through_layer(f, t):
+    """Path length through a slab normal to x, per unit thickness: 1 over the
+    direction's x component (geometry, not the oracle's expression)."""
+    return 1.0 / _direction(f, t)[0]
+
+
+def _material_states():
+    # tgl away from 0: there the first-order q2pt variance (theta^2 tgl^2
+    # q2pt^2) vanishes and the second-order term q2pt^2 theta^4 / 2, which a
+    # linearised filter does not carry, would dominate the Monte-Carlo
+    return [np.array([0.3, 300.0, 4.0, 20.0, f, t, k])
+            for f, t, k in [(0.5, 0.8, 2.0), (-0.7, -0.4, -1.3), (0.1, 0.35, 3.0), (0.0, 1.1, -0.4),
+                            (-0.3, 0.6, 0.25)]]
+
+
+def test_bethe_slope_matches_finite_differences():
+    for bg in [0.4, 1.0, 3.5, 10.0, 200.0]:
+        h = 1e-5 * bg
+        fd = (O.bethe(bg + h) - O.bethe(bg - h)) / (2 * h)
+        assert O.bethe_dbg(bg) == pytest.approx(fd, rel=1e-7, abs=1e-9)
+
+
+def _scatter_mc(f, t, k, theta2, n, seed):
+    """Two independent projected angles of variance theta2 about the track
+    direction, applied to the direction exactly; the momentum is unchanged.
+    Returns samples of (snp, tgl, q2pt) after the deflection."""
+    g = np.random.default_rng(seed)
+    d = _direction(f, t)
+    e1 = np.array([-d[1], d[0], 0.0]) / math.hypot(d[0], d[1])  # transverse, in the bending plane
+    e2 = np.cross(d, e1)                                         # completes the right-handed triad
+    a1 = g.normal(0.0, math.sqrt(theta2), n)
+    a2 = g.normal(0.0, math.sqrt(theta2), n)
+    dn = d[None, :] + np.tan(a1)[:, None] * e1[None, :] + np.tan(a2)[:, None] * e2[None, :]
+    dn /= np.linalg.norm(dn, axis=1)[:, None]
+    ct = np.hypot(dn[:, 0], dn[:, 1])           # cos(lambda')
+    snp = dn[:, 1] / ct
+    tgl = dn[:, 2] / ct
+    q2pt = k * (d[0] ** 2 + d[1] ** 2) ** 0.5 / ct  # q/(p cos(lambda')), p fixed
+    return np.stack([snp, tgl, q2pt], axis=1)
+
+
+def _material_state_jacobian(st, inward=False):
+    step = O.material_inward if inward else O.material
+    J = np.eye(5)
+    for j in (2, 3, 4):
+        h = 1e-6 * max(1.0, abs(st[2 + j]))
+        sp, sm = st.copy(), st.copy()
+        sp[2 + j] += h
+        sm[2 + j] -= h
+        okp, op, _ = step(sp, np.zeros(15))
+        okm, om, _ = step(sm, np.zeros(15))
+        assert okp and okm
+        J[:, j] = (op[2:7] - om[2:7]) / (2 * h)
+    return J
+
+
+@pytest.mark.parametrize("inward", [False, True])
+def test_material_scattering_matches_monte_carlo_of_two_angles(inward):
+    """The covariance the step adds, against the sample covariance of two
+    projected scattering angles of the Highland variance (over the geometric
+    path) carried through the exact direction geometry, then through the
+    step's own energy-loss Jacobian (taken by finite differences)."""
+    step = O.material_inward if inward else O.material
+    for n_state, st in enumerate(_material_states()):
+        f, t, k = st[4], st[5], st[6]
+        p = math.sqrt(1 + t * t) / abs(k)
+        beta = p / math.hypot(p, M_PION)
+        theta2 = O.highland(p, beta, MAT_X0 * _path_through_layer(f, t))
+        smp = _scatter_mc(f, t, k, theta2, 400_000, 100 + n_state)
+        Q = np.zeros((5, 5))
+        Q[2:, 2:] = np.cov(smp, rowvar=False)
+        J = _material_state_jacobian(st, inward)
+        want = J @ Q @ J.T
+        ok, _, c1 = step(st, np.zeros(15))
+        assert ok
+        got = _full(c1)
+        # diagonal within the Monte-Carlo error (~0.3 % at 400k samples)
+        for i in (2, 3, 4):
+            assert got[i, i] == pytest.approx(want[i, i], rel=0.015), (st, i)
+        # the tgl-q2pt correlation (both come from the polar angle)
+        assert got[4, 3] == pytest.approx(want[4, 3], rel=0.015, abs=0.01 * math.sqrt(want[3, 3] * want[4, 4]))
+        # nothing outside the angular block; snp uncorrelated with the polar angle
+        assert np.all(got[:2, :] == 0)
+        for i, j in ((3, 2), (4, 2)):
+            assert abs(got[i, j] - want[i, j]) < 0.01 * math.sqrt(want[i, i] * want[j, j]) + 1e-300
+
+
+@pytest.mark.parametrize("inward", [False, True])
+def test_material_energy_change_is_the_bethe_loss_over_the_path(inward):
+    """E(p) - E(p') equals the Bethe mean loss at the entry momentum times the
+    areal density along the geometric path (the reverse going inward); the
+    angles and position do not change."""
+    step = O.material_inward if inward else O.material
+    sign = -1.0 if inward else 1.0
+    for st in _material_states():
+        f, t, k = st[4], st[5], st[6]
+        ok, s1, _ = step(st, np.zeros(15))
+        assert ok
+        np.testing.assert_array_equal(s1[:6], st[:6])
+        p0 = math.sqrt(1 + t * t) / abs(k)
+        p1 = math.sqrt(1 + t * t) / abs(s1[6])
+        assert s1[6] * k > 0
+        de = math.hypot(p0, M_PION) - math.hypot(p1, M_PION)
+        want = sign * O.bethe(p0 / M_PION) * MAT_RHO * _path_through_layer(f, t) * 1e-3
+        assert de == pytest.approx(want, rel=1e-10)
+
+
+@pytest.mark.parametrize("inward", [False, True])
+def test_material_covariance_transport_is_the_jacobian_of_the_state_map(inward):
+    """Apart from the added scattering, the step carries the covariance by the
+    Jacobian of its own state change: C'(C) - C'(0) = J C J^T, with J from
+    finite differences of the step's (snp, tgl, q2pt) map."""
+    step = O.material_inward if inward else O.material
+    for st in _material_states():
+        J = _material_state_jacobian(st, inward)
+        # the loss depends on q2pt through p and the Bethe slope, and on the
+        # path length through snp and tgl
+        assert J[4, 4] != pytest.approx(st[6] / st[6], abs=1e-9)
+        for _ in range(3):
+            c = _random_cov()
+            ok, _, c1 = step(st, c)
+            ok0, _, c0 = step(st, np.zeros(15))
+            assert ok and ok0
+            got = _full(c1) - _full(c0)
+            want = J @ _full(c) @ J.T
+            scale = np.sqrt(np.outer(np.diag(want), np.diag(want)))
+            np.testing.assert_allclose(got, want, rtol=1e-6, atol=1e-7 * scale.max())
+            assert np.all(np.abs(got - want) <= 2e-6 * scale + 1e-300)
+
 # ---------------------------------------------------------------- update
 def _info_form(st, c, layer, meas):
     """Information-filter posterior (textbook alternative to the gain form)."""
