@@ -184,7 +184,9 @@ TRD_API int trd_index_copy_out(const trd_index_t *index, int32_t *offsets, int32
  * returns TRD_EINVAL.  All calls on a device share that scratch: calls that
  * overlap on the GPU (other streams, other threads) race and must be ordered
  * by the caller.  The first call on each device looks up the array's device
- * address (no allocation); make that first call before any stream capture.
+ * address (no allocation), and so does the first call after the device's
+ * context was re-created (cudaDeviceReset); make such a call before any
+ * stream capture.
  * Asynchronous on `stream`; the inputs must stay valid until it completes.
  * Errors: TRD_EINVAL (NULL pointer, size or bin width beyond the limits,
  * misaligned records), TRD_ECUDA.                                           */
@@ -207,9 +209,10 @@ TRD_API int trd_index_build_noalloc(const trd_tracklets_t *tracklets, float y_bi
  * Seeds are processed in order of decreasing |q/pT| (lanes that work together
  * then have roads of similar width); results do not depend on the order and
  * are written at the seeds' input positions.  The call's scratch (136 bytes
- * per seed + 512: sorted seed states and staged results) is taken from the
- * device's default memory pool, ordered on `stream` (cudaMallocAsync /
- * cudaFreeAsync).
+ * per seed + 528: sorted seed states, staged results and the call's own work
+ * counter, so calls in flight on any number of streams never share one) is
+ * taken from the device's default memory pool, ordered on `stream`
+ * (cudaMallocAsync / cudaFreeAsync).
  * Errors: TRD_EINVAL (NULL pointers, n < 0, n_hyp outside 1..TRD_MAX_HYP,
  * non-positive road/cut), TRD_ENOMEM (no scratch), TRD_ECUDA (launch
  * failure).                                                                 */
@@ -381,6 +384,13 @@ TRD_API int trd_voxel_solve(trd_ctx_t *ctx, const int64_t *voxel_sums, int32_t m
 
 /* ---- batches of timeframes (Sec. 3.1: Run 3 processes time frames of many
  * collisions; here many time frames at once) ----------------------------------
+ * A batched follow, "follow n_tf timeframes in one persistent, graph-captured
+ * launch", is split here into create / run / free: a CUDA graph is bound to
+ * its buffers when it is captured, so the capture (trd_batch_create, which
+ * also sizes the batch's index and scratch) happens once and each
+ * trd_batch_run replays it on fresh contents of the same buffers.  One
+ * create + run + free is the single-call form; a caller that refills the
+ * buffers keeps the batch and calls run again.
  * trd_batch_create: prepare one CUDA graph that, for n_tf timeframes stored
  * back to back, builds a single index over all their tracklets and follows
  * all their seeds in one persistent launch that pulls seeds of every
@@ -394,7 +404,7 @@ TRD_API int trd_voxel_solve(trd_ctx_t *ctx, const int64_t *voxel_sums, int32_t m
  *       Result tracklet ids are local to each seed's timeframe.
  *   params, y_bin_width, launch: as for trd_index_build / trd_follow_tuned.
  * The library owns the batch (index, offsets, the follower's scratch of 136
- * bytes per seed + 512, graph); free with trd_batch_free.  Seeds are taken
+ * bytes per seed + 528, graph); free with trd_batch_free.  Seeds are taken
  * timeframe by timeframe, each timeframe's in decreasing-|q/pT| order; each
  * seed's arithmetic is the same as in trd_follow on its timeframe alone, so
  * results are identical.
@@ -444,7 +454,10 @@ TRD_API int trd_server_create(trd_ctx_t *ctx, const trd_server_cfg_t *cfg, trd_s
 /* trd_server_submit: queue one timeframe.  seeds, tracklets and results are
  * HOST pointers (layouts as for trd_follow) that must stay valid until the
  * request completes; page-locked host memory lets the copies overlap other
- * requests' kernels.  *ticket identifies the request.  Errors: TRD_EINVAL,
+ * requests' kernels.  *ticket identifies the request.  The host result
+ * buffers are named here rather than at poll time because the result copies
+ * are enqueued on the request's stream right behind its kernels (they then
+ * overlap the next request's work); poll only reports that they landed.  Errors: TRD_EINVAL,
  * TRD_ENOMEM (the request alone exceeds the budget), TRD_EAGAIN (queue
  * full: retry later).                                                       */
 TRD_API int trd_server_submit(trd_server_t *server, const trd_seeds_t *seeds,

@@ -44,14 +44,6 @@ void free_index_buffers(trd_index *x)
 }  // namespace
 
 namespace trd_host {
-// Each launch takes its own work-counter slot, so launches in flight on
-// different streams never share a counter (up to kCounterSlots at once).
-int *next_counter(trd_ctx *ctx)
-{
-    const unsigned k = __atomic_fetch_add(&ctx->launch_seq, 1u, __ATOMIC_RELAXED);
-    return ctx->counters + (k % kCounterSlots);
-}
-
 // Allocate an index for up to `capacity` tracklets of `n_tf` timeframes.
 int index_alloc(trd_ctx *ctx, int32_t capacity, float y_bin_width, int32_t n_tf, trd_index **out)
 {
@@ -130,8 +122,6 @@ int trd_ctx_create(int device, trd_ctx_t **ctx)
     c->sm_count = prop.multiProcessorCount;
     c->max_threads_per_sm = prop.maxThreadsPerMultiProcessor;
     c->l2_bytes = static_cast<size_t>(prop.l2CacheSize);
-    c->launch_seq = 0;
-    c->counters = nullptr;
     // the follower and the server take stream-ordered scratch from the
     // device's default pool on every call: keep freed blocks in the pool
     // (the default threshold of 0 returns them to the system at every
@@ -142,11 +132,6 @@ int trd_ctx_create(int device, trd_ctx_t **ctx)
         (void)cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
     }
     (void)cudaGetLastError();
-    if (cudaMalloc(&c->counters, sizeof(int32_t) * kCounterSlots) != cudaSuccess) {
-        (void)cudaGetLastError();
-        delete c;
-        return TRD_ENOMEM;
-    }
     *ctx = c;
     return TRD_OK;
 }
@@ -154,9 +139,6 @@ int trd_ctx_create(int device, trd_ctx_t **ctx)
 int trd_ctx_destroy(trd_ctx_t *ctx)
 {
     if (!ctx) return TRD_EINVAL;
-    cudaSetDevice(ctx->device);
-    cudaFree(ctx->counters);
-    (void)cudaGetLastError();
     delete ctx;
     return TRD_OK;
 }
@@ -286,7 +268,7 @@ int trd_host::follow_checked(trd_ctx *ctx, const trd_seeds_t *seeds, const trd_i
     IndexView iv{index->offsets, index->rec, index->stats, index->nb, index->inv_w,
                  index->has_x ? index->recx : nullptr};
     return trd_host::follow_launch(ctx, seeds, iv, p, out, static_cast<cudaStream_t>(stream), lanes_per_track,
-                                   block_threads, min_blocks, trd_host::next_counter(ctx), nullptr, 1, align, true,
+                                   block_threads, min_blocks, nullptr, nullptr, 1, align, true,
                                    parked);
 }
 

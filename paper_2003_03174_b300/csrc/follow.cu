@@ -577,6 +577,9 @@ __device__ __forceinline__ int sort_bin(float q2pt, int tf, int n_tf)
 
 // Scratch of one follower call (device, n seeds; the base 16-byte aligned):
 //   bin_count [kSortBins]     seeds per |q/pT| bin (zeroed before k_seed_key)
+//   counter   [4]             the follower's work counter (zeroed by
+//                             k_seed_key), then padding: each call in flight
+//                             has its own
 //   rec       [n][8] float4   one 128-byte record per sorted position: first
 //                             the parked seed (k_seed_prepare), then the
 //                             staged result (stage_result)
@@ -588,13 +591,16 @@ __device__ __forceinline__ int sort_bin(float q2pt, int tf, int n_tf)
 // unused until the result is staged.
 struct ParkedView {
     int32_t *bin_count;
+    int32_t *counter;
     float4 *rec;
     int32_t *rank, *inv;
 };
 
+constexpr int kParkedHead = kSortBins + 4;  // bin counts, work counter, padding
+
 __host__ __device__ inline size_t parked_words(int n)
 {
-    return static_cast<size_t>(kSortBins) + static_cast<size_t>(32 + 2) * static_cast<size_t>(n);
+    return static_cast<size_t>(kParkedHead) + static_cast<size_t>(32 + 2) * static_cast<size_t>(n);
 }
 
 __host__ __device__ inline ParkedView parked_view(void *base, int n)
@@ -602,8 +608,9 @@ __host__ __device__ inline ParkedView parked_view(void *base, int n)
     int32_t *w = static_cast<int32_t *>(base);
     ParkedView v;
     v.bin_count = w;
-    v.rec = reinterpret_cast<float4 *>(w + kSortBins);  // 512 bytes in: still 16-byte aligned
-    v.rank = w + kSortBins + 32 * static_cast<size_t>(n);
+    v.counter = w + kSortBins;
+    v.rec = reinterpret_cast<float4 *>(w + kParkedHead);  // 528 bytes in: still 16-byte aligned
+    v.rank = w + kParkedHead + 32 * static_cast<size_t>(n);
     v.inv = v.rank + n;
     return v;
 }
@@ -1078,7 +1085,8 @@ int prepare_launch(const trd_seeds_t *seeds, const trd_params_t *p, trd_results_
                    void *parked, int *counter, const int32_t *seed_offsets, int n_tf, const trd_alignment_t *align)
 {
     if (seeds->n == 0) return TRD_OK;
-    if (!parked || !counter) return TRD_EINVAL;
+    if (!parked) return TRD_EINVAL;
+    if (!counter) counter = parked_view(parked, seeds->n).counter;
     SeedsView sv{seeds->alpha, seeds->x, seeds->y, seeds->z, seeds->snp, seeds->tgl, seeds->q2pt, seeds->cov,
                  seeds->n, seed_offsets, seed_offsets ? n_tf : 1, seeds->trigger};
     const Params P = make_params(p, align);
@@ -1114,6 +1122,7 @@ int follow_launch(const trd_ctx *ctx, const trd_seeds_t *seeds, const IndexView 
         parked = own;
     }
     const ParkedView pk = sv.n > 0 ? parked_view(parked, sv.n) : ParkedView{};
+    if (!counter) counter = pk.counter;  // the call's own, inside its scratch
     const int rc = ext ? dispatch<true>(ctx, sv, iv, P, o, pk, s, G, mb, block, p->n_hyp, counter, prepare)
                        : dispatch<false>(ctx, sv, iv, P, o, pk, s, G, mb, block, p->n_hyp, counter, prepare);
     if (own && cudaFreeAsync(own, s) != cudaSuccess) {

@@ -15,11 +15,14 @@
 // The pad rows of one (chamber, y bin) are adjacent, so the follower reads
 // one contiguous range per y bin.  Order inside a bucket is not defined;
 // the follower's selection does not depend on it (ties break on tracklet id).
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 
+#include "noalloc_cache.h"
 #include "trd_device.cuh"
 #include "trd_internal.h"
 
@@ -313,36 +316,59 @@ constexpr size_t kNoAllocWords =
 static __device__ __align__(256) int32_t g_noalloc_scratch[kNoAllocWords];
 
 constexpr int kNoAllocMaxDevices = 64;
-struct NoAllocDevice {
-    int32_t *scratch;  // device address of g_noalloc_scratch on this device
-    int sm_count;
-};
-NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
-int g_noalloc_ready[kNoAllocMaxDevices];  // guarded by __atomic builtins
+trd_host::NoAllocEntry g_noalloc_dev[kNoAllocMaxDevices];
+std::mutex g_noalloc_mu;
 
-// Once per device, with that device current: the host-side name of the array
-// is not a device address, so fetch the address the kernels must be given.
-int noalloc_setup(int dev, NoAllocDevice *out)
+// The current context's id through the driver API (resolved once through the
+// runtime, so the library needs no link against the driver library).
+bool current_ctx_id(unsigned long long *id)
 {
-    if (__atomic_load_n(&g_noalloc_ready[dev], __ATOMIC_ACQUIRE)) {
-        *out = g_noalloc_dev[dev];
-        return TRD_OK;
-    }
-    NoAllocDevice d{};
+    using GetCurrent = CUresult (*)(CUcontext *);
+    using GetId = CUresult (*)(CUcontext, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *a = nullptr, *b = nullptr;
+        cudaDriverEntryPointQueryResult qa{}, qb{};
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) == cudaSuccess &&
+            qa == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) == cudaSuccess &&
+            qb == cudaDriverEntryPointSuccess) {
+            get_current = reinterpret_cast<GetCurrent>(a);
+            get_id = reinterpret_cast<GetId>(b);
+        }
+        (void)cudaGetLastError();
+    });
+    if (!get_current || !get_id) return false;
+    CUcontext c = nullptr;
+    if (get_current(&c) != CUDA_SUCCESS || !c) return false;
+    return get_id(c, id) == CUDA_SUCCESS;
+}
+
+// With the device current: fetch the address the kernels must be given (the
+// host-side name of the array is not a device address) and the SM count.
+int noalloc_lookup(int dev, trd_host::NoAllocEntry *e)
+{
     void *p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
         (void)cudaGetLastError();
         return TRD_ECUDA;
     }
-    d.scratch = static_cast<int32_t *>(p);
-    if (cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    e->scratch = static_cast<int32_t *>(p);
+    if (cudaDeviceGetAttribute(&e->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         (void)cudaGetLastError();
         return TRD_ECUDA;
     }
-    g_noalloc_dev[dev] = d;  // the same values whichever thread writes first
-    __atomic_store_n(&g_noalloc_ready[dev], 1, __ATOMIC_RELEASE);
-    *out = d;
     return TRD_OK;
+}
+
+// Once per device and context (again after the context was re-created).
+int noalloc_setup(int dev, trd_host::NoAllocEntry *out)
+{
+    const int rc = trd_host::noalloc_resolve(g_noalloc_dev, kNoAllocMaxDevices, g_noalloc_mu, dev, current_ctx_id,
+                                             noalloc_lookup, out);
+    return rc ? TRD_ECUDA : TRD_OK;
 }
 
 }  // namespace
@@ -360,7 +386,7 @@ extern "C" int trd_index_build_noalloc(const trd_tracklets_t *t, float y_bin_wid
     int dev = 0;
     TRD_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kNoAllocMaxDevices) return TRD_ECUDA;
-    NoAllocDevice d;
+    trd_host::NoAllocEntry d;
     const int rc = noalloc_setup(dev, &d);
     if (rc) return rc;
 

@@ -6,15 +6,11 @@
 
 #include "../../include/trd_abi.h"
 
-constexpr int kCounterSlots = 1024;
-
 struct trd_ctx {
     int device;
     int sm_count;
     int max_threads_per_sm;
     size_t l2_bytes;
-    int32_t *counters;   // [kCounterSlots] device work counters, one per launch in flight
-    unsigned launch_seq; // next slot (atomic)
 };
 
 // Device-resident tracklet index (built by trd_index_build / rebuild).
@@ -72,7 +68,6 @@ int prepare_launch(const trd_seeds_t *seeds, const trd_params_t *p, trd_results_
 int follow_checked(trd_ctx *ctx, const trd_seeds_t *seeds, const trd_index *index, const trd_params_t *p,
                    const trd_alignment_t *align, trd_results_t *out, void *stream, const trd_launch_t *launch,
                    void *parked);
-int *next_counter(trd_ctx *ctx);
 int index_alloc(trd_ctx *ctx, int32_t capacity, float y_bin_width, int32_t n_tf, trd_index **out);
 void index_release(trd_index *x);
 int scan_blocks_for(int n);

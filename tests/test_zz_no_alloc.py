@@ -55,6 +55,9 @@ def _check_one(ctx, trk_np, w, stream):
     records = torch.full((max(n, 1), 8), float("nan"), dtype=torch.float32, device="cuda")
     stats = torch.full((4,), 12345, dtype=torch.int32, device="cuda")
     ts = trd.tracklets_struct(dev)
+    # the fills and copies above ran on torch's current stream; the call runs
+    # on its own (non-blocking) stream, so it must wait for them
+    stream.wait_stream(torch.cuda.current_stream())
     rc = fn(C.byref(ts), float(w), C.c_void_p(offsets.data_ptr()), C.c_void_p(records.data_ptr()),
             C.c_void_p(stats.data_ptr()), C.c_void_p(stream.cuda_stream))
     assert rc == trd.TRD_OK
