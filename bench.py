@@ -225,7 +225,7 @@ def cpu_baseline(tf, sample_seeds: int, reps: int = 1, align=None):
     dt1 = time.perf_counter() - t2
     O.follow(tf.seeds, tf.tracklets, tf.params, seed_index=sel[:64], n_threads=os.cpu_count(), **akw)
     matched1 = int((r1["n_trk"] >= 2).sum())
-    return dict(value=matched / dt, unit=UNIT, cores=os.cpu_count(), kind="oracle",
+    return dict(value=matched / dt, unit=UNIT, cores=os.cpu_count(), kind="oracle", oracle=r, sel=sel,
                 sample=(f"all {n} seeds" if len(sel) == n else
                         f"{len(sel)} of {n} seeds (every {n // len(sel)}th)") + " against all "
                        f"{tf.n_tracklets} tracklets; chamber bucketing included; {dt:.2f} s",
@@ -272,12 +272,70 @@ def run_reference(args):
     return 0
 
 
+def parity_report(gpu, ora, sel, n):
+    """The timed launch's results against the FP64 oracle on the same seeds,
+    element by element, with the tolerances of the parity tests."""
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from parity import compare
+    try:
+        rep = compare(gpu, ora, sel=sel)
+        ok, msg = True, None
+    except AssertionError as e:
+        rep, ok, msg = {}, False, str(e).splitlines()[0][:300]
+    out = {"seeds_compared": int(len(sel)), "of": int(n), "pass": ok,
+           "tolerance": "par 1e-4 x max(|v|, sigma), chi2 1e-3 abs, cov 1e-3 x sqrt(CiiCjj); ids, counts, "
+                        "status identical unless the oracle's decision margin < 1e-3"}
+    if msg:
+        out["failure"] = msg
+    for k in ("same_path", "exempt", "bad_path", "max_par_rel_each", "p99_par_rel", "max_chi2_abs",
+              "p99_chi2_abs", "max_cov_rel"):
+        if k in rep:
+            out[k] = rep[k]
+    if "max_par_rel_each" in out:
+        out["par_order"] = ["y", "z", "snp", "tgl", "q2pt"]
+    return out
+
+
+def served_summary(inputs, args, ctx):
+    """Config 5 at one arrival rate, 1.5x the plain path's capacity: the
+    server against the plain one-request-at-a-time path on the same stream."""
+    sizes, payloads = inputs
+    m = served_measure(payloads, [1.5], args.requests, args.slots, args.warmup, ctx=ctx)
+    p = m["points"][0]
+    return {"workload": f"served: Poisson arrivals at 1.5x the plain path's capacity "
+                        f"({p['rate_req_per_s']:.0f} requests/s), {len(payloads)} distinct timeframes, "
+                        f"seed counts log-normal (median 100k, sigma 0.8, cap 600k), N=3; "
+                        f"{args.slots} slots, 60 GB budget, pinned host buffers",
+            "unit": UNIT, "requests": p["served"]["requests"],
+            "server": {"throughput": p["served"]["throughput"], "p50_ms": p["served"]["p50_ms"],
+                       "p99_ms": p["served"]["p99_ms"]},
+            "plain": {"throughput": p["plain"]["throughput"], "p50_ms": p["plain"]["p50_ms"],
+                      "p99_ms": p["plain"]["p99_ms"]},
+            "plain_mean_service_ms": m["plain_mean_service_ms"],
+            "results_identical": m["results_identical"]}
+
+
+def batched_summary(inputs, args, ctx):
+    """Config 4: the 64-timeframe graph replay against 64 plain launches."""
+    counts, tfs = inputs
+    m = batched_measure(tfs, counts, args.steps, args.warmup, ctx=ctx)
+    return {"workload": m["config"]["workload"], "unit": UNIT, "launch": m["config"]["launch"],
+            "batched": m["batched"], "plain": m["plain"], "ratio": m["ratio"],
+            "results_identical": m["results_identical"], "clocks": m["clocks"]}
+
+
 def run_ours(args):
     import torch
     from paper_2003_03174_b300 import trd
     from synth import make_workload
 
     ws, rank, local = _dist()
+    # the served stream's and the batch's timeframes, drawn by spawn-started
+    # pools before the first CUDA call (one replica only: they are measured
+    # on N = 1)
+    extra = ws == 1 and args.workload == "timeframe" and not args.alignment
+    served_in = make_served_inputs(args.n_payloads) if extra and not args.no_served else None
+    batched_in = make_batched_inputs(args.n_tf) if extra and not args.no_batched else None
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
@@ -372,6 +430,14 @@ def run_ours(args):
         torch.distributed.barrier()
     total_s, matched_all = reduce_over_ranks(sum(step_ms) / 1e3, matched, dev)
     value = matched_all * args.steps / total_s
+    # the results of the timed launch configuration, for the parity check
+    with torch.cuda.stream(stream):
+        if graph is not None:
+            graph.run(stream)
+        else:
+            step()
+    torch.cuda.synchronize()
+    timed_results = {k: v.cpu().numpy() for k, v in res.items()}
 
     # end to end through the library's host-buffer entry point (the server):
     # pinned host inputs -> device, index + follow, results -> host, with the
@@ -475,6 +541,7 @@ def run_ours(args):
                               "ms_per_step": statistics.mean(follow_ms)},
             "refit": refit,
         }
+        line["parity"] = None
         if ws == 1 and not args.no_cpu_baseline:
             # the calibration pass's oracle runs ~50x longer per seed: 10,000 of them
             cb = cpu_baseline(tf, args.cpu_sample if wl == WORKLOAD else min(args.cpu_sample, 10_000),
@@ -482,6 +549,11 @@ def run_ours(args):
             line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
             line["cpu_baseline"]["one_thread"] = cb["one_thread"]
             line["refit"]["cpu_baseline"] = cb["refit"]
+            line["parity"] = parity_report(timed_results, cb["oracle"], cb["sel"], n)
+        if served_in is not None:
+            line["served"] = served_summary(served_in, args, ctx)
+        if batched_in is not None:
+            line["batched"] = batched_summary(batched_in, args, ctx)
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -529,17 +601,23 @@ def time_refit(ctx, res, trk, params, stream, flush, steps, warmup, hbm, fp32_pe
                                        "unit": "TFLOP/s", "frac": flops / (ms / 1e3) / 1e12 / fp32_peak}}}
 
 
-def run_batched(args):
-    """64 timeframes (seed counts log-uniform in 5k-400k, N = 3): one graph
-    replay of the batch against 64 plain launches (index rebuild + follow per
-    timeframe, each with its own resident index), same launch shape."""
-    from synth.timeframe import batched_seed_counts, concat, make_batch
-    counts = batched_seed_counts(args.n_tf)
-    tfs = make_batch(counts, seed=0, workers=os.cpu_count())  # spawn pool before any CUDA call
+def make_batched_inputs(n_tf):
+    """The batched workload's timeframes (seed counts log-uniform in 5k-400k,
+    N = 3), drawn by a spawn-started process pool."""
+    from synth.timeframe import batched_seed_counts, make_batch
+    counts = batched_seed_counts(n_tf)
+    return counts, make_batch(counts, seed=0, workers=os.cpu_count())
+
+
+def batched_measure(tfs, counts, steps, warmup, ctx=None):
+    """One graph replay of the batch against len(tfs) plain launches (index
+    rebuild + follow per timeframe, each with its own resident index), same
+    launch shape; results compared element by element."""
     import torch
     from paper_2003_03174_b300 import autotune, trd
-    dev = torch.device("cuda", 0)
-    ctx = trd.Context(0)
+    from synth.timeframe import concat
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ctx = ctx or trd.Context(dev.index)
     params = tfs[0].params
     seeds, trk, so, to = concat(tfs)
     s_all, t_all = trd.to_device(seeds, dev), trd.to_device(trk, dev)
@@ -569,27 +647,25 @@ def run_batched(args):
 
     def timed(fn):
         with torch.cuda.stream(stream):
-            for _ in range(args.warmup):
+            for _ in range(warmup):
                 fn()
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            for _ in range(args.steps):
+            for _ in range(steps):
                 fn()
             e1.record(stream)
         torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / 1e3 / args.steps
+        return e0.elapsed_time(e1) / 1e3 / steps
 
-    with ClockSampler(0) as clk:
+    with ClockSampler(dev.index) as clk:
         t_plain = timed(plain_step)
         t_batch = timed(lambda: batch.run(stream))
     matched_b = int((res_all["n_trk"] >= 2).sum().item())
     matched_p = sum(int((rv["n_trk"] >= 2).sum().item()) for _, _, _, rv in plain)
     same = all(torch.equal(rv[key], res_all[key][..., so[k]:so[k + 1]])
                for k, (_, _, _, rv) in enumerate(plain) for key in rv)
-    line = {
-        "metric": METRIC, "workload": "batched", "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+    out = {
         "config": {"workload": f"batched: {len(tfs)} timeframes, {int(so[-1])} seeds, {int(to[-1])} tracklets, "
                                f"seed counts log-uniform 5k-400k, N=3, 3-sigma road",
                    "launch": shape, "index_y_bin_cm": w, "l2": "inputs (~1.5 GB) larger than L2"},
@@ -597,10 +673,28 @@ def run_batched(args):
                     "path": "trd_batch_run: one CUDA graph (index build over all timeframes + one persistent follow)"},
         "plain": {"value": matched_p / t_plain, "ms_per_step": 1e3 * t_plain,
                   "path": f"{len(tfs)} x (trd_index_rebuild + trd_follow) on one stream"},
-        "speedup_batched_vs_plain": t_plain / t_batch,
+        "ratio": t_plain / t_batch,
         "results_identical": bool(same),
         "gpu_launches_per_step": {"batched": 8, "plain": 8 * len(tfs)},
         "clocks": clk.summary(),
+    }
+    for _, _, idx, _ in plain:
+        idx.free()
+    batch.free()
+    return out
+
+
+def run_batched(args):
+    """64 timeframes (seed counts log-uniform in 5k-400k, N = 3): one graph
+    replay of the batch against 64 plain launches."""
+    counts, tfs = make_batched_inputs(args.n_tf)  # spawn pool before any CUDA call
+    m = batched_measure(tfs, counts, args.steps, args.warmup)
+    line = {
+        "metric": METRIC, "workload": "batched", "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "config": m["config"], "batched": m["batched"], "plain": m["plain"],
+        "speedup_batched_vs_plain": m["ratio"], "results_identical": m["results_identical"],
+        "gpu_launches_per_step": m["gpu_launches_per_step"], "clocks": m["clocks"],
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -752,22 +846,25 @@ def _pct(v, q):
     return float(np.percentile(np.asarray(v), q)) if len(v) else None
 
 
-def run_served(args):
-    """Served stream: Poisson arrivals, seed counts log-normal (median 100k,
-    sigma 0.8, capped at 600k), N = 3, 60 GB admission budget.  For each
-    arrival rate (multiples of the plain path's capacity) the same request
-    sequence goes through (a) the server (trd_server_submit/poll, pinned host
-    buffers, several requests in flight) and (b) the plain path (one request
-    at a time in arrival order: copies in, index rebuild, follow, copies out,
-    synchronise).  Latency = completion - arrival."""
-    import threading
+def make_served_inputs(n_payloads):
+    """The served stream's distinct timeframes (seed counts log-normal, median
+    100k, sigma 0.8, capped at 600k; N = 3), drawn by a spawn-started pool."""
     from synth.timeframe import make_batch, served_seed_counts
-    sizes = served_seed_counts(args.n_payloads, seed=0)
-    payloads = make_batch(sizes, seed=7, workers=os.cpu_count())  # before any CUDA call
+    sizes = served_seed_counts(n_payloads, seed=0)
+    return sizes, make_batch(sizes, seed=7, workers=os.cpu_count())
+
+
+def served_measure(payloads, rates, n_requests, slots, warmup, ctx=None):
+    """For each arrival rate (multiples of the plain path's capacity) the same
+    Poisson request sequence goes through (a) the server (trd_server_submit /
+    poll, pinned host buffers, several requests in flight) and (b) the plain
+    path (one request at a time in arrival order: copies in, index rebuild,
+    follow, copies out, synchronise).  Latency = completion - arrival."""
+    import threading
     import torch
     from paper_2003_03174_b300 import trd
-    dev = torch.device("cuda", 0)
-    ctx = trd.Context(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ctx = ctx or trd.Context(dev.index)
     params = payloads[0].params
     pin = [trd.pinned_inputs(tf.seeds, tf.tracklets) for tf in payloads]
     outs = [trd.host_results(tf.n_seeds, pinned=True) for tf in payloads]
@@ -807,25 +904,24 @@ def run_served(args):
     matched = [int((torch.as_tensor(outs[j]["n_trk"]) >= 2).sum()) for j in range(len(payloads))]
     cap_plain = 1.0 / mean_service  # requests/s of the plain path
 
-    srv = trd.Server(ctx, params, max_slots=args.slots, mem_budget_bytes=60 << 30)
+    srv = trd.Server(ctx, params, max_slots=slots, mem_budget_bytes=60 << 30)
     srv_outs = [trd.host_results(tf.n_seeds, pinned=True) for tf in payloads]
     # warm-up: grow every slot's resident index, then W rounds with every
     # payload in flight (the device pool at its steady size, the pinned
     # blocks' first transfers)
     for j in range(len(payloads)):
         srv.wait(srv.submit(pin[j][0], pin[j][1], srv_outs[j]))
-    for _ in range(max(1, args.warmup)):
+    for _ in range(max(1, warmup)):
         for t in [srv.submit(pin[j][0], pin[j][1], srv_outs[j]) for j in range(len(payloads))]:
             srv.wait(t, 60_000)
     rng = np.random.Generator(np.random.Philox(key=99))
     points = []
-    for mult in args.rates:
+    for mult in rates:
         lam = mult * cap_plain
-        n_req = args.requests
+        n_req = n_requests
         arrivals = np.cumsum(rng.exponential(1.0 / lam, n_req))
         order = [int(k) % len(payloads) for k in range(n_req)]
         # (a) served
-        lat, tickets = [], []
         base = time.monotonic()  # same clock as the server's steady clock
         done_at = {}
 
@@ -856,7 +952,7 @@ def run_served(args):
                   "p99_ms": 1e3 * _pct(lat, 99), "requests": n_req}
         # (b) plain: single queue, one request at a time in arrival order
         base = time.perf_counter()
-        free_at, lat_p = 0.0, []
+        lat_p = []
         for k in range(n_req):
             wait = base + arrivals[k] - time.perf_counter()
             if wait > 0:
@@ -869,9 +965,20 @@ def run_served(args):
         points.append({"rate_req_per_s": lam, "rate_vs_plain_capacity": mult, "served": served,
                        "plain": plain})
     srv.close()
+    index.free()
     # the same request through the server alone and in the mix gives the same result
     same = all(np.array_equal(np.asarray(srv_outs[j]["tracklet_id"]), np.asarray(outs[j]["tracklet_id"]))
                for j in range(len(payloads)))
+    return {"points": points, "plain_mean_service_ms": 1e3 * mean_service, "results_identical": bool(same)}
+
+
+def run_served(args):
+    """Served stream: Poisson arrivals, seed counts log-normal (median 100k,
+    sigma 0.8, capped at 600k), N = 3, 60 GB admission budget, arrival rates
+    swept to saturation."""
+    sizes, payloads = make_served_inputs(args.n_payloads)  # before any CUDA call
+    m = served_measure(payloads, args.rates, args.requests, args.slots, args.warmup)
+    points = m["points"]
     sat = max(points, key=lambda p: p["served"]["throughput"])
     line = {
         "metric": METRIC, "workload": "served", "unit": UNIT, "n_gpus": 1, "dtype": "f32",
@@ -879,12 +986,12 @@ def run_served(args):
         "config": {"workload": f"served: Poisson arrivals; {len(payloads)} distinct timeframes, seed counts "
                                f"log-normal (median 100k, sigma 0.8, cap 600k), mean {int(np.mean(sizes))} "
                                f"seeds; N=3, 3-sigma road; 60 GB budget; {args.slots} slots; pinned host buffers",
-                   "plain_mean_service_ms": 1e3 * mean_service},
+                   "plain_mean_service_ms": m["plain_mean_service_ms"]},
         "saturation": {"served_throughput": sat["served"]["throughput"],
                        "served_p50_ms": sat["served"]["p50_ms"], "served_p99_ms": sat["served"]["p99_ms"],
                        "plain_throughput": max(p["plain"]["throughput"] for p in points)},
         "sweep": points,
-        "results_identical_served_vs_plain": bool(same),
+        "results_identical_served_vs_plain": m["results_identical"],
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -912,6 +1019,8 @@ def main():
                     help="misaligned chambers, per-tracklet radii and a field map (trd_follow_aligned)")
     ap.add_argument("--association", type=int, default=0,
                     help="interactions per timeframe (per-interaction association); 0 = off")
+    ap.add_argument("--no-served", action="store_true", help="leave the served stream out of the default line")
+    ap.add_argument("--no-batched", action="store_true", help="leave the batch out of the default line")
     ap.add_argument("--n-payloads", type=int, default=16)
     ap.add_argument("--requests", type=int, default=64)
     ap.add_argument("--slots", type=int, default=4)

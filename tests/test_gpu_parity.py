@@ -1,9 +1,10 @@
 """Parity of the CUDA follower (through the C ABI) with the FP64 oracle.
 
 Element-by-element comparison on the same seeded inputs at sizes the oracle
-finishes in seconds, sampled comparison at the full workload sizes in the
-launch configuration the benchmark times, and the edge cases (empty and
-invalid inputs, ragged tails, every hypothesis count and mode).
+finishes in seconds, every seed of the full timeframe (and every 20th seed of
+the calibration pass) in the launch configuration the benchmark times, and
+the edge cases (empty and invalid inputs, ragged tails, every hypothesis count
+and mode).
 """
 import math
 
@@ -192,29 +193,50 @@ def test_event_rotated_by_one_sector(ctx):
     compare(g, o)
 
 
-def test_full_timeframe_sampled_parity(ctx):
-    """200k seeds, ~1M tracklets, N = 1, 3 sigma road: the benchmark's launch;
-    the oracle follows a sample of 2500 seeds against all tracklets."""
+def _bench_step_results(ctx, tf):
+    """The benchmark's step on a workload: the autotuned launch shape and bin
+    width, one CUDA-graph replay of index rebuild + follow (the library's
+    single-timeframe batch)."""
+    from paper_2003_03174_b300 import autotune, trd
+    s, t = trd.to_device(tf.seeds), trd.to_device(tf.tracklets)
+    tuned = autotune.tune(ctx, s, t, tf.params, cache=None, reps=3)
+    shape = {k: tuned[k] for k in ("lanes_per_track", "block_threads", "min_blocks_per_sm")}
+    res = trd.alloc_results(tf.n_seeds)
+    batch = ctx.batch_create(s, t, [0, tf.n_seeds], [0, tf.n_tracklets], tf.params, res,
+                             y_bin_width=tuned["y_bin_width"], **shape)
+    stream = torch.cuda.Stream()
+    for _ in range(2):  # a replay over the previous replay's buffers too
+        batch.run(stream)
+    torch.cuda.synchronize()
+    out = to_numpy(res)
+    batch.free()
+    return out
+
+
+def test_full_timeframe_parity_every_seed(ctx):
+    """200k seeds, ~1M tracklets, N = 1, 3 sigma road: every seed of the
+    benchmark's timed step against the oracle following all of them."""
     tf = make_workload("timeframe")
-    g, _ = run_gpu(ctx, tf)
-    rng = np.random.default_rng(0)
-    sel = np.unique(np.concatenate([np.arange(0, tf.n_seeds, 100), rng.integers(0, tf.n_seeds, 500),
-                                    np.arange(tf.n_seeds - 37, tf.n_seeds)]))
-    o = O.follow(tf.seeds, tf.tracklets, tf.params, seed_index=sel)
-    compare(g, o, sel=sel)
+    g = _bench_step_results(ctx, tf)
+    o = O.follow(tf.seeds, tf.tracklets, tf.params)
+    rep = compare(g, o)
+    assert rep["same_path"] >= 0.995 * tf.n_seeds
     # Sec. 3.1: purity ~1 in pp, falling to ~0.9 for low-momentum tracks at
     # Pb-Pb density; this timeframe is Pb-Pb-like (1M tracklets, 30% noise)
     ep = efficiency_purity(g["tracklet_id"], tf.truth_ids)
     assert ep["efficiency_reachable"] > 0.95 and ep["purity"] > 0.85
 
 
-def test_full_calibration_sampled_parity(ctx):
-    """450k seeds with the coherent y distortion, 5 sigma road, N = 6."""
+def test_full_calibration_parity(ctx):
+    """450k seeds with the coherent y distortion, 5 sigma road, N = 6, in the
+    benchmark's step; the oracle follows 22,500 of them (every 20th) against
+    all tracklets."""
     tf = make_workload("calibration")
-    g, _ = run_gpu(ctx, tf)
-    sel = np.arange(0, tf.n_seeds, 1500)
+    g = _bench_step_results(ctx, tf)
+    sel = np.arange(0, tf.n_seeds, 20)
     o = O.follow(tf.seeds, tf.tracklets, tf.params, seed_index=sel)
-    compare(g, o, sel=sel)
+    rep = compare(g, o, sel=sel)
+    assert rep["same_path"] >= 0.99 * sel.size
 
 
 @pytest.mark.parametrize("n_hyp,shapes", [(6, ((8, 3), (32, 3), (32, 4), (8, 4))),
