@@ -133,10 +133,10 @@ TRD_API int trd_ctx_destroy(trd_ctx_t *ctx);
 TRD_API int trd_ctx_sm_count(const trd_ctx_t *ctx);
 
 /* ---- tracklet index (Sec. 3: "all tracklets inside a search road") --------
- * trd_index_build: bucket the tracklets by (chamber, y bin, pad row) with a
- * counting sort on `stream`, and record the largest vyy and vzz.  The pad
- * rows of one (chamber, y bin) are adjacent, so a road query is one
- * contiguous range per y bin.  y_bin_width (cm, > 0; 0 selects 2 cm)
+ * trd_index_build: bucket the tracklets by (chamber, pad row, y bin) with a
+ * counting sort on `stream`, and record the largest vyy and vzz.  The y bins
+ * of one (chamber, pad row) are adjacent, so a road query is one contiguous
+ * range per pad row.  y_bin_width (cm, >= 0.05; 0 selects 2 cm)
  * sets the bin size.  The library allocates and owns the index (*out, freed
  * by trd_index_free); the input arrays may be reused once `stream` has passed
  * the build.  Errors: TRD_EINVAL, TRD_ENOMEM, TRD_ECUDA.                     */
@@ -160,8 +160,8 @@ TRD_API int trd_index_info(const trd_index_t *index, int32_t *n_indexed, int32_t
 
 /* Copies the index to host memory (synchronises with its build stream), for
  * inspection and tests.  offsets: n_buckets + 1 int32 (bucket b holds
- * entries offsets[b] .. offsets[b+1]-1; bucket = (chamber * n_ybins +
- * y bin) * 18 + pad row); ids: n_indexed int32 input indices in bucket order.
+ * entries offsets[b] .. offsets[b+1]-1; bucket = (chamber * 18 + pad row) *
+ * n_ybins + y bin); ids: n_indexed int32 input indices in bucket order.
  * Either pointer may be NULL.  Host pointers, caller-owned.                 */
 TRD_API int trd_index_copy_out(const trd_index_t *index, int32_t *offsets, int32_t *ids);
 
@@ -172,7 +172,7 @@ TRD_API int trd_index_copy_out(const trd_index_t *index, int32_t *offsets, int32
  * the device).  It runs the same kernels as trd_index_build on the current
  * device and writes the index into the caller's device buffers:
  *   offsets  n_buckets + 1 int32, n_buckets = 540 * 18 * ceil(132 / w)
- *            (bucket = (chamber * n_ybins + y bin) * 18 + pad row)
+ *            (bucket = (chamber * 18 + pad row) * n_ybins + y bin)
  *   records  8 floats per tracklet (16-byte aligned): {y, z, dy, input index
  *            as int32 bits}, {vyy, vzz, vyz, trigger as int32 bits (-1 when
  *            the tracklets carry none)}, in bucket order; the first

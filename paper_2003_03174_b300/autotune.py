@@ -55,7 +55,7 @@ def _time(fn, stream, reps):
 
 
 def tune(ctx: trd.Context, seeds: dict, tracklets: dict, params: dict,
-         bin_widths=(1.0, 2.0, 4.0), reps: int = 7, cache: str | None = DEFAULT_CACHE,
+         bin_widths=(0.5, 1.0, 2.0), reps: int = 7, cache: str | None = DEFAULT_CACHE,
          force: bool = False) -> dict:
     """Return {'y_bin_width', 'lanes_per_track', 'block_threads',
     'min_blocks_per_sm', 'ms', 'table'} for this workload."""

@@ -181,13 +181,13 @@ struct ExtList {
 
 // Road query + candidate tests for one hypothesis at layer l (Sec. 3).
 // The road bounds z_tl to z +- Rz (pad rows r_lo..r_hi) and the measured y to
-// y +- (W + |tan tau| Rz) (y bins b_lo..b_hi); each y bin is one contiguous
-// range of the index over those rows.  The candidates of the first two bins
-// form one list: their {y, z} are read eight at a time (one dependent L2
-// round trip, which also brings each 32-byte record into L1), a bit mask
-// keeps those inside the road's y/z bounds, and only those get the full test
-// (record read again from L1).  More than two bins (very wide roads) are
-// handled the same way, two at a time.
+// y +- (W + |tan tau| Rz) (y bins b_lo..b_hi); each pad row is one contiguous
+// range of the index over those bins.  The candidates of two rows form one
+// list: their {y, z} are read eight at a time (one dependent L2 round trip,
+// which also brings each 32-byte record into L1), a bit mask keeps those
+// inside the road's y/z bounds, and only those get the full test (record read
+// again from L1).  More than two rows (long z roads) are handled the same
+// way, two at a time.
 // Road geometry of a hypothesis for the EXT kernels: its radius and the
 // straight-line slopes dy/dx = tan(phi), dz/dx = tan(lambda)/cos(phi).
 struct LinExt {
@@ -227,6 +227,11 @@ __device__ __forceinline__ void full_test(int pos, const IndexView &ix, float tt
     L.insert(score + chi2, parent, __float_as_int(a.w), pos, chi2);
 }
 
+#ifndef TRD_SCAN_CHUNK
+#define TRD_SCAN_CHUNK 12
+#endif
+constexpr int kScanChunk = TRD_SCAN_CHUNK;  // candidates whose {y, z} loads are in flight together
+
 template <int NH, bool EXT>
 __device__ void scan_candidates(const TrackState &s, int l, int chamber, int cbase, float score, const Params &P,
                                 const IndexView &ix, float vyy_max_in, float vzz_max, float dx_max, int trig,
@@ -262,30 +267,36 @@ __device__ void scan_candidates(const TrackState &s, int l, int chamber, int cba
     const float half = W + fabsf(tt) * Rz + 1e-3f + 1e-6f * fabsf(yh);
     const int b_lo = ybin_of(yh - half, ix.inv_w, ix.nb), b_hi = ybin_of(yh + half, ix.inv_w, ix.nb);
     const float2 *yz = reinterpret_cast<const float2 *>(ix.rec);  // {y, z} of record p at yz[4 p]
-    for (int b = b_lo; b <= b_hi; b += 2) {
-        const int base = bucket_of(cbase + chamber, b, 0, ix.nb);
-        const bool two = b + 1 <= b_hi;
-        const int beg0 = __ldg(&ix.offsets[base + r_lo]);
-        const int end0 = __ldg(&ix.offsets[base + r_hi + 1]);
-        int beg1 = 0, end1 = 0;
-        if (two) {
-            beg1 = __ldg(&ix.offsets[base + kRowsPerStack + r_lo]);
-            end1 = __ldg(&ix.offsets[base + kRowsPerStack + r_hi + 1]);
+    const int nb = ix.nb;
+    for (int r = r_lo; r <= r_hi; r += 3) {
+        // up to three pad rows: their six bounds are loaded together
+        const int base = bucket_of(cbase + chamber, 0, r, nb);
+        const int beg0 = __ldg(&ix.offsets[base + b_lo]);
+        const int end0 = __ldg(&ix.offsets[base + b_hi + 1]);
+        int beg1 = 0, end1 = 0, beg2 = 0, end2 = 0;
+        if (r + 1 <= r_hi) {
+            beg1 = __ldg(&ix.offsets[base + nb + b_lo]);
+            end1 = __ldg(&ix.offsets[base + nb + b_hi + 1]);
+        }
+        if (r + 2 <= r_hi) {
+            beg2 = __ldg(&ix.offsets[base + 2 * nb + b_lo]);
+            end2 = __ldg(&ix.offsets[base + 2 * nb + b_hi + 1]);
         }
         const int n0 = end0 - beg0;
-        const int n = n0 + (end1 - beg1);
+        const int n01 = n0 + (end1 - beg1);
+        const int n = n01 + (end2 - beg2);
 #pragma unroll 1
-        for (int j0 = 0; j0 < n; j0 += 8) {
-            float2 c[8];
+        for (int j0 = 0; j0 < n; j0 += kScanChunk) {
+            float2 c[kScanChunk];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
+            for (int u = 0; u < kScanChunk; ++u) {
                 const int j = j0 + u;
-                const int pos = j < n0 ? beg0 + j : beg1 + (j - n0);
+                const int pos = j < n0 ? beg0 + j : (j < n01 ? beg1 + (j - n0) : beg2 + (j - n01));
                 c[u] = j < n ? __ldg(&yz[4 * pos]) : make_float2(INFINITY, INFINITY);
             }
             unsigned mask = 0;
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
+            for (int u = 0; u < kScanChunk; ++u) {
                 const float ry = (__fsub_rn(c[u].x, yh) - yl) + tt * (z - c[u].y);
                 const float rz = c[u].y - z;
                 if (fabsf(ry) <= W && fabsf(rz) <= Rz) mask |= 1u << u;
@@ -294,7 +305,7 @@ __device__ void scan_candidates(const TrackState &s, int l, int chamber, int cba
                 const int u = __ffs(mask) - 1;
                 mask &= mask - 1u;
                 const int j = j0 + u;
-                const int pos = j < n0 ? beg0 + j : beg1 + (j - n0);
+                const int pos = j < n0 ? beg0 + j : (j < n01 ? beg1 + (j - n0) : beg2 + (j - n01));
                 full_test<NH, EXT>(pos, ix, tt, z, yh, yl, n2, syy_trk, syz_trk, c11, vyy_res, P.resmode, dy_pred,
                                    gate, P.cut, score, 0, trig, e, L);
             }
@@ -370,17 +381,23 @@ __device__ void scan_group(bool mine, const TrackState &s, int l, int chamber, i
             he.fr = __shfl_sync(gmask, e.fr, h, G);
             he.tr = __shfl_sync(gmask, e.tr, h, G);
         }
-        for (int b = hb_lo; b <= hb_hi; b += 2) {
-            const int base = hbase + b * kRowsPerStack;
-            const int beg0 = __ldg(&ix.offsets[base + hr_lo]);
-            const int end0 = __ldg(&ix.offsets[base + hr_hi + 1]);
-            int beg1 = 0, end1 = 0;
-            if (b + 1 <= hb_hi) {
-                beg1 = __ldg(&ix.offsets[base + kRowsPerStack + hr_lo]);
-                end1 = __ldg(&ix.offsets[base + kRowsPerStack + hr_hi + 1]);
+        for (int r = hr_lo; r <= hr_hi; r += 3) {
+            // up to three pad rows: their six bounds are loaded together
+            const int base = hbase + r * ix.nb;
+            const int beg0 = __ldg(&ix.offsets[base + hb_lo]);
+            const int end0 = __ldg(&ix.offsets[base + hb_hi + 1]);
+            int beg1 = 0, end1 = 0, beg2 = 0, end2 = 0;
+            if (r + 1 <= hr_hi) {
+                beg1 = __ldg(&ix.offsets[base + ix.nb + hb_lo]);
+                end1 = __ldg(&ix.offsets[base + ix.nb + hb_hi + 1]);
+            }
+            if (r + 2 <= hr_hi) {
+                beg2 = __ldg(&ix.offsets[base + 2 * ix.nb + hb_lo]);
+                end2 = __ldg(&ix.offsets[base + 2 * ix.nb + hb_hi + 1]);
             }
             const int n0 = end0 - beg0;
-            const int n = n0 + (end1 - beg1);
+            const int n01 = n0 + (end1 - beg1);
+            const int n = n01 + (end2 - beg2);
             // lane q takes candidates q, q + G, ...: ceil(n / G) of them, four at a time
             const int per_lane = (n + G - 1) / G;
             for (int u0 = 0; u0 < per_lane; u0 += 4) {
@@ -388,7 +405,7 @@ __device__ void scan_group(bool mine, const TrackState &s, int l, int chamber, i
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int j = q + G * (u0 + u);
-                    const int pos = j < n0 ? beg0 + j : beg1 + (j - n0);
+                    const int pos = j < n0 ? beg0 + j : (j < n01 ? beg1 + (j - n0) : beg2 + (j - n01));
                     c[u] = j < n ? __ldg(&yzs[4 * pos]) : make_float2(INFINITY, INFINITY);
                 }
                 unsigned mask = 0;
@@ -402,7 +419,7 @@ __device__ void scan_group(bool mine, const TrackState &s, int l, int chamber, i
                     const int u = __ffs(mask) - 1;
                     mask &= mask - 1u;
                     const int j = q + G * (u0 + u);
-                    const int pos = j < n0 ? beg0 + j : beg1 + (j - n0);
+                    const int pos = j < n0 ? beg0 + j : (j < n01 ? beg1 + (j - n0) : beg2 + (j - n01));
                     full_test<NH, EXT>(pos, ix, tt, hz, hyh, hyl, n2, hsyy, hsyz, hc11, hvres, P.resmode, hdyp,
                                        hgate, P.cut, hscore, h, trig, he, L);
                 }
@@ -953,6 +970,41 @@ k_follow(SeedsView sv, IndexView ix, Params P, ParkedView pk, int *counter)
     }
 }
 
+// Layer-synchronous follower for one hypothesis per seed (G = 1): a warp
+// takes 32 consecutive sorted positions (seeds of similar momentum) and
+// carries its 32 seeds through the six layers together, so every lane runs
+// the same layer's code at the same time: the seed loads, the result stores
+// and the layer's transport, road set-up and update are issued once per warp
+// instead of once per lane whose seed happens to be at that step.  A lane
+// whose seed ended waits for the warp's last layer.
+template <int MINB, bool EXT>
+__global__ void __launch_bounds__(128, MINB)
+k_follow_sync(SeedsView sv, IndexView ix, Params P, ParkedView pk, int *counter)
+{
+    wait_prior_grid();
+    extern __shared__ float smem[];
+    float *sm = smem + threadIdx.x;  // the snapshot of this thread's state before the layer's transport
+    const int stride = blockDim.x;
+    const int lane = threadIdx.x & 31;
+    const float vyy_max = __uint_as_float(__ldg(&ix.stats[0]));
+    const float vzz_max = __uint_as_float(__ldg(&ix.stats[1]));
+    const float dx_max = EXT && ix.recx ? __uint_as_float(__ldg(&ix.stats[3])) : 0.0f;
+    for (;;) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(counter, 32);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= sv.n) break;
+        const int pos = base + lane;
+        Lane H;
+        int i;
+        bool have = pos < sv.n && start_seed<1>(pos, 0, sv, pk, H, i);
+        for (int l = 0; l < kLayers && __any_sync(0xffffffffu, have); ++l) {
+            if (have && layer_step<1, 1, EXT>(pos, l, 0, 0u, ix, P, pk.rec, sm, stride, vyy_max, vzz_max, dx_max, H))
+                have = false;
+        }
+    }
+}
+
 // The staged results to the seeds' input positions: thread i reads its
 // seed's 128-byte record and writes the result arrays with full lines.  Seeds
 // that ended in k_seed_prepare (inv -1) already have their results.
@@ -1014,8 +1066,13 @@ static int launch(const trd_ctx *ctx, const SeedsView &sv, const IndexView &ix, 
     if (sv.n == 0) return TRD_OK;
     const int groups = block / G;
     const size_t smem = sizeof(float) * 24 * groups;
+    void (*kernel)(SeedsView, IndexView, Params, ParkedView, int *);
+    if constexpr (G == 1)
+        kernel = k_follow_sync<MINB, EXT>;
+    else
+        kernel = k_follow<G, NH, MINB, EXT>;
     int per_sm = 0;
-    TRD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_follow<G, NH, MINB, EXT>, block, smem));
+    TRD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem));
     per_sm = per_sm > 0 ? per_sm : 1;
     const long long need = (static_cast<long long>(sv.n) + groups - 1) / groups;
     const int grid = static_cast<int>(std::min<long long>(need, static_cast<long long>(ctx->sm_count) * per_sm));
@@ -1026,7 +1083,7 @@ static int launch(const trd_ctx *ctx, const SeedsView &sv, const IndexView &ix, 
         if (rc) return rc;
     }
     // the follower and the gather start while their predecessor drains
-    TRD_CUDA_TRY(launch_after(k_follow<G, NH, MINB, EXT>, dim3(grid), dim3(block), smem, s, sv, ix, P, pk, counter));
+    TRD_CUDA_TRY(launch_after(kernel, dim3(grid), dim3(block), smem, s, sv, ix, P, pk, counter));
     TRD_CUDA_TRY(launch_after(k_results_gather, dim3((sv.n + 255) / 256), dim3(256), 0, s, sv.n, pk, o));
     return TRD_OK;
 }

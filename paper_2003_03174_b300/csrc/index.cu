@@ -1,7 +1,7 @@
 // index.cu -- the tracklet index (Sec. 3: "all tracklets inside a search road
 // based on the covariance matrices of the tracks are considered").
 //
-// Tracklets are bucketed by (chamber, y bin, pad row) with a counting sort:
+// Tracklets are bucketed by (chamber, pad row, y bin) with a counting sort:
 //   1. count: bucket of each tracklet; a fire-and-forget atomic add on the
 //      bucket's counter (nothing waits for its return); block-reduced maxima
 //      of vyy and vzz bound the road width.
@@ -12,8 +12,8 @@
 //      position, where its 32-byte record goes; when every tracklet is placed,
 //      offsets[b + 1] holds the end of bucket b, i.e. the start of bucket
 //      b + 1, so offsets[b] is the first position of bucket b for every b.
-// The pad rows of one (chamber, y bin) are adjacent, so the follower reads
-// one contiguous range per y bin.  Order inside a bucket is not defined;
+// The y bins of one (chamber, pad row) are adjacent, so the follower reads
+// one contiguous range per pad row.  Order inside a bucket is not defined;
 // the follower's selection does not depend on it (ties break on tracklet id).
 #include <cuda.h>
 #include <cuda_runtime.h>

@@ -191,11 +191,12 @@ __device__ __forceinline__ int row_of_z(float z, float z_lo)
     return static_cast<int>(u);
 }
 
-// Bucket order: chamber, then y bin, then pad row, so that the pad rows of one
-// y bin are adjacent and a road query reads one contiguous range per y bin.
+// Bucket order: chamber, then pad row, then y bin, so that the y bins of one
+// pad row are adjacent and a road query reads one contiguous range per pad
+// row, however narrow the bins.
 __device__ __forceinline__ int bucket_of(int chamber, int ybin, int row, int nb)
 {
-    return (chamber * nb + ybin) * kRowsPerStack + row;
+    return (chamber * kRowsPerStack + row) * nb + ybin;
 }
 
 // Timeframe of element i in a batch laid out by offsets off[0..n_tf]

@@ -118,10 +118,10 @@ def _bucket_reference(trk, w):
     inv_w = f32(1.0) / f32(w)
     nb = int(math.ceil(np.float32(132.0) / np.float32(w)))
     yb = np.clip(np.floor((trk["y"] + f32(66.0)).astype(f32) * inv_w), 0, nb - 1).astype(np.int64)
-    return (ch * nb + yb) * 18 + row, nb
+    return (ch * 18 + row) * nb + yb, nb
 
 
-@pytest.mark.parametrize("w", [2.0, 0.7])
+@pytest.mark.parametrize("w", [2.0, 0.7, 0.25])
 def test_index_buckets_are_exact(ctx, w):
     tf = make_workload("timeframe", seed=11, n_seeds=30_000)
     from paper_2003_03174_b300 import trd
