@@ -70,13 +70,13 @@ REFIT_FLOPS_PER_LAYER = 460
 # from one ncu capture (39.05 MB read, 0.76 MB written: the 20 MB of output
 # is still in L2 when the kernel ends), valid only for the source measured.
 REFIT_TRAFFIC = {"source_sha256_16": "d0afd33335175e46", "bytes": 39.81e6}
-# DRAM bytes (read + write) of one trd_follow call on this workload from ncu
-# captures of its four kernels (k_seed_key 0.82 MB, k_seed_prepare 24.43 MB,
-# k_follow_sync 63.63 MB, k_results_gather 26.43 MB; ncu empties the caches
+# DRAM bytes (read + write) of one trd_follow call on this workload from one
+# ncu capture per kernel (k_seed_key 0.82 MB, k_seed_prepare 23.74 MB,
+# k_follow_sync 64.93 MB, k_results_gather 26.56 MB; ncu empties the caches
 # before each kernel, so the gather's reads of the staged results, L2 hits in
 # a plain run, count here), valid only for the kernel source it was measured
 # on: reported as null once follow.cu, trd_device.cuh or track_model.cuh change.
-FOLLOW_TRAFFIC = {"source_sha256_16": "9432d9d9481c0b9a", "bytes": 115.31e6}
+FOLLOW_TRAFFIC = {"source_sha256_16": "9432d9d9481c0b9a", "bytes": 116.05e6}
 # DRAM bytes (read 207.63 MB + write 13.23 MB) of one k_residuals launch on the
 # 100,000-track map from one ncu capture; the 450,000-track map holds ~3 GB on
 # the device and is not captured, so the figure is reported for the captured
