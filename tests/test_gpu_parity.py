@@ -318,6 +318,53 @@ def test_one_momentum_bin(ctx, n):
     compare(g, o)
 
 
+@pytest.mark.parametrize("n", [31, 32, 33, 95])
+def test_ragged_warps_of_seeds(ctx, n):
+    """One hypothesis: a warp carries 32 consecutive sorted seeds through the
+    layers together; seed counts around a warp's size leave the last warp
+    partly empty."""
+    tf = make_timeframe(n, seed=40 + n, noise=0.3)
+    g, _ = run_gpu(ctx, tf)
+    compare(g, O.follow(tf.seeds, tf.tracklets, tf.params))
+
+
+def test_a_warp_of_seeds_that_all_end_early(ctx):
+    """40 seeds with |q/pT| = 40 c/GeV (the helix cannot reach the layers)
+    sort into the first momentum bin, so one warp holds only seeds that end
+    at the first layer while the other warps follow ordinary seeds; seeds
+    that run out of their missing-layer budget early (no tracklets at all in
+    their chambers) end at layer 2 beside seeds that reach layer 5."""
+    tf = make_timeframe(600, seed=44, noise=0.3)
+    s = {k: v.copy() for k, v in tf.seeds.items()}
+    s["q2pt"][:40] = np.where(np.arange(40) % 2 == 0, 40.0, -40.0).astype(np.float32)
+    t = {k: v.copy() for k, v in tf.tracklets.items()}
+    # no tracklets in the sectors of seeds 100..299's frames: most of them
+    # spend their two missing layers and stop
+    sec = (((s["alpha"][100:300].astype(np.float64) + math.pi) % (2 * math.pi)) / (2 * math.pi / 18)).astype(int)
+    drop = np.isin(t["chamber"] // 30, np.unique(sec)[:3])
+    t = {k: v[~drop] for k, v in t.items()}
+    g, _ = run_gpu(ctx, tf, seeds=s, tracklets=t)
+    o = O.follow(s, t, tf.params)
+    assert np.all(g["status"][:40] == O.STATUS_PROP_FAIL)
+    assert (o["n_miss"] == 2).sum() > 20 and (o["status"] != 0).sum() > 40
+    compare(g, o)
+
+
+def test_launch_shapes_do_not_change_one_hypothesis_results(ctx):
+    """Block sizes and register budgets of the layer-synchronous follower
+    (and so the number of warps resident per SM) change nothing."""
+    tf = make_workload("timeframe", seed=45, n_seeds=6000)
+    from paper_2003_03174_b300 import trd
+    s, t = trd.to_device(tf.seeds), trd.to_device(tf.tracklets)
+    idx = ctx.index_build(t)
+    outs = [to_numpy(ctx.follow(s, idx, tf.params, lanes_per_track=1, block_threads=b, min_blocks_per_sm=m))
+            for b, m in ((64, 4), (64, 6), (128, 5), (128, 8))]
+    torch.cuda.synchronize()
+    for o in outs[1:]:
+        for k in outs[0]:
+            np.testing.assert_array_equal(o[k], outs[0][k], err_msg=k)
+
+
 def test_resident_index_rebuilds_stay_exact(ctx):
     """A resident index rebuilt with different tracklet sets in turn (the
     bucket counters return to zero after every build): each build's offsets

@@ -67,8 +67,8 @@ def test_budget_admits_one_request_at_a_time(ctx, tfs):
     big = max(tfs, key=lambda t: t.n_seeds)
     # the server charges a request's inputs and results plus its stream's index:
     # leave room for the index and one and a half requests, never for two
-    # (with the follower's scratch: 136 B per seed + 512 B)
-    io = 220 * big.n_seeds + 36 * big.n_tracklets + 7 * 256 + 136 * big.n_seeds + 512 + 256
+    # (with the follower's scratch: 136 B per seed + 528 B)
+    io = 220 * big.n_seeds + 36 * big.n_tracklets + 7 * 256 + 136 * big.n_seeds + 528 + 256
     index = 40 * big.n_tracklets + 8 * 540 * 18 * 66 + 4096
     one = index + io + io // 2
     srv = trd.Server(ctx, big.params, max_slots=4, mem_budget_bytes=one)
