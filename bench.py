@@ -67,9 +67,9 @@ REFIT_BYTES_PER_TRACKLET = 24
 # ~250, material ~60)
 REFIT_FLOPS_PER_LAYER = 460
 # DRAM bytes (read + write) of one k_refit launch on the 200k-seed timeframe
-# from one ncu capture (39.05 MB read, 0.76 MB written: the 20 MB of output
+# from one ncu capture (39.06 MB read, 0.82 MB written: the 20 MB of output
 # is still in L2 when the kernel ends), valid only for the source measured.
-REFIT_TRAFFIC = {"source_sha256_16": "d0afd33335175e46", "bytes": 39.81e6}
+REFIT_TRAFFIC = {"source_sha256_16": "89b8201dbc53c40e", "bytes": 39.88e6}
 # DRAM bytes (read + write) of one trd_follow call on this workload from one
 # ncu capture per kernel (k_seed_key 0.82 MB, k_seed_prepare 23.74 MB,
 # k_follow_sync 64.93 MB, k_results_gather 26.56 MB; ncu empties the caches
@@ -77,11 +77,11 @@ REFIT_TRAFFIC = {"source_sha256_16": "d0afd33335175e46", "bytes": 39.81e6}
 # a plain run, count here), valid only for the kernel source it was measured
 # on: reported as null once follow.cu, trd_device.cuh or track_model.cuh change.
 FOLLOW_TRAFFIC = {"source_sha256_16": "9432d9d9481c0b9a", "bytes": 116.05e6}
-# DRAM bytes (read 207.63 MB + write 13.23 MB) of one k_residuals launch on the
+# DRAM bytes (read 206.49 MB + write 12.93 MB) of one k_residuals launch on the
 # 100,000-track map from one ncu capture; the 450,000-track map holds ~3 GB on
 # the device and is not captured, so the figure is reported for the captured
 # size only (the voxel array's write-back does not grow with the tracks).
-RES_TRAFFIC = {"source_sha256_16": "3fa7da3ab857720a", "bytes": 220.86e6, "tracks": 100_000}
+RES_TRAFFIC = {"source_sha256_16": "51aa59957a720dce", "bytes": 219.42e6, "tracks": 100_000}
 RES_SOURCES = ("residuals.cu", "trd_device.cuh", "track_model.cuh")
 
 
