@@ -182,12 +182,12 @@ struct ExtList {
 // Road query + candidate tests for one hypothesis at layer l (Sec. 3).
 // The road bounds z_tl to z +- Rz (pad rows r_lo..r_hi) and the measured y to
 // y +- (W + |tan tau| Rz) (y bins b_lo..b_hi); each pad row is one contiguous
-// range of the index over those bins.  The candidates of two rows form one
-// list: their {y, z} are read eight at a time (one dependent L2 round trip,
-// which also brings each 32-byte record into L1), a bit mask keeps those
-// inside the road's y/z bounds, and only those get the full test (record read
-// again from L1).  More than two rows (long z roads) are handled the same
-// way, two at a time.
+// range of the index over those bins.  The candidates of up to three rows
+// form one list: the first halves of their records, {y, z, dy, id}, are read
+// eight at a time (one dependent L2 round trip, which also brings each 32-byte
+// record into L1), a bit mask keeps those inside the road's y/z bounds and
+// the deflection gate, and only those get the full test (record read again
+// from L1).  Longer z roads are handled the same way, three rows at a time.
 // Road geometry of a hypothesis for the EXT kernels: its radius and the
 // straight-line slopes dy/dx = tan(phi), dz/dx = tan(lambda)/cos(phi).
 struct LinExt {
@@ -200,6 +200,8 @@ __device__ __forceinline__ void full_test(int pos, const IndexView &ix, float tt
                                           int resmode, float dy_pred, float gate, float cut, float score,
                                           int parent, int trig, const LinExt &e, ExtList<NH> &L)
 {
+    // (the first half is an L1 hit: the pre-filter read it; taking it from
+    // the pre-filter's registers would index them by a run-time slot)
     const float4 a = __ldg(&ix.rec[2 * pos]);
     const float4 v = __ldg(&ix.rec[2 * pos + 1]);
     // per-interaction association (Sec. 4): other interactions' tracklets are not candidates
@@ -227,10 +229,7 @@ __device__ __forceinline__ void full_test(int pos, const IndexView &ix, float tt
     L.insert(score + chi2, parent, __float_as_int(a.w), pos, chi2);
 }
 
-#ifndef TRD_SCAN_CHUNK
-#define TRD_SCAN_CHUNK 12
-#endif
-constexpr int kScanChunk = TRD_SCAN_CHUNK;  // candidates whose {y, z} loads are in flight together
+constexpr int kScanChunk = 8;  // candidates whose loads are in flight together
 
 template <int NH, bool EXT>
 __device__ void scan_candidates(const TrackState &s, int l, int chamber, int cbase, float score, const Params &P,
@@ -266,7 +265,6 @@ __device__ void scan_candidates(const TrackState &s, int l, int chamber, int cba
     const int r_lo = row_of_z(z - Rz, zlo), r_hi = row_of_z(z + Rz, zlo);
     const float half = W + fabsf(tt) * Rz + 1e-3f + 1e-6f * fabsf(yh);
     const int b_lo = ybin_of(yh - half, ix.inv_w, ix.nb), b_hi = ybin_of(yh + half, ix.inv_w, ix.nb);
-    const float2 *yz = reinterpret_cast<const float2 *>(ix.rec);  // {y, z} of record p at yz[4 p]
     const int nb = ix.nb;
     for (int r = r_lo; r <= r_hi; r += 3) {
         // up to three pad rows: their six bounds are loaded together
@@ -287,19 +285,22 @@ __device__ void scan_candidates(const TrackState &s, int l, int chamber, int cba
         const int n = n01 + (end2 - beg2);
 #pragma unroll 1
         for (int j0 = 0; j0 < n; j0 += kScanChunk) {
-            float2 c[kScanChunk];
+            float4 c[kScanChunk];  // the records' first halves {y, z, dy, id}
 #pragma unroll
             for (int u = 0; u < kScanChunk; ++u) {
                 const int j = j0 + u;
                 const int pos = j < n0 ? beg0 + j : (j < n01 ? beg1 + (j - n0) : beg2 + (j - n01));
-                c[u] = j < n ? __ldg(&yz[4 * pos]) : make_float2(INFINITY, INFINITY);
+                c[u] = j < n ? __ldg(&ix.rec[2 * pos]) : make_float4(INFINITY, INFINITY, INFINITY, 0.0f);
             }
+            // pre-filter: the road's y/z box and the deflection gate (the
+            // gate is the full test's own condition, taken here because dy
+            // arrives with y and z)
             unsigned mask = 0;
 #pragma unroll
             for (int u = 0; u < kScanChunk; ++u) {
                 const float ry = (__fsub_rn(c[u].x, yh) - yl) + tt * (z - c[u].y);
                 const float rz = c[u].y - z;
-                if (fabsf(ry) <= W && fabsf(rz) <= Rz) mask |= 1u << u;
+                if (fabsf(ry) <= W && fabsf(rz) <= Rz && !(fabsf(c[u].z - dy_pred) > gate)) mask |= 1u << u;
             }
             while (mask) {
                 const int u = __ffs(mask) - 1;
@@ -362,7 +363,6 @@ __device__ void scan_group(bool mine, const TrackState &s, int l, int chamber, i
         base_ch = bucket_of(cbase + chamber, 0, 0, ix.nb);
     }
     const float n2 = P.road * P.road;
-    const float2 *yzs = reinterpret_cast<const float2 *>(ix.rec);
     for (int h = 0; h < NH; ++h) {  // hypotheses live in lanes 0..NH-1
         if (!__shfl_sync(gmask, static_cast<int>(mine), h, G)) continue;
         const float hz = __shfl_sync(gmask, z, h, G), hyh = __shfl_sync(gmask, yh, h, G);
@@ -401,19 +401,19 @@ __device__ void scan_group(bool mine, const TrackState &s, int l, int chamber, i
             // lane q takes candidates q, q + G, ...: ceil(n / G) of them, four at a time
             const int per_lane = (n + G - 1) / G;
             for (int u0 = 0; u0 < per_lane; u0 += 4) {
-                float2 c[4];
+                float4 c[4];  // the records' first halves {y, z, dy, id}
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int j = q + G * (u0 + u);
                     const int pos = j < n0 ? beg0 + j : (j < n01 ? beg1 + (j - n0) : beg2 + (j - n01));
-                    c[u] = j < n ? __ldg(&yzs[4 * pos]) : make_float2(INFINITY, INFINITY);
+                    c[u] = j < n ? __ldg(&ix.rec[2 * pos]) : make_float4(INFINITY, INFINITY, INFINITY, 0.0f);
                 }
                 unsigned mask = 0;
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const float ry = (__fsub_rn(c[u].x, hyh) - hyl) + tt * (hz - c[u].y);
                     const float rz = c[u].y - hz;
-                    if (fabsf(ry) <= hW && fabsf(rz) <= hRz) mask |= 1u << u;
+                    if (fabsf(ry) <= hW && fabsf(rz) <= hRz && !(fabsf(c[u].z - hdyp) > hgate)) mask |= 1u << u;
                 }
                 while (mask) {
                     const int u = __ffs(mask) - 1;
