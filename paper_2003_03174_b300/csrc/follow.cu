@@ -534,26 +534,6 @@ __device__ __forceinline__ int gshfl(unsigned mask, int v, int src)
     return G == 1 ? v : __shfl_sync(mask, v, src, G);
 }
 
-// Next seed for this group from the launch's work counter.  G == 1: the lanes
-// that ask together share one atomicAdd (warp-aggregated).
-template <int G>
-__device__ __forceinline__ int fetch_seed(int *counter, unsigned gmask, int q)
-{
-    if (G == 1) {
-        const unsigned mask = __activemask();
-        const int lane = threadIdx.x & 31;
-        const int leader = __ffs(mask) - 1;
-        int base = 0;
-        if (lane == leader) base = atomicAdd(counter, __popc(mask));
-        base = __shfl_sync(mask, base, leader);
-        return base + __popc(mask & ((1u << lane) - 1u));
-    } else {
-        int t = 0;
-        if (q == 0) t = atomicAdd(counter, 1);
-        return __shfl_sync(gmask, t, 0, G);
-    }
-}
-
 // Per-seed registers of one lane (hypothesis q of its group).
 struct Lane {
     TrackState s;
@@ -935,9 +915,15 @@ __device__ __forceinline__ bool layer_step(int pos, int l, int q, unsigned gmask
     return false;
 }
 
-// Persistent follower: every group loops over seeds taken from the launch's
-// counter and over their layers in one flattened loop, so a lane whose seed
-// ends takes the next seed instead of idling while its warp finishes.
+// Persistent, layer-synchronous follower: a warp takes 32 / G consecutive
+// sorted positions (seeds of similar momentum; G lanes per seed) with one
+// atomic and carries its seeds through the six layers together, so every
+// group of the warp runs the same layer's code at the same time: the seed
+// loads, the layer's transport, road set-up and update, the merge of the
+// groups' lists and the result stores are issued once per warp instead of
+// once per group whose seed happens to be at that step.  A group whose seed
+// ended waits for the warp's last layer.  The snapshot of each group's state
+// before the layer's transport sits in shared memory (24 floats per group).
 template <int G, int NH, int MINB, bool EXT>
 __global__ void __launch_bounds__(128, MINB)
 k_follow(SeedsView sv, IndexView ix, Params P, ParkedView pk, int *counter)
@@ -947,59 +933,24 @@ k_follow(SeedsView sv, IndexView ix, Params P, ParkedView pk, int *counter)
     const int groups = blockDim.x / G;
     const int g = threadIdx.x / G;
     const int q = G == 1 ? 0 : (threadIdx.x & (G - 1));
-    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
-    float *sm = smem + g;
-    const float vyy_max = __uint_as_float(__ldg(&ix.stats[0]));
-    const float vzz_max = __uint_as_float(__ldg(&ix.stats[1]));
-    const float dx_max = EXT && ix.recx ? __uint_as_float(__ldg(&ix.stats[3])) : 0.0f;
-    Lane H;
-    int pos = 0, l = 0;
-    bool have = false;
-    for (;;) {
-        if (!have) {
-            pos = fetch_seed<G>(counter, gmask, q);
-            if (pos >= sv.n) break;
-            int i;
-            have = start_seed<G>(pos, q, sv, pk, H, i);
-            l = 0;
-            if (!have) continue;
-        }
-        if (layer_step<G, NH, EXT>(pos, l, q, gmask, ix, P, pk.rec, sm, groups, vyy_max, vzz_max, dx_max, H))
-            have = false;
-        ++l;
-    }
-}
-
-// Layer-synchronous follower for one hypothesis per seed (G = 1): a warp
-// takes 32 consecutive sorted positions (seeds of similar momentum) and
-// carries its 32 seeds through the six layers together, so every lane runs
-// the same layer's code at the same time: the seed loads, the result stores
-// and the layer's transport, road set-up and update are issued once per warp
-// instead of once per lane whose seed happens to be at that step.  A lane
-// whose seed ended waits for the warp's last layer.
-template <int MINB, bool EXT>
-__global__ void __launch_bounds__(128, MINB)
-k_follow_sync(SeedsView sv, IndexView ix, Params P, ParkedView pk, int *counter)
-{
-    wait_prior_grid();
-    extern __shared__ float smem[];
-    float *sm = smem + threadIdx.x;  // the snapshot of this thread's state before the layer's transport
-    const int stride = blockDim.x;
     const int lane = threadIdx.x & 31;
+    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+    float *sm = smem + g;
     const float vyy_max = __uint_as_float(__ldg(&ix.stats[0]));
     const float vzz_max = __uint_as_float(__ldg(&ix.stats[1]));
     const float dx_max = EXT && ix.recx ? __uint_as_float(__ldg(&ix.stats[3])) : 0.0f;
     for (;;) {
         int base = 0;
-        if (lane == 0) base = atomicAdd(counter, 32);
+        if (lane == 0) base = atomicAdd(counter, 32 / G);
         base = __shfl_sync(0xffffffffu, base, 0);
         if (base >= sv.n) break;
-        const int pos = base + lane;
+        const int pos = base + lane / G;
         Lane H;
         int i;
-        bool have = pos < sv.n && start_seed<1>(pos, 0, sv, pk, H, i);
+        bool have = pos < sv.n && start_seed<G>(pos, q, sv, pk, H, i);
         for (int l = 0; l < kLayers && __any_sync(0xffffffffu, have); ++l) {
-            if (have && layer_step<1, 1, EXT>(pos, l, 0, 0u, ix, P, pk.rec, sm, stride, vyy_max, vzz_max, dx_max, H))
+            if (have && layer_step<G, NH, EXT>(pos, l, q, gmask, ix, P, pk.rec, sm, groups, vyy_max, vzz_max,
+                                               dx_max, H))
                 have = false;
         }
     }
@@ -1066,11 +1017,7 @@ static int launch(const trd_ctx *ctx, const SeedsView &sv, const IndexView &ix, 
     if (sv.n == 0) return TRD_OK;
     const int groups = block / G;
     const size_t smem = sizeof(float) * 24 * groups;
-    void (*kernel)(SeedsView, IndexView, Params, ParkedView, int *);
-    if constexpr (G == 1)
-        kernel = k_follow_sync<MINB, EXT>;
-    else
-        kernel = k_follow<G, NH, MINB, EXT>;
+    void (*kernel)(SeedsView, IndexView, Params, ParkedView, int *) = k_follow<G, NH, MINB, EXT>;
     int per_sm = 0;
     TRD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem));
     per_sm = per_sm > 0 ? per_sm : 1;
