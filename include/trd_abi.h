@@ -404,8 +404,10 @@ TRD_API int trd_voxel_solve(trd_ctx_t *ctx, const int64_t *voxel_sums, int32_t m
  *       Result tracklet ids are local to each seed's timeframe.
  *   params, y_bin_width, launch: as for trd_index_build / trd_follow_tuned.
  * The library owns the batch (index, offsets, the follower's scratch of 136
- * bytes per seed + 528, graph); free with trd_batch_free.  Seeds are taken
- * timeframe by timeframe, each timeframe's in decreasing-|q/pT| order; each
+ * bytes per seed + 16 + 512 * min(n_tf, 8), graph); free with trd_batch_free.
+ * Seeds are taken timeframe by timeframe, each timeframe's in
+ * decreasing-|q/pT| order (128 momentum bins per timeframe up to 8
+ * timeframes, 1,024 bins shared out beyond); each
  * seed's arithmetic is the same as in trd_follow on its timeframe alone, so
  * results are identical.
  * trd_batch_run replays the graph on `stream` (asynchronous).  A batch must

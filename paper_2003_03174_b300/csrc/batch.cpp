@@ -75,7 +75,7 @@ int trd_batch_create(trd_ctx_t *ctx, int32_t n_tf, const int32_t *seed_offsets, 
     }
     if (cudaMalloc(&b->soff, sizeof(int32_t) * (n_tf + 1)) != cudaSuccess ||
         cudaMalloc(&b->counter, sizeof(int32_t)) != cudaSuccess ||
-        (seeds->n > 0 && cudaMalloc(&b->parked, trd_host::parked_bytes(seeds->n)) != cudaSuccess)) {
+        (seeds->n > 0 && cudaMalloc(&b->parked, trd_host::parked_bytes(seeds->n, n_tf)) != cudaSuccess)) {
         release(b);
         return TRD_ENOMEM;
     }

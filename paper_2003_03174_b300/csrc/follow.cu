@@ -555,7 +555,8 @@ struct Lane {
 // seed state is parked at the seed's sorted position and the result is staged
 // there too, so the follower reads and writes consecutive addresses; a gather
 // kernel then writes the results at the input positions with full lines.
-constexpr int kSortBins = 128;
+constexpr int kSortBins = 128;        // momentum bins of one timeframe
+constexpr int kMaxSortBins = 1024;    // bins of a batch of timeframes (128 per timeframe up to 8)
 constexpr float kSortBinsPerUnit = 28.0f;
 constexpr int kKeyThreads = 256;
 constexpr int kKeyItems = 8;
@@ -563,17 +564,24 @@ constexpr int kParkedWords = 25;  // words of a parked record
 
 // A batch of timeframes is taken timeframe by timeframe (each one's tracklet
 // records then stay in L2 while its seeds are followed), each in momentum
-// order at the resolution the 128 bins leave: bin = (timeframe * 128 +
-// momentum bin) / n_tf (two momentum bins per timeframe at 64 timeframes).
+// order at the resolution its share of the bins leaves: a batch has
+// sort_bins(n_tf) = 128 * min(n_tf, 8) bins and bin = (timeframe * 128 +
+// momentum bin) * bins / (128 * n_tf) (all 128 momentum bins of each
+// timeframe up to 8 timeframes, 16 of them at 64).
+__host__ __device__ __forceinline__ int sort_bins(int n_tf) { return kSortBins * (n_tf < 8 ? n_tf : 8); }
+
 __device__ __forceinline__ int sort_bin(float q2pt, int tf, int n_tf)
 {
     const float a = fabsf(q2pt) * kSortBinsPerUnit;  // NaN fails the test: first bin
     const int local = a < static_cast<float>(kSortBins - 1) ? kSortBins - 1 - static_cast<int>(a) : 0;
-    return n_tf == 1 ? local : (tf * kSortBins + local) / n_tf;
+    if (n_tf == 1) return local;
+    return static_cast<int>((static_cast<long long>(tf) * kSortBins + local) * sort_bins(n_tf) /
+                            (static_cast<long long>(kSortBins) * n_tf));
 }
 
-// Scratch of one follower call (device, n seeds; the base 16-byte aligned):
-//   bin_count [kSortBins]     seeds per |q/pT| bin (zeroed before k_seed_key)
+// Scratch of one follower call (device, n seeds of n_tf timeframes; the base
+// 16-byte aligned):
+//   bin_count [sort_bins]     seeds per sort bin (zeroed before k_seed_key)
 //   counter   [4]             the follower's work counter (zeroed by
 //                             k_seed_key), then padding: each call in flight
 //                             has its own
@@ -591,23 +599,26 @@ struct ParkedView {
     int32_t *counter;
     float4 *rec;
     int32_t *rank, *inv;
+    int nbins;
 };
 
-constexpr int kParkedHead = kSortBins + 4;  // bin counts, work counter, padding
+// bin counts, work counter, padding (528 bytes for one timeframe: a multiple of 16)
+__host__ __device__ inline int parked_head(int n_tf) { return sort_bins(n_tf) + 4; }
 
-__host__ __device__ inline size_t parked_words(int n)
+__host__ __device__ inline size_t parked_words(int n, int n_tf)
 {
-    return static_cast<size_t>(kParkedHead) + static_cast<size_t>(32 + 2) * static_cast<size_t>(n);
+    return static_cast<size_t>(parked_head(n_tf)) + static_cast<size_t>(32 + 2) * static_cast<size_t>(n);
 }
 
-__host__ __device__ inline ParkedView parked_view(void *base, int n)
+__host__ __device__ inline ParkedView parked_view(void *base, int n, int n_tf)
 {
     int32_t *w = static_cast<int32_t *>(base);
     ParkedView v;
+    v.nbins = sort_bins(n_tf);
     v.bin_count = w;
-    v.counter = w + kSortBins;
-    v.rec = reinterpret_cast<float4 *>(w + kParkedHead);  // 528 bytes in: still 16-byte aligned
-    v.rank = w + kParkedHead + 32 * static_cast<size_t>(n);
+    v.counter = w + v.nbins;
+    v.rec = reinterpret_cast<float4 *>(w + parked_head(n_tf));  // still 16-byte aligned
+    v.rank = w + parked_head(n_tf) + 32 * static_cast<size_t>(n);
     v.inv = v.rank + n;
     return v;
 }
@@ -621,8 +632,8 @@ k_seed_key(const float *__restrict__ q2pt, int n, const int32_t *__restrict__ so
            int *__restrict__ counter)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0) *counter = 0;
-    __shared__ int h[kSortBins], base[kSortBins];
-    for (int t = threadIdx.x; t < kSortBins; t += kKeyThreads) h[t] = 0;
+    __shared__ int h[kMaxSortBins], base[kMaxSortBins];
+    for (int t = threadIdx.x; t < pk.nbins; t += kKeyThreads) h[t] = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int i0 = blockIdx.x * (kKeyThreads * kKeyItems) + threadIdx.x;
@@ -639,7 +650,7 @@ k_seed_key(const float *__restrict__ q2pt, int n, const int32_t *__restrict__ so
         r[u] = first + __popc(peers & ((1u << lane) - 1u));
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < kSortBins; t += kKeyThreads) base[t] = h[t] ? atomicAdd(&pk.bin_count[t], h[t]) : 0;
+    for (int t = threadIdx.x; t < pk.nbins; t += kKeyThreads) base[t] = h[t] ? atomicAdd(&pk.bin_count[t], h[t]) : 0;
     __syncthreads();
 #pragma unroll
     for (int u = 0; u < kKeyItems; ++u) {
@@ -657,17 +668,19 @@ __global__ void __launch_bounds__(256) k_seed_prepare(SeedsView sv, Params P, Re
 {
     wait_prior_grid();
     // first sorted position of every bin: exclusive scan of the bin counts
-    static_assert(kSortBins == 4 * 32, "one warp scans four bins per lane");
-    __shared__ int s_off[kSortBins];
+    // (one warp, nbins / 32 consecutive bins per lane)
+    static_assert(kSortBins % 32 == 0 && kMaxSortBins % kSortBins == 0, "bins per lane");
+    __shared__ int s_off[kMaxSortBins];
     static_assert(kParkedWords % 2 == 1, "an odd row length keeps the lanes' rows in distinct banks");
     __shared__ float s_rec[256 / 32][32][kParkedWords];  // each warp's records
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
-        int c[4], sum = 0;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            c[j] = pk.bin_count[4 * lane + j];
-            sum += c[j];
+        const int per = pk.nbins / 32;
+        int sum = 0;
+        for (int j = 0; j < per; ++j) {
+            const int c = pk.bin_count[per * lane + j];
+            s_off[per * lane + j] = c;
+            sum += c;
         }
         int x = sum;
 #pragma unroll
@@ -676,10 +689,10 @@ __global__ void __launch_bounds__(256) k_seed_prepare(SeedsView sv, Params P, Re
             if (lane >= o2) x += t;
         }
         int run = x - sum;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            s_off[4 * lane + j] = run;
-            run += c[j];
+        for (int j = 0; j < per; ++j) {
+            const int c = s_off[per * lane + j];
+            s_off[per * lane + j] = run;
+            run += c;
         }
     }
     __syncthreads();
@@ -1001,7 +1014,7 @@ using namespace trd;
 static int prepare_kernels(const SeedsView &sv, const Params &P, const ResultsView &o, const ParkedView &pk,
                            int *counter, cudaStream_t s)
 {
-    TRD_CUDA_TRY(cudaMemsetAsync(pk.bin_count, 0, sizeof(int32_t) * kSortBins, s));
+    TRD_CUDA_TRY(cudaMemsetAsync(pk.bin_count, 0, sizeof(int32_t) * pk.nbins, s));
     const int per_block = kKeyThreads * kKeyItems;
     k_seed_key<<<(sv.n + per_block - 1) / per_block, kKeyThreads, 0, s>>>(sv.q2pt, sv.n, sv.soff, sv.n_tf, pk,
                                                                            counter);
@@ -1080,7 +1093,7 @@ static Params make_params(const trd_params_t *p, const trd_alignment_t *align)
     return P;
 }
 
-size_t parked_bytes(int32_t n) { return n > 0 ? sizeof(int32_t) * parked_words(n) : 0; }
+size_t parked_bytes(int32_t n, int32_t n_tf) { return n > 0 ? sizeof(int32_t) * parked_words(n, n_tf) : 0; }
 
 // The seeds' pre-pass alone (it does not read the index, so a captured step
 // can run it beside the index build).  parked: parked_bytes(n) of device
@@ -1090,13 +1103,14 @@ int prepare_launch(const trd_seeds_t *seeds, const trd_params_t *p, trd_results_
 {
     if (seeds->n == 0) return TRD_OK;
     if (!parked) return TRD_EINVAL;
-    if (!counter) counter = parked_view(parked, seeds->n).counter;
+    const int ntf = seed_offsets ? n_tf : 1;
+    if (!counter) counter = parked_view(parked, seeds->n, ntf).counter;
     SeedsView sv{seeds->alpha, seeds->x, seeds->y, seeds->z, seeds->snp, seeds->tgl, seeds->q2pt, seeds->cov,
                  seeds->n, seed_offsets, seed_offsets ? n_tf : 1, seeds->trigger};
     const Params P = make_params(p, align);
     ResultsView o{out->alpha, out->x, out->par, out->cov, out->chi2, out->n_trk, out->n_miss, out->status,
                   out->tracklet_id};
-    return prepare_kernels(sv, P, o, parked_view(parked, seeds->n), counter, s);
+    return prepare_kernels(sv, P, o, parked_view(parked, seeds->n, ntf), counter, s);
 }
 
 int follow_launch(const trd_ctx *ctx, const trd_seeds_t *seeds, const IndexView &iv, const trd_params_t *p,
@@ -1119,13 +1133,13 @@ int follow_launch(const trd_ctx *ctx, const trd_seeds_t *seeds, const IndexView 
     void *own = nullptr;
     if (sv.n > 0 && !parked) {
         if (!prepare) return TRD_EINVAL;  // the pre-pass's output is needed
-        if (cudaMallocAsync(&own, parked_bytes(sv.n), s) != cudaSuccess) {
+        if (cudaMallocAsync(&own, parked_bytes(sv.n, sv.n_tf), s) != cudaSuccess) {
             (void)cudaGetLastError();
             return TRD_ENOMEM;
         }
         parked = own;
     }
-    const ParkedView pk = sv.n > 0 ? parked_view(parked, sv.n) : ParkedView{};
+    const ParkedView pk = sv.n > 0 ? parked_view(parked, sv.n, sv.n_tf) : ParkedView{};
     if (!counter) counter = pk.counter;  // the call's own, inside its scratch
     const int rc = ext ? dispatch<true>(ctx, sv, iv, P, o, pk, s, G, mb, block, p->n_hyp, counter, prepare)
                        : dispatch<false>(ctx, sv, iv, P, o, pk, s, G, mb, block, p->n_hyp, counter, prepare);

@@ -61,7 +61,7 @@ int follow_launch(const trd_ctx *ctx, const trd_seeds_t *seeds, const IndexView 
                   int n_tf = 1, const trd_alignment_t *align = nullptr, bool prepare = true,
                   void *parked = nullptr);
 // Device scratch of the seeds' pre-pass for n seeds (sorted, rotated states).
-size_t parked_bytes(int32_t n);
+size_t parked_bytes(int32_t n, int32_t n_tf = 1);
 int prepare_launch(const trd_seeds_t *seeds, const trd_params_t *p, trd_results_t *out, cudaStream_t s,
                    void *parked, int *counter, const int32_t *seed_offsets = nullptr, int n_tf = 1,
                    const trd_alignment_t *align = nullptr);
