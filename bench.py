@@ -71,12 +71,12 @@ REFIT_FLOPS_PER_LAYER = 460
 # is still in L2 when the kernel ends), valid only for the source measured.
 REFIT_TRAFFIC = {"source_sha256_16": "89b8201dbc53c40e", "bytes": 39.88e6}
 # DRAM bytes (read + write) of one trd_follow call on this workload from one
-# ncu capture per kernel (k_seed_key 0.82 MB, k_seed_prepare 23.74 MB,
-# k_follow_sync 64.93 MB, k_results_gather 26.56 MB; ncu empties the caches
+# ncu capture per kernel (k_seed_key 0.82 MB, k_seed_prepare 24.19 MB,
+# k_follow 62.77 MB, k_results_gather 26.43 MB; ncu empties the caches
 # before each kernel, so the gather's reads of the staged results, L2 hits in
 # a plain run, count here), valid only for the kernel source it was measured
 # on: reported as null once follow.cu, trd_device.cuh or track_model.cuh change.
-FOLLOW_TRAFFIC = {"source_sha256_16": "9432d9d9481c0b9a", "bytes": 116.05e6}
+FOLLOW_TRAFFIC = {"source_sha256_16": "d4b0650166fa517a", "bytes": 114.21e6}
 # DRAM bytes (read 206.49 MB + write 12.93 MB) of one k_residuals launch on the
 # 100,000-track map from one ncu capture; the 450,000-track map holds ~3 GB on
 # the device and is not captured, so the figure is reported for the captured
@@ -482,7 +482,7 @@ def run_ours(args):
     hbm = peaks.get("hbm_gbs")
     follow_avg_s = statistics.mean(follow_ms) / 1e3
     achieved = n * bytes_per_seed / follow_avg_s / 1e9
-    roof = {"bound": "hbm", "kernel": "trd_follow (k_seed_key + k_seed_prepare + k_follow_sync + k_results_gather)",
+    roof = {"bound": "hbm", "kernel": "trd_follow (k_seed_key + k_seed_prepare + k_follow + k_results_gather)",
             "achieved": achieved,
             "peak": hbm if hbm else 6400.0, "unit": "GB/s",
             "peak_source": "measured" if hbm else "fallback",
