@@ -308,7 +308,7 @@ def served_summary(inputs, args, ctx):
                         f"{args.slots} slots, 60 GB budget, pinned host buffers",
             "unit": UNIT, "requests": p["served"]["requests"],
             "server": {"throughput": p["served"]["throughput"], "p50_ms": p["served"]["p50_ms"],
-                       "p99_ms": p["served"]["p99_ms"]},
+                       "p99_ms": p["served"]["p99_ms"], "timeline": p["served"]["timeline"]},
             "plain": {"throughput": p["plain"]["throughput"], "p50_ms": p["plain"]["p50_ms"],
                       "p99_ms": p["plain"]["p99_ms"]},
             "plain_mean_service_ms": m["plain_mean_service_ms"],
@@ -854,7 +854,39 @@ def make_served_inputs(n_payloads):
     return sizes, make_batch(sizes, seed=7, workers=os.cpu_count())
 
 
-def served_measure(payloads, rates, n_requests, slots, warmup, ctx=None):
+def _covered(a, b, spans):
+    """Length of [a, b] covered by the union of the intervals in spans."""
+    cut = sorted((max(a, x), min(b, y)) for x, y in spans if y > a and x < b)
+    tot, end = 0.0, a
+    for x, y in cut:
+        if y > end:
+            tot += y - max(x, end)
+            end = y
+    return tot
+
+
+def timeline_summary(marks):
+    """Stage marks (start, inputs in, kernels done, results out; device-clock
+    ms) of a stream of server requests: median stage times, the share of the
+    copy time that ran while another request's kernels were running, and the
+    share of the span in which some request's kernels ran."""
+    kern = [(m[1], m[2]) for m in marks]
+    copy_tot = copy_under = 0.0
+    for i, m in enumerate(marks):
+        others = kern[:i] + kern[i + 1:]
+        for a, b in ((m[0], m[1]), (m[2], m[3])):
+            copy_tot += b - a
+            copy_under += _covered(a, b, others)
+    t0, t1 = min(m[0] for m in marks), max(m[3] for m in marks)
+    return {"inputs_ms_p50": float(np.median([m[1] - m[0] for m in marks])),
+            "kernels_ms_p50": float(np.median([m[2] - m[1] for m in marks])),
+            "results_ms_p50": float(np.median([m[3] - m[2] for m in marks])),
+            "copy_time_under_other_kernels": copy_under / copy_tot if copy_tot > 0 else 0.0,
+            "kernels_busy_share_of_span": _covered(t0, t1, kern) / (t1 - t0) if t1 > t0 else 0.0,
+            "source": "CUDA events on each request's stream (trd_timing_t start/inputs/kernels/results_ms)"}
+
+
+def served_measure(payloads, rates, n_requests, slots, warmup, ctx=None, timeline_out=None):
     """For each arrival rate (multiples of the plain path's capacity) the same
     Poisson request sequence goes through (a) the server (trd_server_submit /
     poll, pinned host buffers, several requests in flight) and (b) the plain
@@ -930,7 +962,9 @@ def served_measure(payloads, rates, n_requests, slots, warmup, ctx=None):
                 for t, (jj, t_arr) in list(pending.items()):
                     tm = srv.poll(t)
                     if tm is not None:
-                        done_at[t] = (tm["done_s"], base + t_arr, jj)
+                        done_at[t] = (tm["done_s"], base + t_arr, jj,
+                                      (tm["start_ms"], tm["inputs_ms"], tm["kernels_ms"], tm["results_ms"]),
+                                      tm["slot"])
                         pending.pop(t)
                 time.sleep(50e-6)
         pending = {}
@@ -949,7 +983,16 @@ def served_measure(payloads, rates, n_requests, slots, warmup, ctx=None):
         lat = [v[0] - v[1] for v in done_at.values()]
         m_tot = sum(matched[v[2]] for v in done_at.values())
         served = {"throughput": m_tot / (last - first), "p50_ms": 1e3 * _pct(lat, 50),
-                  "p99_ms": 1e3 * _pct(lat, 99), "requests": n_req}
+                  "p99_ms": 1e3 * _pct(lat, 99), "requests": n_req,
+                  "timeline": timeline_summary([v[3] for v in done_at.values()])}
+        if timeline_out:
+            with open(timeline_out, "w") as fh:
+                fh.write("ticket,slot,payload,seeds,arrival_ms,start_ms,inputs_ms,kernels_ms,results_ms\n")
+                t_org = min(v[3][0] for v in done_at.values())
+                for t in sorted(done_at):
+                    v = done_at[t]
+                    fh.write(f"{t},{v[4]},{v[2]},{payloads[v[2]].n_seeds},{1e3 * (v[1] - first):.3f},"
+                             + ",".join(f"{x - t_org:.3f}" for x in v[3]) + "\n")
         # (b) plain: single queue, one request at a time in arrival order
         base = time.perf_counter()
         lat_p = []
@@ -977,7 +1020,7 @@ def run_served(args):
     sigma 0.8, capped at 600k), N = 3, 60 GB admission budget, arrival rates
     swept to saturation."""
     sizes, payloads = make_served_inputs(args.n_payloads)  # before any CUDA call
-    m = served_measure(payloads, args.rates, args.requests, args.slots, args.warmup)
+    m = served_measure(payloads, args.rates, args.requests, args.slots, args.warmup, timeline_out=args.timeline)
     points = m["points"]
     sat = max(points, key=lambda p: p["served"]["throughput"])
     line = {
@@ -1025,6 +1068,8 @@ def main():
     ap.add_argument("--requests", type=int, default=64)
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--rates", type=float, nargs="+", default=[0.5, 0.8, 1.0, 1.3, 1.7, 2.5])
+    ap.add_argument("--timeline", default=None,
+                    help="--workload served: write the last rate's per-request stage marks to this CSV file")
     ap.add_argument("--lanes", type=int, default=0, help="lanes per seed (with --no-autotune)")
     ap.add_argument("--block", type=int, default=0, help="block threads (with --no-autotune)")
     ap.add_argument("--min-blocks", type=int, default=0, help="register budget (with --no-autotune)")

@@ -441,11 +441,19 @@ typedef struct {
     trd_launch_t launch;       /* follower launch shape (zeros = defaults) */
 } trd_server_cfg_t;
 
-/* Host-clock seconds (steady clock) of one request, and its GPU time. */
+/* Host-clock seconds (steady clock) of one request, its GPU time, and its
+ * stages on the device clock: milliseconds since the server was created, read
+ * from CUDA events recorded on the request's stream before its first input
+ * copy (start_ms), after its last input copy (inputs_ms), after its index
+ * build and follower (kernels_ms) and after its last result copy
+ * (results_ms).  The marks of requests on different slots share that origin,
+ * so they show which requests' copies ran under which requests' kernels.
+ * A failed request's marks are zero.                                        */
 typedef struct {
     double submit_s, admit_s, done_s; /* done_s: stream callback after the results landed */
     float gpu_ms;                     /* first input copy to last result copy, CUDA events */
     int32_t slot;
+    float start_ms, inputs_ms, kernels_ms, results_ms;
 } trd_timing_t;
 
 /* trd_server_create: errors TRD_EINVAL (bad config or parameters),

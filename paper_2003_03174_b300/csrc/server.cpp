@@ -47,9 +47,31 @@ struct Request {
     int error = TRD_OK;
     // device buffers (stream-ordered allocations on the slot's stream)
     void *dbuf = nullptr;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // stream-ordered marks: before the input copies, after them, after the
+    // index build and follower, after the result copies
+    cudaEvent_t ev0 = nullptr, ev_in = nullptr, ev_k = nullptr, ev1 = nullptr;
     float gpu_ms = 0;
+    float stage_ms[4] = {0, 0, 0, 0};  // the four marks on the server's device clock
 };
+
+bool create_events(Request *r)
+{
+    if (cudaEventCreate(&r->ev0) == cudaSuccess && cudaEventCreate(&r->ev_in) == cudaSuccess &&
+        cudaEventCreate(&r->ev_k) == cudaSuccess && cudaEventCreate(&r->ev1) == cudaSuccess)
+        return true;
+    (void)cudaGetLastError();
+    return false;
+}
+
+void destroy_events(Request *r)
+{
+    cudaEvent_t *ev[4] = {&r->ev0, &r->ev_in, &r->ev_k, &r->ev1};
+    for (cudaEvent_t *e : ev)
+        if (*e) {
+            cudaEventDestroy(*e);
+            *e = nullptr;
+        }
+}
 
 struct Slot {
     cudaStream_t stream = nullptr;
@@ -101,6 +123,7 @@ struct trd_server {
     size_t used = 0;       // bytes of admitted requests' I/O buffers
     size_t index_used = 0; // bytes of the slots' resident indices
     bool stop = false;
+    cudaEvent_t ev_ref = nullptr;  // origin of the requests' device-clock marks
     std::thread worker;
     int fatal = TRD_OK;
 };
@@ -178,6 +201,7 @@ int start_request(trd_server *S, Slot &slot, Request *r)
     TRD_CUDA_TRY(cudaEventRecord(r->ev0, st));
     int rc = in.issue(cudaMemcpyHostToDevice, st);
     if (rc) return rc;
+    TRD_CUDA_TRY(cudaEventRecord(r->ev_in, st));
     trd_seeds_t dseeds{ds, ds + n, ds + 2 * static_cast<size_t>(n), ds + 3 * static_cast<size_t>(n),
                        ds + 4 * static_cast<size_t>(n), ds + 5 * static_cast<size_t>(n),
                        ds + 6 * static_cast<size_t>(n), ds + 7 * static_cast<size_t>(n), n,
@@ -193,6 +217,7 @@ int start_request(trd_server *S, Slot &slot, Request *r)
     rc = trd_host::follow_checked(S->ctx, &dseeds, slot.index, &S->cfg.params, nullptr, &dres, st, &S->cfg.launch,
                                   parked);
     if (rc) return rc;
+    TRD_CUDA_TRY(cudaEventRecord(r->ev_k, st));
     // results back: alpha x par[5] cov[15] chi2 (23 float rows), then 9 int rows
     float *hf[5] = {r->out.alpha, r->out.x, r->out.par, r->out.cov, r->out.chi2};
     const int rows_f[5] = {1, 1, 5, 15, 1};
@@ -249,6 +274,8 @@ void worker_loop(trd_server *S)
             Request *r = S->inflight[k];
             if (r->state.load() == 2) {
                 cudaEventElapsedTime(&r->gpu_ms, r->ev0, r->ev1);
+                const cudaEvent_t marks[4] = {r->ev0, r->ev_in, r->ev_k, r->ev1};
+                for (int k2 = 0; k2 < 4; ++k2) cudaEventElapsedTime(&r->stage_ms[k2], S->ev_ref, marks[k2]);
                 S->used -= r->bytes;
                 S->slots[r->slot].busy = nullptr;
                 S->inflight[k] = S->inflight.back();
@@ -355,6 +382,15 @@ int trd_server_create(trd_ctx_t *ctx, const trd_server_cfg_t *cfg, trd_server_t 
             delete S;
             return TRD_ECUDA;
         }
+    // the origin of the requests' device-clock marks
+    if (cudaEventCreate(&S->ev_ref) != cudaSuccess || cudaEventRecord(S->ev_ref, S->slots[0].stream) != cudaSuccess ||
+        cudaEventSynchronize(S->ev_ref) != cudaSuccess) {
+        if (S->ev_ref) cudaEventDestroy(S->ev_ref);
+        for (auto &z : S->slots) cudaStreamDestroy(z.stream);
+        (void)cudaGetLastError();
+        delete S;
+        return TRD_ECUDA;
+    }
     // keep freed stream-ordered memory in the pool between requests
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, ctx->device) == cudaSuccess) {
@@ -386,19 +422,19 @@ int trd_server_submit(trd_server_t *S, const trd_seeds_t *seeds, const trd_track
     r->trk = *trk;
     r->out = *results;
     r->bytes = bytes;
-    if (cudaEventCreate(&r->ev0) != cudaSuccess || cudaEventCreate(&r->ev1) != cudaSuccess) {
-        (void)cudaGetLastError();
+    if (!create_events(r)) {
+        destroy_events(r);
         delete r;
         return TRD_ECUDA;
     }
     std::lock_guard<std::mutex> g(S->mu);
     if (S->stop) {
+        destroy_events(r);
         delete r;
         return TRD_EINVAL;
     }
     if (static_cast<int>(S->queue.size()) >= S->cfg.max_queue) {
-        cudaEventDestroy(r->ev0);
-        cudaEventDestroy(r->ev1);
+        destroy_events(r);
         delete r;
         return TRD_EAGAIN;
     }
@@ -420,10 +456,13 @@ static int finish(trd_server *S, Request *r, trd_timing_t *t)
         t->done_s = r->t_done.load();
         t->gpu_ms = r->gpu_ms;
         t->slot = r->slot;
+        t->start_ms = r->stage_ms[0];
+        t->inputs_ms = r->stage_ms[1];
+        t->kernels_ms = r->stage_ms[2];
+        t->results_ms = r->stage_ms[3];
     }
     const int rc = r->state.load() == 3 ? r->error : TRD_OK;
-    cudaEventDestroy(r->ev0);
-    cudaEventDestroy(r->ev1);
+    destroy_events(r);
     S->all.erase(r->ticket);
     delete r;
     return rc;
@@ -484,10 +523,10 @@ int trd_server_destroy(trd_server_t *S)
         cudaStreamDestroy(sl.stream);
     }
     for (auto &kv : S->all) {
-        cudaEventDestroy(kv.second->ev0);
-        cudaEventDestroy(kv.second->ev1);
+        destroy_events(kv.second);
         delete kv.second;
     }
+    if (S->ev_ref) cudaEventDestroy(S->ev_ref);
     (void)cudaGetLastError();
     delete S;
     return TRD_OK;

@@ -86,7 +86,8 @@ class ServerCfg(C.Structure):
 
 class Timing(C.Structure):
     _fields_ = [("submit_s", C.c_double), ("admit_s", C.c_double), ("done_s", C.c_double),
-                ("gpu_ms", C.c_float), ("slot", C.c_int32)]
+                ("gpu_ms", C.c_float), ("slot", C.c_int32), ("start_ms", C.c_float), ("inputs_ms", C.c_float),
+                ("kernels_ms", C.c_float), ("results_ms", C.c_float)]
 
 
 _lib = None
@@ -377,7 +378,8 @@ class Server:
         self._live.pop(ticket, None)
         _check(fn, rc)
         return dict(submit_s=tm.submit_s, admit_s=tm.admit_s, done_s=tm.done_s, gpu_ms=tm.gpu_ms,
-                    slot=tm.slot)
+                    slot=tm.slot, start_ms=tm.start_ms, inputs_ms=tm.inputs_ms, kernels_ms=tm.kernels_ms,
+                    results_ms=tm.results_ms)
 
     def poll(self, ticket: int):
         """Timing dict when finished, None while pending (raises on failure)."""

@@ -54,9 +54,18 @@ def test_served_results_equal_alone_and_requests_overlap(ctx, tfs, slots, pinned
             np.testing.assert_array_equal(got[k], alone[k], err_msg=k)
         assert tm["submit_s"] <= tm["admit_s"] <= tm["done_s"]
         assert 0 <= tm["slot"] < slots
-    # continuous batching: some requests were on the GPU at the same time
+        # the device-clock stage marks: copies in, kernels, copies out in order,
+        # spanning the request's GPU time (event resolution ~0.5 us)
+        assert 0 <= tm["start_ms"] <= tm["inputs_ms"] <= tm["kernels_ms"] <= tm["results_ms"]
+        assert abs((tm["results_ms"] - tm["start_ms"]) - tm["gpu_ms"]) < 0.01 + 1e-3 * tm["gpu_ms"]
+    # continuous batching: some requests were on the GPU at the same time;
+    # with pinned buffers also on the device clock (copies from pageable
+    # memory go through a staging buffer one at a time)
     iv = sorted((tm["admit_s"], tm["done_s"]) for tm in timings)
     assert any(b[0] < a[1] for a, b in zip(iv, iv[1:]))
+    if pinned:
+        dv = sorted((tm["start_ms"], tm["results_ms"]) for tm in timings)
+        assert any(b[0] < a[1] for a, b in zip(dv, dv[1:]))
     st = srv.stats()
     assert st["queued"] == 0 and st["in_flight"] == 0
     srv.close()
