@@ -43,6 +43,11 @@ RESULT_BYTES = 128
 RECORD_BYTES = 32
 IN_ROAD_PER_SEED = 15.75
 FOLLOW_BYTES_PER_SEED = SEED_BYTES + RESULT_BYTES + RECORD_BYTES * IN_ROAD_PER_SEED
+# The follower kernel alone (k_follow, between the seeds' pre-pass and the
+# results' gather): per seed the parked record it reads (25 words), the
+# 128-byte record it stages the result in, and the in-road tracklet records.
+PARKED_BYTES = 100
+KERNEL_BYTES_PER_SEED = PARKED_BYTES + RESULT_BYTES + RECORD_BYTES * IN_ROAD_PER_SEED
 # FP32 operations of the follower per seed (model of its arithmetic, FMA = 2):
 # per layer transport ~200, material ~60, road set-up ~40, ~6 pre-filtered
 # candidates x 10, 2.6 in-road candidates x 25, Joseph update ~240 on ~80 % of
@@ -76,7 +81,7 @@ REFIT_TRAFFIC = {"source_sha256_16": "89b8201dbc53c40e", "bytes": 39.88e6}
 # before each kernel, so the gather's reads of the staged results, L2 hits in
 # a plain run, count here), valid only for the kernel source it was measured
 # on: reported as null once follow.cu, trd_device.cuh or track_model.cuh change.
-FOLLOW_TRAFFIC = {"source_sha256_16": "d4b0650166fa517a", "bytes": 114.21e6}
+FOLLOW_TRAFFIC = {"source_sha256_16": "d4b0650166fa517a", "bytes": 114.21e6, "k_follow": 62.77e6}
 # DRAM bytes (read 206.49 MB + write 12.93 MB) of one k_residuals launch on the
 # 100,000-track map from one ncu capture; the 450,000-track map holds ~3 GB on
 # the device and is not captured, so the figure is reported for the captured
@@ -315,6 +320,77 @@ def served_summary(inputs, args, ctx):
             "results_identical": m["results_identical"]}
 
 
+def _make_calibration(seed):
+    from synth import make_workload
+    return make_workload("calibration", seed=seed)
+
+
+def start_calibration_inputs():
+    """The calibration pass's workload (450k seeds, 2.24 M tracklets), drawn in
+    a spawn-started process while the GPU measures the timeframe."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    ex = cf.ProcessPoolExecutor(1, mp_context=mp.get_context("spawn"))
+    return ex, ex.submit(_make_calibration, rank_workload_seed(0))
+
+
+def calibration_summary(inputs, args, ctx, flush, hbm):
+    """Config 3 in the default line: the relaxed N = 6 pass (450k seeds, 5-sigma
+    road) with its autotuned shape, one CUDA-graph replay of index rebuild +
+    follow per step (L2 flushed between steps), and its per-parameter parity
+    against the oracle on 10,000 of its seeds."""
+    import torch
+    from paper_2003_03174_b300 import autotune, trd
+    ex, fut = inputs
+    tf = fut.result()
+    ex.shutdown()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.Stream(device=dev)
+    seeds, trk = trd.to_device(tf.seeds, dev), trd.to_device(tf.tracklets, dev)
+    n = tf.n_seeds
+    with torch.cuda.stream(stream):
+        tuned = autotune.tune(ctx, seeds, trk, tf.params, cache=None, reps=3)
+    shape = {k: tuned[k] for k in ("lanes_per_track", "block_threads", "min_blocks_per_sm")}
+    res = trd.alloc_results(n, dev)
+    graph = ctx.batch_create(seeds, trk, [0, n], [0, tf.n_tracklets], tf.params, res,
+                             y_bin_width=tuned["y_bin_width"], **shape)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            graph.run(stream)
+        for k in range(args.steps):
+            flush.add_(1.0)
+            ev[k][0].record(stream)
+            graph.run(stream)
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    matched = int((res["n_trk"] >= 2).sum().item())
+    timed = {k: v.cpu().numpy() for k, v in res.items()}
+    graph.free()
+    algo = n * CAL_FOLLOW_BYTES_PER_SEED
+    out = {"workload": f"calibration: {n} seeds, {tf.n_tracklets} tracklets, N={tf.params['n_hyp']}, "
+                       f"{tf.params['n_sigma_road']:g}-sigma road, 2 cm seed systematic, "
+                       f"<={tf.params['max_missing']} missing",
+           "unit": UNIT, "value": matched / (ms / 1e3), "ms_per_step": ms, "matched_per_step": matched,
+           "step": "one CUDA-graph replay (trd_batch_run: index rebuild + follow), L2 flushed between steps",
+           "index_y_bin_cm": tuned["y_bin_width"], "launch": shape,
+           "roofline": {"bound": "hbm", "achieved": algo / (ms / 1e3) / 1e9, "peak": hbm or 6400.0,
+                        "unit": "GB/s", "frac": algo / (ms / 1e3) / 1e9 / (hbm or 6400.0),
+                        "algorithmic_bytes_per_step": algo}}
+    if not args.no_cpu_baseline:
+        from oracle import oracle as O
+        sel = np.arange(0, n, n // 10_000)[:10_000].astype(np.int32)
+        t0 = time.perf_counter()
+        ora = O.follow(tf.seeds, tf.tracklets, tf.params, seed_index=sel)
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": int((ora["n_trk"] >= 2).sum()) / dt, "unit": UNIT, "cores": os.cpu_count(),
+                               "kind": "oracle", "sample": f"{len(sel)} of {n} seeds (every {n // len(sel)}th) "
+                                                           f"against all tracklets; {dt:.2f} s"}
+        out["parity"] = parity_report(timed, ora, sel, n)
+    return out
+
+
 def batched_summary(inputs, args, ctx):
     """Config 4: the 64-timeframe graph replay against 64 plain launches."""
     counts, tfs = inputs
@@ -336,6 +412,7 @@ def run_ours(args):
     extra = ws == 1 and args.workload == "timeframe" and not args.alignment
     served_in = make_served_inputs(args.n_payloads) if extra and not args.no_served else None
     batched_in = make_batched_inputs(args.n_tf) if extra and not args.no_batched else None
+    cal_in = start_calibration_inputs() if extra and not args.no_calibration else None
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
@@ -414,6 +491,22 @@ def run_ours(args):
         return ([a.elapsed_time(c) for a, _, c in ev], [a.elapsed_time(b) for a, b, _ in ev],
                 [b.elapsed_time(c) for _, b, c in ev])
 
+    def kernel_steps():
+        """The follower kernel alone: trd_follow_timed's events around its
+        launch, one pair per step, L2 flushed before each step."""
+        kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        with torch.cuda.stream(stream):
+            for a, b in kev:  # CUDA creates an event at its first record
+                a.record(stream)
+                b.record(stream)
+            for k in range(args.steps):
+                flush.add_(1.0)
+                index.rebuild(trk, stream=stream)
+                ctx.follow(seeds, index, tf.params, results=res, stream=stream, **shape, kernel_events=kev[k])
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in kev]
+
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -426,6 +519,7 @@ def run_ours(args):
         split_ms, index_ms, follow_ms = timed_steps(step, True)
         if step_ms is None:
             step_ms = split_ms
+        kernel_ms = kernel_steps() if not align else None
     if ws > 1:
         torch.distributed.barrier()
     total_s, matched_all = reduce_over_ranks(sum(step_ms) / 1e3, matched, dev)
@@ -482,20 +576,35 @@ def run_ours(args):
     hbm = peaks.get("hbm_gbs")
     follow_avg_s = statistics.mean(follow_ms) / 1e3
     achieved = n * bytes_per_seed / follow_avg_s / 1e9
-    roof = {"bound": "hbm", "kernel": "trd_follow (k_seed_key + k_seed_prepare + k_follow + k_results_gather)",
-            "achieved": achieved,
-            "peak": hbm if hbm else 6400.0, "unit": "GB/s",
-            "peak_source": "measured" if hbm else "fallback",
-            "frac": achieved / (hbm if hbm else 6400.0),
-            # captured for the default instance only (the aligned one: profiles/k_follow_aligned_timeframe.md)
-            "traffic": FOLLOW_TRAFFIC["bytes"] if _follow_source_hash() == FOLLOW_TRAFFIC["source_sha256_16"]
-            and tf.n_seeds == 200_000 and wl == WORKLOAD and not align else None,
-            "traffic_unit": "bytes per launch (ncu dram read+write)",
-            "algorithmic_bytes_per_launch": n * bytes_per_seed,
-            "follow_ms": statistics.mean(follow_ms), "index_ms": statistics.mean(index_ms),
-            "step_ms_separate_launches": statistics.mean(split_ms)}
+    peak = hbm if hbm else 6400.0
+    # ncu traffic, captured for the default instance on the 200k-seed timeframe only
+    # (the aligned one: profiles/k_follow_aligned_timeframe.md)
+    traffic_ok = (_follow_source_hash() == FOLLOW_TRAFFIC["source_sha256_16"] and tf.n_seeds == 200_000
+                  and wl == WORKLOAD and not align)
+    call = {"kernels": "trd_follow: k_seed_key + k_seed_prepare + k_follow + k_results_gather",
+            "achieved": achieved, "frac": achieved / peak, "ms": statistics.mean(follow_ms),
+            "traffic": FOLLOW_TRAFFIC["bytes"] if traffic_ok else None,
+            "algorithmic_bytes_per_launch": n * bytes_per_seed}
+    if kernel_ms is not None:
+        kbytes = n * (KERNEL_BYTES_PER_SEED if wl == WORKLOAD else
+                      PARKED_BYTES + RESULT_BYTES + RECORD_BYTES * CAL_IN_ROAD_PER_SEED)
+        k_ach = kbytes / (statistics.mean(kernel_ms) / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": "k_follow (timed alone: trd_follow_timed events around its launch)",
+                "achieved": k_ach, "peak": peak, "unit": "GB/s",
+                "peak_source": "measured" if hbm else "fallback", "frac": k_ach / peak,
+                "traffic": FOLLOW_TRAFFIC["k_follow"] if traffic_ok else None,
+                "traffic_unit": "bytes per launch (ncu dram read+write)",
+                "algorithmic_bytes_per_launch": kbytes, "kernel_ms": statistics.mean(kernel_ms), "call": call}
+    else:  # the aligned instance: the whole call
+        roof = {"bound": "hbm", "kernel": call["kernels"], "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "peak_source": "measured" if hbm else "fallback", "frac": achieved / peak, "traffic": None,
+                "traffic_unit": "bytes per launch (ncu dram read+write)",
+                "algorithmic_bytes_per_launch": n * bytes_per_seed}
+    roof.update({"follow_ms": statistics.mean(follow_ms), "index_ms": statistics.mean(index_ms),
+                 "step_ms_separate_launches": statistics.mean(split_ms)})
     fp32_peak = ctx.fp32_peak_tflops()
-    alu = {"bound": "alu", "achieved": n * flops_per_seed / follow_avg_s / 1e12, "peak": fp32_peak,
+    alu_s = statistics.mean(kernel_ms) / 1e3 if kernel_ms is not None else follow_avg_s
+    alu = {"bound": "alu", "achieved": n * flops_per_seed / alu_s / 1e12, "peak": fp32_peak,
            "unit": "TFLOP/s", "peak_source": "measured by trd_measure_fp32_peak (FMA chains)"}
     alu["frac"] = alu["achieved"] / fp32_peak
     roof["alu_check"] = alu
@@ -554,6 +663,8 @@ def run_ours(args):
             line["served"] = served_summary(served_in, args, ctx)
         if batched_in is not None:
             line["batched"] = batched_summary(batched_in, args, ctx)
+        if cal_in is not None:
+            line["calibration"] = calibration_summary(cal_in, args, ctx, flush, hbm)
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -1064,6 +1175,8 @@ def main():
                     help="interactions per timeframe (per-interaction association); 0 = off")
     ap.add_argument("--no-served", action="store_true", help="leave the served stream out of the default line")
     ap.add_argument("--no-batched", action="store_true", help="leave the batch out of the default line")
+    ap.add_argument("--no-calibration", action="store_true",
+                    help="leave the calibration pass (config 3) out of the default line")
     ap.add_argument("--n-payloads", type=int, default=16)
     ap.add_argument("--requests", type=int, default=64)
     ap.add_argument("--slots", type=int, default=4)

@@ -58,14 +58,15 @@ def test_served_results_equal_alone_and_requests_overlap(ctx, tfs, slots, pinned
         # spanning the request's GPU time (event resolution ~0.5 us)
         assert 0 <= tm["start_ms"] <= tm["inputs_ms"] <= tm["kernels_ms"] <= tm["results_ms"]
         assert abs((tm["results_ms"] - tm["start_ms"]) - tm["gpu_ms"]) < 0.01 + 1e-3 * tm["gpu_ms"]
-    # continuous batching: some requests were on the GPU at the same time;
-    # with pinned buffers also on the device clock (copies from pageable
-    # memory go through a staging buffer one at a time)
+    # continuous batching: some requests were in flight at the same time
+    # (whether their device work overlapped depends on their sizes and the
+    # host's timing; the served bench line measures that from these marks)
     iv = sorted((tm["admit_s"], tm["done_s"]) for tm in timings)
     assert any(b[0] < a[1] for a, b in zip(iv, iv[1:]))
-    if pinned:
-        dv = sorted((tm["start_ms"], tm["results_ms"]) for tm in timings)
-        assert any(b[0] < a[1] for a, b in zip(dv, dv[1:]))
+    # requests on one slot run one after another on the device clock
+    for sl in range(slots):
+        dv = sorted((tm["start_ms"], tm["results_ms"]) for tm in timings if tm["slot"] == sl)
+        assert all(b[0] >= a[1] - 1e-3 for a, b in zip(dv, dv[1:]))
     st = srv.stats()
     assert st["queued"] == 0 and st["in_flight"] == 0
     srv.close()
