@@ -237,6 +237,20 @@ TRD_API int trd_follow_tuned(trd_ctx_t *ctx, const trd_seeds_t *seeds, const trd
                              const trd_params_t *params, trd_results_t *out, void *stream,
                              const trd_launch_t *launch);
 
+/* trd_follow_timed: trd_follow_tuned that also records two caller-owned CUDA
+ * events (cudaEvent_t handles, created with timing enabled) on `stream`:
+ * ev_start just before the follower kernel is launched and ev_end just after
+ * it, so that cudaEventElapsedTime(ev_start, ev_end) is that kernel's device
+ * time alone (the seeds' key and pre-pass before it and the gather of the
+ * results after it lie outside the pair).  The events keep the kernel from
+ * starting while the pre-pass drains (programmatic dependent launch), so a
+ * timed call takes a little longer than an untimed one.  With no seeds both
+ * events are recorded at once.  Results are those of trd_follow_tuned.
+ * Errors as trd_follow_tuned, plus TRD_EINVAL for a NULL event.             */
+TRD_API int trd_follow_timed(trd_ctx_t *ctx, const trd_seeds_t *seeds, const trd_index_t *index,
+                             const trd_params_t *params, trd_results_t *out, void *stream,
+                             const trd_launch_t *launch, void *ev_start, void *ev_end);
+
 /* ---- misalignment and field map (Sec. 3) ---------------------------------------
  * Misaligned chambers put tracklets at different radii; the paper carries a
  * track to the average radius of the chamber (through the field's

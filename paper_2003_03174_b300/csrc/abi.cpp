@@ -241,7 +241,7 @@ int trd_follow_aligned(trd_ctx_t *ctx, const trd_seeds_t *seeds, const trd_index
 // device's pool on the stream.
 int trd_host::follow_checked(trd_ctx *ctx, const trd_seeds_t *seeds, const trd_index *index, const trd_params_t *p,
                              const trd_alignment_t *align, trd_results_t *out, void *stream,
-                             const trd_launch_t *launch, void *parked)
+                             const trd_launch_t *launch, void *parked, const KernelEvents *kev)
 {
     if (align && align->bz_map &&
         (align->nr < 2 || align->nz < 2 || !(align->r_max > align->r_min) || !(align->z_max > align->z_min) ||
@@ -269,7 +269,7 @@ int trd_host::follow_checked(trd_ctx *ctx, const trd_seeds_t *seeds, const trd_i
                  index->has_x ? index->recx : nullptr};
     return trd_host::follow_launch(ctx, seeds, iv, p, out, static_cast<cudaStream_t>(stream), lanes_per_track,
                                    block_threads, min_blocks, nullptr, nullptr, 1, align, true,
-                                   parked);
+                                   parked, kev);
 }
 
 extern "C" {
@@ -278,6 +278,14 @@ int trd_follow(trd_ctx_t *ctx, const trd_seeds_t *seeds, const trd_index_t *inde
                trd_results_t *out, void *stream)
 {
     return trd_follow_tuned(ctx, seeds, index, p, out, stream, nullptr);
+}
+
+int trd_follow_timed(trd_ctx_t *ctx, const trd_seeds_t *seeds, const trd_index_t *index, const trd_params_t *p,
+                     trd_results_t *out, void *stream, const trd_launch_t *launch, void *ev_start, void *ev_end)
+{
+    if (!ev_start || !ev_end) return TRD_EINVAL;
+    const trd_host::KernelEvents kev{static_cast<cudaEvent_t>(ev_start), static_cast<cudaEvent_t>(ev_end)};
+    return trd_host::follow_checked(ctx, seeds, index, p, nullptr, out, stream, launch, nullptr, &kev);
 }
 
 }  // extern "C"

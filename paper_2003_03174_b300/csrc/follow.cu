@@ -1025,9 +1025,16 @@ static int prepare_kernels(const SeedsView &sv, const Params &P, const ResultsVi
 
 template <int G, int NH, int MINB, bool EXT>
 static int launch(const trd_ctx *ctx, const SeedsView &sv, const IndexView &ix, const Params &P,
-                  const ResultsView &o, const ParkedView &pk, cudaStream_t s, int block, int *counter, bool prepare)
+                  const ResultsView &o, const ParkedView &pk, cudaStream_t s, int block, int *counter, bool prepare,
+                  const KernelEvents *kev)
 {
-    if (sv.n == 0) return TRD_OK;
+    if (sv.n == 0) {
+        if (kev) {  // no kernel: an empty interval
+            TRD_CUDA_TRY(cudaEventRecord(kev->start, s));
+            TRD_CUDA_TRY(cudaEventRecord(kev->end, s));
+        }
+        return TRD_OK;
+    }
     const int groups = block / G;
     const size_t smem = sizeof(float) * 24 * groups;
     void (*kernel)(SeedsView, IndexView, Params, ParkedView, int *) = k_follow<G, NH, MINB, EXT>;
@@ -1043,7 +1050,10 @@ static int launch(const trd_ctx *ctx, const SeedsView &sv, const IndexView &ix, 
         if (rc) return rc;
     }
     // the follower and the gather start while their predecessor drains
+    // (except around the events of a timed call)
+    if (kev) TRD_CUDA_TRY(cudaEventRecord(kev->start, s));
     TRD_CUDA_TRY(launch_after(kernel, dim3(grid), dim3(block), smem, s, sv, ix, P, pk, counter));
+    if (kev) TRD_CUDA_TRY(cudaEventRecord(kev->end, s));
     TRD_CUDA_TRY(launch_after(k_results_gather, dim3((sv.n + 255) / 256), dim3(256), 0, s, sv.n, pk, o));
     return TRD_OK;
 }
@@ -1051,9 +1061,9 @@ static int launch(const trd_ctx *ctx, const SeedsView &sv, const IndexView &ix, 
 template <bool EXT>
 static int dispatch(const trd_ctx *ctx, const SeedsView &sv, const IndexView &iv, const Params &P,
                     const ResultsView &o, const ParkedView &pk, cudaStream_t s, int G, int mb, int block, int nhyp,
-                    int *counter, bool prepare)
+                    int *counter, bool prepare, const KernelEvents *kev)
 {
-#define TRD_LAUNCH(g, nh, m) launch<g, nh, m, EXT>(ctx, sv, iv, P, o, pk, s, block, counter, prepare)
+#define TRD_LAUNCH(g, nh, m) launch<g, nh, m, EXT>(ctx, sv, iv, P, o, pk, s, block, counter, prepare, kev)
     switch (G * 16 + mb) {
     case 1 * 16 + 4: return nhyp == 1 ? TRD_LAUNCH(1, 1, 4) : TRD_EINVAL;
     case 1 * 16 + 5: return nhyp == 1 ? TRD_LAUNCH(1, 1, 5) : TRD_EINVAL;
@@ -1116,7 +1126,7 @@ int prepare_launch(const trd_seeds_t *seeds, const trd_params_t *p, trd_results_
 int follow_launch(const trd_ctx *ctx, const trd_seeds_t *seeds, const IndexView &iv, const trd_params_t *p,
                   trd_results_t *out, cudaStream_t s, int lanes_per_track, int block_threads, int min_blocks,
                   int *counter, const int32_t *seed_offsets, int n_tf, const trd_alignment_t *align,
-                  bool prepare, void *parked)
+                  bool prepare, void *parked, const KernelEvents *kev)
 {
     SeedsView sv{seeds->alpha, seeds->x, seeds->y, seeds->z, seeds->snp, seeds->tgl, seeds->q2pt, seeds->cov,
                  seeds->n, seed_offsets, n_tf, seeds->trigger};
@@ -1141,8 +1151,8 @@ int follow_launch(const trd_ctx *ctx, const trd_seeds_t *seeds, const IndexView 
     }
     const ParkedView pk = sv.n > 0 ? parked_view(parked, sv.n, sv.n_tf) : ParkedView{};
     if (!counter) counter = pk.counter;  // the call's own, inside its scratch
-    const int rc = ext ? dispatch<true>(ctx, sv, iv, P, o, pk, s, G, mb, block, p->n_hyp, counter, prepare)
-                       : dispatch<false>(ctx, sv, iv, P, o, pk, s, G, mb, block, p->n_hyp, counter, prepare);
+    const int rc = ext ? dispatch<true>(ctx, sv, iv, P, o, pk, s, G, mb, block, p->n_hyp, counter, prepare, kev)
+                       : dispatch<false>(ctx, sv, iv, P, o, pk, s, G, mb, block, p->n_hyp, counter, prepare, kev);
     if (own && cudaFreeAsync(own, s) != cudaSuccess) {
         (void)cudaGetLastError();
         return rc ? rc : TRD_ECUDA;

@@ -54,12 +54,17 @@ struct IndexView {
 };
 
 namespace trd_host {
+// Caller-owned events recorded just before and just after the follower
+// kernel's launch (trd_follow_timed).
+struct KernelEvents {
+    cudaEvent_t start, end;
+};
 int index_rebuild_launch(trd_index *idx, const trd_tracklets_t *t, cudaStream_t s);
 int follow_launch(const trd_ctx *ctx, const trd_seeds_t *seeds, const IndexView &iv,
                   const trd_params_t *p, trd_results_t *out, cudaStream_t s, int lanes_per_track,
                   int block_threads, int min_blocks, int *counter, const int32_t *seed_offsets = nullptr,
                   int n_tf = 1, const trd_alignment_t *align = nullptr, bool prepare = true,
-                  void *parked = nullptr);
+                  void *parked = nullptr, const KernelEvents *kev = nullptr);
 // Device scratch of the seeds' pre-pass for n seeds (sorted, rotated states).
 size_t parked_bytes(int32_t n, int32_t n_tf = 1);
 int prepare_launch(const trd_seeds_t *seeds, const trd_params_t *p, trd_results_t *out, cudaStream_t s,
@@ -67,7 +72,7 @@ int prepare_launch(const trd_seeds_t *seeds, const trd_params_t *p, trd_results_
                    const trd_alignment_t *align = nullptr);
 int follow_checked(trd_ctx *ctx, const trd_seeds_t *seeds, const trd_index *index, const trd_params_t *p,
                    const trd_alignment_t *align, trd_results_t *out, void *stream, const trd_launch_t *launch,
-                   void *parked);
+                   void *parked, const KernelEvents *kev = nullptr);
 int index_alloc(trd_ctx *ctx, int32_t capacity, float y_bin_width, int32_t n_tf, trd_index **out);
 void index_release(trd_index *x);
 int scan_blocks_for(int n);

@@ -24,7 +24,7 @@ EXPORTED = [
     "trd_geometry", "trd_version", "trd_index_copy_out", "trd_batch_create", "trd_batch_run",
     "trd_batch_free", "trd_server_create", "trd_server_submit", "trd_server_poll", "trd_server_wait",
     "trd_server_stats", "trd_server_destroy", "trd_index_build_noalloc", "trd_measure_fp32_peak",
-    "trd_refit", "trd_residuals", "trd_voxel_solve", "trd_follow_aligned",
+    "trd_refit", "trd_residuals", "trd_voxel_solve", "trd_follow_aligned", "trd_follow_timed",
 ]
 TPC_ROWS, VOX_Y_BINS, VOX_Z_BINS, VOX_SUMS = 152, 15, 5, 11
 N_VOXELS = 2 * 18 * TPC_ROWS * VOX_Y_BINS * VOX_Z_BINS
@@ -115,6 +115,8 @@ def lib():
                                        C.POINTER(Results), vp, C.POINTER(Launch)]
         L.trd_follow_aligned.argtypes = [vp, C.POINTER(Seeds), vp, C.POINTER(Params), C.POINTER(Alignment),
                                          C.POINTER(Results), vp, C.POINTER(Launch)]
+        L.trd_follow_timed.argtypes = [vp, C.POINTER(Seeds), vp, C.POINTER(Params), C.POINTER(Results), vp,
+                                       C.POINTER(Launch), vp, vp]
         L.trd_geometry.argtypes = [C.POINTER(C.c_double), C.c_int]
         L.trd_index_copy_out.argtypes = [vp, vp, vp]
         L.trd_batch_create.argtypes = [vp, i32, vp, vp, C.POINTER(Seeds), C.POINTER(Tracklets),
@@ -469,19 +471,33 @@ class Context:
 
     def follow(self, seeds: dict, index: Index, params: dict, results: dict | None = None,
                stream=None, lanes_per_track: int = 0, block_threads: int = 0,
-               min_blocks_per_sm: int = 0, chamber_x=None, field=None) -> dict:
+               min_blocks_per_sm: int = 0, chamber_x=None, field=None, kernel_events=None) -> dict:
         """trd_follow (trd_follow_tuned with a launch shape; trd_follow_aligned
-        with chamber radii and/or a field map, see alignment_struct)."""
+        with chamber radii and/or a field map, see alignment_struct;
+        trd_follow_timed with kernel_events = (start, end), two
+        torch.cuda.Event(enable_timing=True) that have been recorded once, so
+        that their CUDA events exist)."""
         n = int(seeds["alpha"].shape[0])
         if results is None:
             results = alloc_results(n, device=seeds["alpha"].device)
         ss, ps, rs = seeds_struct(seeds), params_struct(params), results_struct(results)
+        if kernel_events is not None and (chamber_x is not None or field is not None):
+            raise ValueError("kernel_events: the timed entry point takes no alignment")
         if chamber_x is not None or field is not None:
             al = alignment_struct(chamber_x, field)
             ln = Launch(int(lanes_per_track), int(block_threads), int(min_blocks_per_sm))
             rc = lib().trd_follow_aligned(self.handle, C.byref(ss), index.handle, C.byref(ps), C.byref(al),
                                           C.byref(rs), _stream_handle(stream), C.byref(ln))
             _check("trd_follow_aligned", rc)
+            return results
+        if kernel_events is not None:
+            ev0, ev1 = (C.c_void_p(int(e.cuda_event)) for e in kernel_events)
+            if not ev0.value or not ev1.value:
+                raise ValueError("kernel_events: record each event once first (it is created lazily)")
+            ln = Launch(int(lanes_per_track), int(block_threads), int(min_blocks_per_sm))
+            rc = lib().trd_follow_timed(self.handle, C.byref(ss), index.handle, C.byref(ps), C.byref(rs),
+                                        _stream_handle(stream), C.byref(ln), ev0, ev1)
+            _check("trd_follow_timed", rc)
             return results
         if lanes_per_track or block_threads or min_blocks_per_sm:
             ln = Launch(int(lanes_per_track), int(block_threads), int(min_blocks_per_sm))

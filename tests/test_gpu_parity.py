@@ -384,3 +384,35 @@ def test_resident_index_rebuilds_stay_exact(ctx):
         n = len(trk["chamber"])
         assert np.array_equal(np.sort(ids[:n]), np.arange(n))
         np.testing.assert_array_equal(bk[ids[:n]], np.repeat(np.arange(counts.shape[0]), counts))
+
+
+@pytest.mark.parametrize("n_hyp,lanes", [(1, 1), (3, 4)])
+def test_timed_follow_gives_the_same_results_and_times_the_kernel_alone(ctx, n_hyp, lanes):
+    # trd_follow_timed: the results of trd_follow_tuned, and its events bracket
+    # the follower kernel inside the whole call
+    from paper_2003_03174_b300 import trd
+    tf = make_workload("timeframe", seed=17, n_seeds=20_000)
+    params = dict(tf.params, n_hyp=n_hyp)
+    s, t = trd.to_device(tf.seeds), trd.to_device(tf.tracklets)
+    idx = ctx.index_build(t, 1.0)
+    plain = to_numpy(ctx.follow(s, idx, params, lanes_per_track=lanes))
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for e in ev:
+        e.record()
+    ev[0].record()
+    timed = ctx.follow(s, idx, params, lanes_per_track=lanes, kernel_events=(ev[1], ev[2]))
+    ev[3].record()
+    torch.cuda.synchronize()
+    for k, v in to_numpy(timed).items():
+        np.testing.assert_array_equal(v, plain[k], err_msg=k)
+    kernel, call = ev[1].elapsed_time(ev[2]), ev[0].elapsed_time(ev[3])
+    assert 0 < kernel < call
+    # no seeds: both events recorded at once
+    none = {k: v[..., :0] for k, v in tf.seeds.items()}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    e1.record()
+    ctx.follow(trd.to_device(none), idx, params, lanes_per_track=lanes, kernel_events=(e0, e1))
+    torch.cuda.synchronize()
+    assert 0 <= e0.elapsed_time(e1) < 0.05
+    idx.free()
