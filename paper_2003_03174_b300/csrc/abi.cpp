@@ -266,7 +266,7 @@ int trd_host::follow_checked(trd_ctx *ctx, const trd_seeds_t *seeds, const trd_i
     }
     TRD_CUDA_TRY(cudaSetDevice(ctx->device));
     IndexView iv{index->offsets, index->rec, index->stats, index->nb, index->inv_w,
-                 index->has_x ? index->recx : nullptr};
+                 index->has_x ? index->recx : nullptr, index->n_input};
     return trd_host::follow_launch(ctx, seeds, iv, p, out, static_cast<cudaStream_t>(stream), lanes_per_track,
                                    block_threads, min_blocks, nullptr, nullptr, 1, align, true,
                                    parked, kev);

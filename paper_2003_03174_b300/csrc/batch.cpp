@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -132,8 +133,10 @@ int trd_batch_create(trd_ctx_t *ctx, int32_t n_tf, const int32_t *seed_offsets, 
         if (ok && !rc) rc = trd_host::index_rebuild_launch(b->index, tracklets, cs);
         if (ok && !rc) ok = cudaStreamWaitEvent(cs, join, 0) == cudaSuccess;
         if (ok && !rc) {
+            int32_t most = 0;
+            for (int t = 0; t < n_tf; ++t) most = std::max(most, tracklet_offsets[t + 1] - tracklet_offsets[t]);
             IndexView iv{b->index->offsets, b->index->rec, b->index->stats, b->index->nb, b->index->inv_w,
-                         tracklets->x ? b->index->recx : nullptr};
+                         tracklets->x ? b->index->recx : nullptr, most};
             rc = trd_host::follow_launch(ctx, seeds, iv, params, results, cs, launch ? launch->lanes_per_track : 0,
                                          launch ? launch->block_threads : 0, launch ? launch->min_blocks_per_sm : 0,
                                          b->counter, n_tf > 1 ? b->soff : nullptr, n_tf, nullptr, false,

@@ -179,6 +179,26 @@ struct ExtList {
     }
 };
 
+// The selection order (score, parent rank, tracklet id) as one unsigned
+// 64-bit key, for the groups' merge: the score's bits made orderable, then
+// the parent (3 bits) and the id (28 bits, kMissing as the largest).  Needs
+// tracklet ids below kKeyIdMask (the library checks the index's size).
+constexpr unsigned kKeyIdMask = 0x0fffffffu;
+
+__device__ __forceinline__ unsigned long long head_key(float s, int par, int id)
+{
+    unsigned u = __float_as_uint(s);
+    u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+    const unsigned lo = (static_cast<unsigned>(par) << 28) | (id == kMissing ? kKeyIdMask : static_cast<unsigned>(id));
+    return (static_cast<unsigned long long>(u) << 32) | lo;
+}
+
+__device__ __forceinline__ float key_score(unsigned long long k)
+{
+    const unsigned t = static_cast<unsigned>(k >> 32);
+    return __uint_as_float((t & 0x80000000u) ? (t & 0x7fffffffu) : ~t);
+}
+
 // Road query + candidate tests for one hypothesis at layer l (Sec. 3).
 // The road bounds z_tl to z +- Rz (pad rows r_lo..r_hi) and the measured y to
 // y +- (W + |tan tau| Rz) (y bins b_lo..b_hi); each pad row is one contiguous
@@ -833,19 +853,41 @@ __device__ __forceinline__ bool layer_step(int pos, int l, int q, unsigned gmask
         for (int rr = 0; rr < P.nhyp; ++rr) {
             // group minimum of the lanes' heads in (score, parent, id) order;
             // bh is the lane holding it
-            float bs = L.score[0];
-            int bp = L.par[0], bid = L.id[0], bh = q;
+            float bs;
+            int bp, bid, bh;
+            if (G >= 8) {
+                // as one 64-bit key (two shuffles a step instead of four); the
+                // keys of the lanes' heads are distinct, so the holder is the
+                // lane whose head equals the minimum
+                const unsigned long long mine = head_key(L.score[0], L.par[0], L.id[0]);
+                unsigned long long best = mine;
 #pragma unroll
-            for (int off = G / 2; off > 0; off >>= 1) {
-                const float os = __shfl_xor_sync(gmask, bs, off, G);
-                const int op = __shfl_xor_sync(gmask, bp, off, G);
-                const int oid = __shfl_xor_sync(gmask, bid, off, G);
-                const int oh = __shfl_xor_sync(gmask, bh, off, G);
-                if (ExtList<NH>::less(os, op, oid, bs, bp, bid)) {
-                    bs = os;
-                    bp = op;
-                    bid = oid;
-                    bh = oh;
+                for (int off = G / 2; off > 0; off >>= 1) {
+                    const unsigned long long o = __shfl_xor_sync(gmask, best, off, G);
+                    best = o < best ? o : best;
+                }
+                bs = key_score(best);
+                const unsigned lo = static_cast<unsigned>(best);
+                bp = static_cast<int>(lo >> 28);
+                bid = (lo & kKeyIdMask) == kKeyIdMask ? kMissing : static_cast<int>(lo & kKeyIdMask);
+                bh = (__ffs(__ballot_sync(gmask, mine == best) & gmask) - 1) & (G - 1);
+            } else {
+                bs = L.score[0];
+                bp = L.par[0];
+                bid = L.id[0];
+                bh = q;
+#pragma unroll
+                for (int off = G / 2; off > 0; off >>= 1) {
+                    const float os = __shfl_xor_sync(gmask, bs, off, G);
+                    const int op = __shfl_xor_sync(gmask, bp, off, G);
+                    const int oid = __shfl_xor_sync(gmask, bid, off, G);
+                    const int oh = __shfl_xor_sync(gmask, bh, off, G);
+                    if (ExtList<NH>::less(os, op, oid, bs, bp, bid)) {
+                        bs = os;
+                        bp = op;
+                        bid = oid;
+                        bh = oh;
+                    }
                 }
             }
             if (!(bs < INFINITY)) break;
@@ -1138,6 +1180,8 @@ int follow_launch(const trd_ctx *ctx, const trd_seeds_t *seeds, const IndexView 
     int G = lanes_per_track;
     if (G <= 0) G = p->n_hyp <= 1 ? 1 : (p->n_hyp <= 2 ? 2 : (p->n_hyp <= 4 ? 4 : 8));
     if (G < p->n_hyp) return TRD_EINVAL;
+    // groups of 8 or more merge by 64-bit keys that hold 28-bit tracklet ids
+    if (G >= 8 && iv.max_tf_tracklets >= static_cast<int32_t>(trd::kKeyIdMask)) return TRD_EINVAL;
     const int mb = min_blocks > 0 ? min_blocks : 4;
     // without a caller scratch: one from the device's pool, ordered on s
     void *own = nullptr;

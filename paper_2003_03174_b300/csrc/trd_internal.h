@@ -51,6 +51,7 @@ struct IndexView {
     int32_t nb;
     float inv_w;
     const float *recx = nullptr;  // radius per record, or null (every tracklet at its layer's radius)
+    int32_t max_tf_tracklets = 0; // most tracklets of one timeframe (their ids' bound)
 };
 
 namespace trd_host {
