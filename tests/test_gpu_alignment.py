@@ -117,3 +117,17 @@ def test_served_misaligned_equals_plain(ctx):
         np.testing.assert_array_equal(out[k], plain[k], err_msg=k)
     o = O.follow(tf.seeds, tf.tracklets, p)
     compare(plain, o)
+
+
+def test_full_aligned_timeframe_parity_every_seed(ctx):
+    """The benchmark's misaligned timeframe (200k seeds, chambers shifted by up
+    to 0.5 cm, tracklets by 0.1 cm more, the Bz(r, z) map): every seed against
+    the oracle (it holds a stack-boundary near tie that moves one track's state
+    without changing its tracklets)."""
+    from synth.timeframe import field_map
+    tf = make_workload("timeframe", misalign=0.5, x_jitter=0.1)
+    fm = field_map(tf.params["bz"])
+    g = _gpu(ctx, tf, tf.params, chamber_x=tf.chamber_x, field=fm, lanes=1)
+    o = O.follow(tf.seeds, tf.tracklets, tf.params, chamber_x=tf.chamber_x, field=fm)
+    rep = compare(g, o)
+    assert rep["same_path"] >= 0.995 * tf.n_seeds
