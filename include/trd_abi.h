@@ -227,8 +227,7 @@ TRD_API int trd_follow(trd_ctx_t *ctx, const trd_seeds_t *seeds, const trd_index
  *   block_threads     64 or 128 (0 = 128)
  *   min_blocks_per_sm register budget: 128-thread blocks kept resident per SM
  *                     (0 = 4; 1 lane: 4, 5, 6 or 8; more lanes: 3 or 4)
- * With 8 or more lanes per seed (lanes_per_track 8 or 32, or 0 with n_hyp >
- * 4) the lanes merge their lists by keys that hold a tracklet id in 28 bits,
+ * The follower orders extensions by keys that hold a tracklet id in 28 bits,
  * so an index of one timeframe may hold at most 268,435,454 tracklets
  * (TRD_EINVAL beyond).                                                      */
 typedef struct {

@@ -113,79 +113,15 @@ __device__ bool to_layer(TrackState &s, int l, const Params &P, int &chamber)
 }
 
 // ---- small sorted extension list (per lane) ---------------------------------
-template <int NH>
-struct ExtList {
-    // extensions kept in the selection order (score, parent rank, tracklet
-    // id; a missing layer has id kMissing and sorts after tracklets)
-    float score[NH];
-    float chi2[NH];
-    int par[NH];
-    int id[NH];
-    int pos[NH];
-    __device__ __forceinline__ void clear()
-    {
-#pragma unroll
-        for (int k = 0; k < NH; ++k) {
-            score[k] = INFINITY;
-            chi2[k] = 0.0f;
-            par[k] = 0x7fffffff;
-            id[k] = kMissing;
-            pos[k] = -1;
-        }
-    }
-    __device__ __forceinline__ static bool less(float sa, int pa, int ia, float sb, int pb, int ib)
-    {
-        return sa < sb || (sa == sb && (pa < pb || (pa == pb && ia < ib)));
-    }
-    __device__ __forceinline__ void insert(float sc, int parent, int tid, int p, float c2)
-    {
-        if (!less(sc, parent, tid, score[NH - 1], par[NH - 1], id[NH - 1])) return;
-        // shift larger entries up, then place (unrolled, stays in registers)
-        bool placed = false;
-#pragma unroll
-        for (int k = NH - 1; k >= 0; --k) {
-            if (placed) continue;
-            const bool move = k > 0 && less(sc, parent, tid, score[k - 1], par[k - 1], id[k - 1]);
-            if (move) {
-                score[k] = score[k - 1];
-                chi2[k] = chi2[k - 1];
-                par[k] = par[k - 1];
-                id[k] = id[k - 1];
-                pos[k] = pos[k - 1];
-            } else {
-                score[k] = sc;
-                chi2[k] = c2;
-                par[k] = parent;
-                id[k] = tid;
-                pos[k] = p;
-                placed = true;
-            }
-        }
-    }
-    __device__ __forceinline__ void pop()
-    {
-#pragma unroll
-        for (int k = 0; k + 1 < NH; ++k) {
-            score[k] = score[k + 1];
-            chi2[k] = chi2[k + 1];
-            par[k] = par[k + 1];
-            id[k] = id[k + 1];
-            pos[k] = pos[k + 1];
-        }
-        score[NH - 1] = INFINITY;
-        par[NH - 1] = 0x7fffffff;
-        id[NH - 1] = kMissing;
-        pos[NH - 1] = -1;
-    }
-};
-
 // The selection order (score, parent rank, tracklet id) as one unsigned
-// 64-bit key, for the groups' merge: the score's bits made orderable, then
-// the parent (3 bits) and the id (28 bits, kMissing as the largest).  Needs
-// tracklet ids below kKeyIdMask (the library checks the index's size).
+// 64-bit key: the score's bits made orderable, then the parent (3 bits) and
+// the id (28 bits, kMissing as the largest, so a missing layer sorts after
+// tracklets of the same score).  Needs tracklet ids below kKeyIdMask (the
+// library checks the index's size); kNoKey (all ones) marks an empty slot.
 constexpr unsigned kKeyIdMask = 0x0fffffffu;
+constexpr unsigned long long kNoKey = ~0ull;
 
-__device__ __forceinline__ unsigned long long head_key(float s, int par, int id)
+__device__ __forceinline__ unsigned long long sel_key(float s, int par, int id)
 {
     unsigned u = __float_as_uint(s);
     u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
@@ -198,6 +134,103 @@ __device__ __forceinline__ float key_score(unsigned long long k)
     const unsigned t = static_cast<unsigned>(k >> 32);
     return __uint_as_float((t & 0x80000000u) ? (t & 0x7fffffffu) : ~t);
 }
+
+__device__ __forceinline__ int key_parent(unsigned long long k) { return static_cast<int>(static_cast<unsigned>(k) >> 28); }
+
+__device__ __forceinline__ int key_id(unsigned long long k)
+{
+    const unsigned id = static_cast<unsigned>(k) & kKeyIdMask;
+    return id == kKeyIdMask ? kMissing : static_cast<int>(id);
+}
+
+template <int NH>
+struct ExtList {
+    // extensions kept in the selection order, with their chi2 and record
+    // position (-1 for a missing layer)
+    unsigned long long key[NH];
+    float chi2[NH];
+    int pos[NH];
+    __device__ __forceinline__ void clear()
+    {
+#pragma unroll
+        for (int k = 0; k < NH; ++k) {
+            key[k] = kNoKey;
+            chi2[k] = 0.0f;
+            pos[k] = -1;
+        }
+    }
+    __device__ __forceinline__ void insert(float sc, int parent, int tid, int p, float c2)
+    {
+        const unsigned long long kk = sel_key(sc, parent, tid);
+        if (!(kk < key[NH - 1])) return;
+        // shift larger entries up, then place (unrolled, stays in registers)
+        bool placed = false;
+#pragma unroll
+        for (int k = NH - 1; k >= 0; --k) {
+            if (placed) continue;
+            const bool move = k > 0 && kk < key[k - 1];
+            if (move) {
+                key[k] = key[k - 1];
+                chi2[k] = chi2[k - 1];
+                pos[k] = pos[k - 1];
+            } else {
+                key[k] = kk;
+                chi2[k] = c2;
+                pos[k] = p;
+                placed = true;
+            }
+        }
+    }
+    __device__ __forceinline__ void pop()
+    {
+#pragma unroll
+        for (int k = 0; k + 1 < NH; ++k) {
+            key[k] = key[k + 1];
+            chi2[k] = chi2[k + 1];
+            pos[k] = pos[k + 1];
+        }
+        key[NH - 1] = kNoKey;
+        pos[NH - 1] = -1;
+    }
+    __device__ __forceinline__ bool empty() const { return key[0] == kNoKey; }
+    __device__ __forceinline__ unsigned long long head_key() const { return key[0]; }
+    __device__ __forceinline__ float head_score() const { return key_score(key[0]); }
+    __device__ __forceinline__ int head_id() const { return key_id(key[0]); }
+    __device__ __forceinline__ float head_chi2() const { return chi2[0]; }
+    __device__ __forceinline__ int head_pos() const { return pos[0]; }
+};
+
+// One entry (N = 1): plain fields, so no key is built for every candidate.
+template <>
+struct ExtList<1> {
+    float score, c2;
+    int par, id, pos;
+    __device__ __forceinline__ void clear()
+    {
+        score = INFINITY;
+        c2 = 0.0f;
+        par = 0x7fffffff;
+        id = kMissing;
+        pos = -1;
+    }
+    __device__ __forceinline__ void insert(float sc, int parent, int tid, int p, float chi2)
+    {
+        if (sc < score || (sc == score && (parent < par || (parent == par && tid < id)))) {
+            score = sc;
+            c2 = chi2;
+            par = parent;
+            id = tid;
+            pos = p;
+        }
+    }
+    __device__ __forceinline__ void pop() { clear(); }
+    __device__ __forceinline__ bool empty() const { return !(score < INFINITY); }
+    __device__ __forceinline__ unsigned long long head_key() const { return empty() ? kNoKey : sel_key(score, par, id); }
+    __device__ __forceinline__ float head_score() const { return score; }
+    __device__ __forceinline__ int head_id() const { return id; }
+    __device__ __forceinline__ float head_chi2() const { return c2; }
+    __device__ __forceinline__ int head_pos() const { return pos; }
+};
 
 // Road query + candidate tests for one hypothesis at layer l (Sec. 3).
 // The road bounds z_tl to z +- Rz (pad rows r_lo..r_hi) and the measured y to
@@ -842,57 +875,31 @@ __device__ __forceinline__ bool layer_step(int pos, int l, int q, unsigned gmask
     float my_score = INFINITY, my_chi2 = 0.0f;
     int kept = 0;
     if (G == 1) {
-        if (L.score[0] < INFINITY) {
-            my_score = L.score[0];
-            my_id = L.id[0];
-            my_pos = L.pos[0];
-            my_chi2 = L.chi2[0];
+        if (!L.empty()) {
+            my_score = L.head_score();
+            my_id = L.head_id();
+            my_pos = L.head_pos();
+            my_chi2 = L.head_chi2();
             kept = 1;
         }
     } else {
         for (int rr = 0; rr < P.nhyp; ++rr) {
-            // group minimum of the lanes' heads in (score, parent, id) order;
-            // bh is the lane holding it
-            float bs;
-            int bp, bid, bh;
-            if (G >= 8) {
-                // as one 64-bit key (two shuffles a step instead of four); the
-                // keys of the lanes' heads are distinct, so the holder is the
-                // lane whose head equals the minimum
-                const unsigned long long mine = head_key(L.score[0], L.par[0], L.id[0]);
-                unsigned long long best = mine;
+            // group minimum of the lanes' heads in (score, parent, id) order
+            // (two shuffles a step); the keys of the lanes' heads are
+            // distinct, so the holder is the lane whose head equals the minimum
+            const unsigned long long mine = L.head_key();
+            unsigned long long best = mine;
 #pragma unroll
-                for (int off = G / 2; off > 0; off >>= 1) {
-                    const unsigned long long o = __shfl_xor_sync(gmask, best, off, G);
-                    best = o < best ? o : best;
-                }
-                bs = key_score(best);
-                const unsigned lo = static_cast<unsigned>(best);
-                bp = static_cast<int>(lo >> 28);
-                bid = (lo & kKeyIdMask) == kKeyIdMask ? kMissing : static_cast<int>(lo & kKeyIdMask);
-                bh = (__ffs(__ballot_sync(gmask, mine == best) & gmask) - 1) & (G - 1);
-            } else {
-                bs = L.score[0];
-                bp = L.par[0];
-                bid = L.id[0];
-                bh = q;
-#pragma unroll
-                for (int off = G / 2; off > 0; off >>= 1) {
-                    const float os = __shfl_xor_sync(gmask, bs, off, G);
-                    const int op = __shfl_xor_sync(gmask, bp, off, G);
-                    const int oid = __shfl_xor_sync(gmask, bid, off, G);
-                    const int oh = __shfl_xor_sync(gmask, bh, off, G);
-                    if (ExtList<NH>::less(os, op, oid, bs, bp, bid)) {
-                        bs = os;
-                        bp = op;
-                        bid = oid;
-                        bh = oh;
-                    }
-                }
+            for (int off = G / 2; off > 0; off >>= 1) {
+                const unsigned long long o = __shfl_xor_sync(gmask, best, off, G);
+                best = o < best ? o : best;
             }
-            if (!(bs < INFINITY)) break;
-            const float wchi2 = __shfl_sync(gmask, L.chi2[0], bh, G);
-            const int wpos = __shfl_sync(gmask, L.pos[0], bh, G);
+            if (best == kNoKey) break;
+            const float bs = key_score(best);
+            const int bp = key_parent(best), bid = key_id(best);
+            const int bh = (__ffs(__ballot_sync(gmask, mine == best) & gmask) - 1) & (G - 1);
+            const float wchi2 = __shfl_sync(gmask, L.head_chi2(), bh, G);
+            const int wpos = __shfl_sync(gmask, L.head_pos(), bh, G);
             if (q == rr) {
                 my_parent = bp;
                 my_id = bid;
@@ -1180,8 +1187,8 @@ int follow_launch(const trd_ctx *ctx, const trd_seeds_t *seeds, const IndexView 
     int G = lanes_per_track;
     if (G <= 0) G = p->n_hyp <= 1 ? 1 : (p->n_hyp <= 2 ? 2 : (p->n_hyp <= 4 ? 4 : 8));
     if (G < p->n_hyp) return TRD_EINVAL;
-    // groups of 8 or more merge by 64-bit keys that hold 28-bit tracklet ids
-    if (G >= 8 && iv.max_tf_tracklets >= static_cast<int32_t>(trd::kKeyIdMask)) return TRD_EINVAL;
+    // the selection keys hold 28-bit tracklet ids
+    if (iv.max_tf_tracklets >= static_cast<int32_t>(trd::kKeyIdMask)) return TRD_EINVAL;
     const int mb = min_blocks > 0 ? min_blocks : 4;
     // without a caller scratch: one from the device's pool, ordered on s
     void *own = nullptr;
