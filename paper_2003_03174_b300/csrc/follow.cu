@@ -367,6 +367,8 @@ __device__ void scan_candidates(const TrackState &s, int l, int chamber, int cba
     }
 }
 
+constexpr int kRoadWords = 21;  // a hypothesis's road in the group scan's table (17 without EXT)
+
 // Group scan (N > 1): the lanes of a seed's group take its hypotheses one at
 // a time and share each one's road: the road is broadcast from the lane that
 // holds the hypothesis, lane q tests candidates q, q + G, ... (eight at a
@@ -376,10 +378,16 @@ __device__ void scan_candidates(const TrackState &s, int l, int chamber, int cba
 template <int G, int NH, bool EXT>
 __device__ void scan_group(bool mine, const TrackState &s, int l, int chamber, int cbase, float score,
                            const Params &P, const IndexView &ix, float vyy_max_in, float vzz_max, float dx_max,
-                           unsigned gmask, int q, int trig, ExtList<NH> &L)
+                           unsigned gmask, int q, int trig, float *road, ExtList<NH> &L)
 {
     const float tt = layer_tilt_tan(l);
-    // this lane's own road (used when it is broadcast)
+    // this lane's own road, written to its column of the block's road table
+    // (row stride = block size), from which the group reads it when its
+    // hypothesis is scanned: registers only hold the road being scanned
+    // (groups of 8 or more; smaller groups broadcast it by shuffles, which
+    // costs them less than the table's loads)
+    constexpr bool kTable = G >= 8;
+    const int S = blockDim.x;
     float z = 0, yh = 0, yl = 0, W = 0, Rz = 0, syy = 0, syz = 0, c11 = 0, vres = 0, dyp = 0, gate = 0;
     int r_lo = 0, r_hi = 0, b_lo = 0, b_hi = -1, base_ch = 0;
     LinExt e{s.x.hi, s.x.lo, 0.0f, 0.0f};
@@ -414,25 +422,52 @@ __device__ void scan_group(bool mine, const TrackState &s, int l, int chamber, i
         b_lo = ybin_of(yh - half, ix.inv_w, ix.nb);
         b_hi = ybin_of(yh + half, ix.inv_w, ix.nb);
         base_ch = bucket_of(cbase + chamber, 0, 0, ix.nb);
+        if (kTable) {
+            const float v[kRoadWords] = {z, yh, yl, W, Rz, syy, syz, c11, vres, dyp, gate, score,
+                                         __int_as_float(r_lo), __int_as_float(r_hi), __int_as_float(b_lo),
+                                         __int_as_float(b_hi), __int_as_float(base_ch), e.xh, e.xl, e.fr, e.tr};
+            float *own = road + threadIdx.x;
+#pragma unroll
+            for (int k = 0; k < (EXT ? kRoadWords : kRoadWords - 4); ++k) own[k * S] = v[k];
+        }
     }
+    if (kTable) __syncwarp(gmask);
     const float n2 = P.road * P.road;
     for (int h = 0; h < NH; ++h) {  // hypotheses live in lanes 0..NH-1
         if (!__shfl_sync(gmask, static_cast<int>(mine), h, G)) continue;
-        const float hz = __shfl_sync(gmask, z, h, G), hyh = __shfl_sync(gmask, yh, h, G);
-        const float hyl = __shfl_sync(gmask, yl, h, G), hW = __shfl_sync(gmask, W, h, G);
-        const float hRz = __shfl_sync(gmask, Rz, h, G), hsyy = __shfl_sync(gmask, syy, h, G);
-        const float hsyz = __shfl_sync(gmask, syz, h, G), hc11 = __shfl_sync(gmask, c11, h, G);
-        const float hvres = __shfl_sync(gmask, vres, h, G), hdyp = __shfl_sync(gmask, dyp, h, G);
-        const float hgate = __shfl_sync(gmask, gate, h, G), hscore = __shfl_sync(gmask, score, h, G);
-        const int hr_lo = __shfl_sync(gmask, r_lo, h, G), hr_hi = __shfl_sync(gmask, r_hi, h, G);
-        const int hb_lo = __shfl_sync(gmask, b_lo, h, G), hb_hi = __shfl_sync(gmask, b_hi, h, G);
-        const int hbase = __shfl_sync(gmask, base_ch, h, G);
+        float hz, hyh, hyl, hW, hRz, hsyy, hsyz, hc11, hvres, hdyp, hgate, hscore;
+        int hr_lo, hr_hi, hb_lo, hb_hi, hbase;
         LinExt he{};
-        if (EXT) {
-            he.xh = __shfl_sync(gmask, e.xh, h, G);
-            he.xl = __shfl_sync(gmask, e.xl, h, G);
-            he.fr = __shfl_sync(gmask, e.fr, h, G);
-            he.tr = __shfl_sync(gmask, e.tr, h, G);
+        if (kTable) {
+            const float *hr = road + (threadIdx.x & ~(G - 1)) + h;  // lane h of this group
+            hz = hr[0], hyh = hr[S], hyl = hr[2 * S], hW = hr[3 * S], hRz = hr[4 * S];
+            hsyy = hr[5 * S], hsyz = hr[6 * S], hc11 = hr[7 * S], hvres = hr[8 * S];
+            hdyp = hr[9 * S], hgate = hr[10 * S], hscore = hr[11 * S];
+            hr_lo = __float_as_int(hr[12 * S]), hr_hi = __float_as_int(hr[13 * S]);
+            hb_lo = __float_as_int(hr[14 * S]), hb_hi = __float_as_int(hr[15 * S]);
+            hbase = __float_as_int(hr[16 * S]);
+            if (EXT) {
+                he.xh = hr[17 * S];
+                he.xl = hr[18 * S];
+                he.fr = hr[19 * S];
+                he.tr = hr[20 * S];
+            }
+        } else {
+            hz = __shfl_sync(gmask, z, h, G), hyh = __shfl_sync(gmask, yh, h, G);
+            hyl = __shfl_sync(gmask, yl, h, G), hW = __shfl_sync(gmask, W, h, G);
+            hRz = __shfl_sync(gmask, Rz, h, G), hsyy = __shfl_sync(gmask, syy, h, G);
+            hsyz = __shfl_sync(gmask, syz, h, G), hc11 = __shfl_sync(gmask, c11, h, G);
+            hvres = __shfl_sync(gmask, vres, h, G), hdyp = __shfl_sync(gmask, dyp, h, G);
+            hgate = __shfl_sync(gmask, gate, h, G), hscore = __shfl_sync(gmask, score, h, G);
+            hr_lo = __shfl_sync(gmask, r_lo, h, G), hr_hi = __shfl_sync(gmask, r_hi, h, G);
+            hb_lo = __shfl_sync(gmask, b_lo, h, G), hb_hi = __shfl_sync(gmask, b_hi, h, G);
+            hbase = __shfl_sync(gmask, base_ch, h, G);
+            if (EXT) {
+                he.xh = __shfl_sync(gmask, e.xh, h, G);
+                he.xl = __shfl_sync(gmask, e.xl, h, G);
+                he.fr = __shfl_sync(gmask, e.fr, h, G);
+                he.tr = __shfl_sync(gmask, e.tr, h, G);
+            }
         }
         for (int r = hr_lo; r <= hr_hi; r += 3) {
             // up to three pad rows: their six bounds are loaded together
@@ -479,6 +514,7 @@ __device__ void scan_group(bool mine, const TrackState &s, int l, int chamber, i
             }
         }
     }
+    if (kTable) __syncwarp(gmask);  // the table is rewritten at the next layer
 }
 
 struct Snapshot {  // pre-transport copy of lane 0's state, in shared memory
@@ -852,8 +888,8 @@ __device__ __forceinline__ bool start_seed(int pos, int q, const SeedsView &sv, 
 // (result written).
 template <int G, int NH, bool EXT>
 __device__ __forceinline__ bool layer_step(int pos, int l, int q, unsigned gmask, const IndexView &ix, const Params &P,
-                                           float4 *res, float *sm, int stride, float vyy_max, float vzz_max,
-                                           float dx_max, Lane &H)
+                                           float4 *res, float *sm, int stride, float *road, float vyy_max,
+                                           float vzz_max, float dx_max, Lane &H)
 {
     TrackState &s = H.s;
     if (q == 0) save_state(sm, stride, s);
@@ -866,7 +902,7 @@ __device__ __forceinline__ bool layer_step(int pos, int l, int q, unsigned gmask
             scan_candidates<NH, EXT>(s, l, chamber, H.cbase, H.score, P, ix, vyy_max, vzz_max, dx_max, H.trig, L);
     } else {
         scan_group<G, NH, EXT>(live && chamber >= 0, s, l, chamber, H.cbase, H.score, P, ix, vyy_max, vzz_max,
-                               dx_max, gmask, q, H.trig, L);
+                               dx_max, gmask, q, H.trig, road, L);
     }
     if (live && H.nmiss < P.maxmiss) L.insert(H.score + P.pmiss, q, kMissing, -1, 0.0f);
 
@@ -998,6 +1034,7 @@ k_follow(SeedsView sv, IndexView ix, Params P, ParkedView pk, int *counter)
     const int lane = threadIdx.x & 31;
     const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
     float *sm = smem + g;
+    float *road = smem + 24 * groups;  // the group scan's road table (G >= 8)
     const float vyy_max = __uint_as_float(__ldg(&ix.stats[0]));
     const float vzz_max = __uint_as_float(__ldg(&ix.stats[1]));
     const float dx_max = EXT && ix.recx ? __uint_as_float(__ldg(&ix.stats[3])) : 0.0f;
@@ -1011,8 +1048,8 @@ k_follow(SeedsView sv, IndexView ix, Params P, ParkedView pk, int *counter)
         int i;
         bool have = pos < sv.n && start_seed<G>(pos, q, sv, pk, H, i);
         for (int l = 0; l < kLayers && __any_sync(0xffffffffu, have); ++l) {
-            if (have && layer_step<G, NH, EXT>(pos, l, q, gmask, ix, P, pk.rec, sm, groups, vyy_max, vzz_max,
-                                               dx_max, H))
+            if (have && layer_step<G, NH, EXT>(pos, l, q, gmask, ix, P, pk.rec, sm, groups, road, vyy_max,
+                                               vzz_max, dx_max, H))
                 have = false;
         }
     }
@@ -1085,7 +1122,8 @@ static int launch(const trd_ctx *ctx, const SeedsView &sv, const IndexView &ix, 
         return TRD_OK;
     }
     const int groups = block / G;
-    const size_t smem = sizeof(float) * 24 * groups;
+    // snapshots (24 floats per group), then the group scan's road table
+    const size_t smem = sizeof(float) * (24 * groups + (G >= 8 ? (EXT ? kRoadWords : kRoadWords - 4) * block : 0));
     void (*kernel)(SeedsView, IndexView, Params, ParkedView, int *) = k_follow<G, NH, MINB, EXT>;
     int per_sm = 0;
     TRD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem));
