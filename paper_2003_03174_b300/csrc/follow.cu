@@ -371,23 +371,19 @@ constexpr int kRoadWords = 21;  // a hypothesis's road in the group scan's table
 
 // Group scan (N > 1): the lanes of a seed's group take its hypotheses one at
 // a time and share each one's road: the road is broadcast from the lane that
-// holds the hypothesis, lane q tests candidates q, q + G, ... (eight at a
+// holds the hypothesis, lane q tests candidates q, q + G, ... (four at a
 // time), and every extension records its parent.  The candidate set, the
 // arithmetic and the selection order are those of one lane scanning its own
-// hypothesis; the work is spread evenly over the group.
+// hypothesis; the work is spread evenly over the group.  This version
+// broadcasts by shuffles (groups of 2 and 4); groups of 8 or more use
+// group_road / group_scan below, through a road table in shared memory.
 template <int G, int NH, bool EXT>
 __device__ void scan_group(bool mine, const TrackState &s, int l, int chamber, int cbase, float score,
                            const Params &P, const IndexView &ix, float vyy_max_in, float vzz_max, float dx_max,
-                           unsigned gmask, int q, int trig, float *road, ExtList<NH> &L)
+                           unsigned gmask, int q, int trig, ExtList<NH> &L)
 {
     const float tt = layer_tilt_tan(l);
-    // this lane's own road, written to its column of the block's road table
-    // (row stride = block size), from which the group reads it when its
-    // hypothesis is scanned: registers only hold the road being scanned
-    // (groups of 8 or more; smaller groups broadcast it by shuffles, which
-    // costs them less than the table's loads)
-    constexpr bool kTable = G >= 8;
-    const int S = blockDim.x;
+    // this lane's own road (used when it is broadcast)
     float z = 0, yh = 0, yl = 0, W = 0, Rz = 0, syy = 0, syz = 0, c11 = 0, vres = 0, dyp = 0, gate = 0;
     int r_lo = 0, r_hi = 0, b_lo = 0, b_hi = -1, base_ch = 0;
     LinExt e{s.x.hi, s.x.lo, 0.0f, 0.0f};
@@ -422,52 +418,25 @@ __device__ void scan_group(bool mine, const TrackState &s, int l, int chamber, i
         b_lo = ybin_of(yh - half, ix.inv_w, ix.nb);
         b_hi = ybin_of(yh + half, ix.inv_w, ix.nb);
         base_ch = bucket_of(cbase + chamber, 0, 0, ix.nb);
-        if (kTable) {
-            const float v[kRoadWords] = {z, yh, yl, W, Rz, syy, syz, c11, vres, dyp, gate, score,
-                                         __int_as_float(r_lo), __int_as_float(r_hi), __int_as_float(b_lo),
-                                         __int_as_float(b_hi), __int_as_float(base_ch), e.xh, e.xl, e.fr, e.tr};
-            float *own = road + threadIdx.x;
-#pragma unroll
-            for (int k = 0; k < (EXT ? kRoadWords : kRoadWords - 4); ++k) own[k * S] = v[k];
-        }
     }
-    if (kTable) __syncwarp(gmask);
     const float n2 = P.road * P.road;
     for (int h = 0; h < NH; ++h) {  // hypotheses live in lanes 0..NH-1
         if (!__shfl_sync(gmask, static_cast<int>(mine), h, G)) continue;
-        float hz, hyh, hyl, hW, hRz, hsyy, hsyz, hc11, hvres, hdyp, hgate, hscore;
-        int hr_lo, hr_hi, hb_lo, hb_hi, hbase;
+        const float hz = __shfl_sync(gmask, z, h, G), hyh = __shfl_sync(gmask, yh, h, G);
+        const float hyl = __shfl_sync(gmask, yl, h, G), hW = __shfl_sync(gmask, W, h, G);
+        const float hRz = __shfl_sync(gmask, Rz, h, G), hsyy = __shfl_sync(gmask, syy, h, G);
+        const float hsyz = __shfl_sync(gmask, syz, h, G), hc11 = __shfl_sync(gmask, c11, h, G);
+        const float hvres = __shfl_sync(gmask, vres, h, G), hdyp = __shfl_sync(gmask, dyp, h, G);
+        const float hgate = __shfl_sync(gmask, gate, h, G), hscore = __shfl_sync(gmask, score, h, G);
+        const int hr_lo = __shfl_sync(gmask, r_lo, h, G), hr_hi = __shfl_sync(gmask, r_hi, h, G);
+        const int hb_lo = __shfl_sync(gmask, b_lo, h, G), hb_hi = __shfl_sync(gmask, b_hi, h, G);
+        const int hbase = __shfl_sync(gmask, base_ch, h, G);
         LinExt he{};
-        if (kTable) {
-            const float *hr = road + (threadIdx.x & ~(G - 1)) + h;  // lane h of this group
-            hz = hr[0], hyh = hr[S], hyl = hr[2 * S], hW = hr[3 * S], hRz = hr[4 * S];
-            hsyy = hr[5 * S], hsyz = hr[6 * S], hc11 = hr[7 * S], hvres = hr[8 * S];
-            hdyp = hr[9 * S], hgate = hr[10 * S], hscore = hr[11 * S];
-            hr_lo = __float_as_int(hr[12 * S]), hr_hi = __float_as_int(hr[13 * S]);
-            hb_lo = __float_as_int(hr[14 * S]), hb_hi = __float_as_int(hr[15 * S]);
-            hbase = __float_as_int(hr[16 * S]);
-            if (EXT) {
-                he.xh = hr[17 * S];
-                he.xl = hr[18 * S];
-                he.fr = hr[19 * S];
-                he.tr = hr[20 * S];
-            }
-        } else {
-            hz = __shfl_sync(gmask, z, h, G), hyh = __shfl_sync(gmask, yh, h, G);
-            hyl = __shfl_sync(gmask, yl, h, G), hW = __shfl_sync(gmask, W, h, G);
-            hRz = __shfl_sync(gmask, Rz, h, G), hsyy = __shfl_sync(gmask, syy, h, G);
-            hsyz = __shfl_sync(gmask, syz, h, G), hc11 = __shfl_sync(gmask, c11, h, G);
-            hvres = __shfl_sync(gmask, vres, h, G), hdyp = __shfl_sync(gmask, dyp, h, G);
-            hgate = __shfl_sync(gmask, gate, h, G), hscore = __shfl_sync(gmask, score, h, G);
-            hr_lo = __shfl_sync(gmask, r_lo, h, G), hr_hi = __shfl_sync(gmask, r_hi, h, G);
-            hb_lo = __shfl_sync(gmask, b_lo, h, G), hb_hi = __shfl_sync(gmask, b_hi, h, G);
-            hbase = __shfl_sync(gmask, base_ch, h, G);
-            if (EXT) {
-                he.xh = __shfl_sync(gmask, e.xh, h, G);
-                he.xl = __shfl_sync(gmask, e.xl, h, G);
-                he.fr = __shfl_sync(gmask, e.fr, h, G);
-                he.tr = __shfl_sync(gmask, e.tr, h, G);
-            }
+        if (EXT) {
+            he.xh = __shfl_sync(gmask, e.xh, h, G);
+            he.xl = __shfl_sync(gmask, e.xl, h, G);
+            he.fr = __shfl_sync(gmask, e.fr, h, G);
+            he.tr = __shfl_sync(gmask, e.tr, h, G);
         }
         for (int r = hr_lo; r <= hr_hi; r += 3) {
             // up to three pad rows: their six bounds are loaded together
@@ -514,7 +483,125 @@ __device__ void scan_group(bool mine, const TrackState &s, int l, int chamber, i
             }
         }
     }
-    if (kTable) __syncwarp(gmask);  // the table is rewritten at the next layer
+}
+
+// Groups of 8 or more, in two steps around a parking of each lane's state in
+// shared memory: each lane writes its own road to its column of the block's
+// road table (row stride = block size), then the group scans its hypotheses
+// reading each one's road from the table.  Neither step needs the lanes'
+// states, so they wait in shared memory meanwhile and the registers hold one
+// road and the lists: 96 registers with 8 B of spill, 5 blocks per SM.
+template <int G, bool EXT>
+__device__ __forceinline__ void group_road(bool mine, const TrackState &s, int l, int chamber, int cbase, float score,
+                                           const Params &P, const IndexView &ix, float vyy_max_in, float vzz_max,
+                                           float dx_max, float *road)
+{
+    if (!mine) return;
+    const int S = blockDim.x;
+    const float tt = layer_tilt_tan(l);
+    const float f = s.f;
+    const float r = sqrtf((1.0f - f) * (1.0f + f));
+    const float uu = f / r - lorentz_tan(P.bz);
+    const float vres = kSigY0 * kSigY0 + kSigY1 * kSigY1 * uu * uu;
+    const float vyy_max = P.resmode ? vres : vyy_max_in;
+    const float c10 = s.c[1], c11 = s.c[2];
+    const float syy = s.c[0] - 2.0f * tt * c10 + tt * tt * c11;
+    const float syz = c10 - tt * c11;
+    float W = P.road * sqrtf(fmaxf(syy + vyy_max, 0.0f)) * 1.0001f + 1e-4f;
+    float Rz = P.road * sqrtf(fmaxf(c11 + vzz_max, 0.0f)) * 1.0001f + 1e-4f;
+    LinExt e{s.x.hi, s.x.lo, 0.0f, 0.0f};
+    if (EXT && ix.recx) {
+        e.fr = f / r;
+        e.tr = s.t / r;
+        const float dxb = dx_max + fabsf(df_to_f(df_add(s.x, df_neg(layer_x_df(l))))) + 1e-4f;
+        W += dxb * fabsf(e.fr) * 1.0001f;
+        Rz += dxb * fabsf(e.tr) * 1.0001f;
+    }
+    const float dyp = kDriftLength * uu;
+    const float gate = P.gate * sqrtf(kSigDy0 * kSigDy0 + kSigDy1 * kSigDy1 * uu * uu);
+    const float z = s.z, yh = s.y.hi, yl = s.y.lo;
+    const float zlo = stack_z_lo(stack_of_chamber(chamber));
+    const int r_lo = row_of_z(z - Rz, zlo), r_hi = row_of_z(z + Rz, zlo);
+    const float half = W + fabsf(tt) * Rz + 1e-3f + 1e-6f * fabsf(yh);
+    const int b_lo = ybin_of(yh - half, ix.inv_w, ix.nb), b_hi = ybin_of(yh + half, ix.inv_w, ix.nb);
+    const int base_ch = bucket_of(cbase + chamber, 0, 0, ix.nb);
+    const float v[kRoadWords] = {z, yh, yl, W, Rz, syy, syz, c11, vres, dyp, gate, score,
+                                 __int_as_float(r_lo), __int_as_float(r_hi), __int_as_float(b_lo),
+                                 __int_as_float(b_hi), __int_as_float(base_ch), e.xh, e.xl, e.fr, e.tr};
+    float *own = road + threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < (EXT ? kRoadWords : kRoadWords - 4); ++k) own[k * S] = v[k];
+}
+
+template <int G, int NH, bool EXT>
+__device__ __forceinline__ void group_scan(bool mine, int l, const Params &P, const IndexView &ix, unsigned gmask,
+                                           int trig, const float *road, ExtList<NH> &L)
+{
+    const int S = blockDim.x;
+    const float tt = layer_tilt_tan(l);
+    const float n2 = P.road * P.road;
+    __syncwarp(gmask);
+    for (int h = 0; h < NH; ++h) {  // hypotheses live in lanes 0..NH-1
+        if (!__shfl_sync(gmask, static_cast<int>(mine), h, G)) continue;
+        const float *hr = road + (threadIdx.x & ~(G - 1)) + h;  // lane h of this group
+        const float hz = hr[0], hyh = hr[S], hyl = hr[2 * S], hW = hr[3 * S], hRz = hr[4 * S];
+        const float hsyy = hr[5 * S], hsyz = hr[6 * S], hc11 = hr[7 * S], hvres = hr[8 * S];
+        const float hdyp = hr[9 * S], hgate = hr[10 * S], hscore = hr[11 * S];
+        const int hr_lo = __float_as_int(hr[12 * S]), hr_hi = __float_as_int(hr[13 * S]);
+        const int hb_lo = __float_as_int(hr[14 * S]), hb_hi = __float_as_int(hr[15 * S]);
+        const int hbase = __float_as_int(hr[16 * S]);
+        LinExt he{};
+        if (EXT) {
+            he.xh = hr[17 * S];
+            he.xl = hr[18 * S];
+            he.fr = hr[19 * S];
+            he.tr = hr[20 * S];
+        }
+        const int q = threadIdx.x & (G - 1);
+        for (int r = hr_lo; r <= hr_hi; r += 3) {
+            const int base = hbase + r * ix.nb;
+            const int beg0 = __ldg(&ix.offsets[base + hb_lo]);
+            const int end0 = __ldg(&ix.offsets[base + hb_hi + 1]);
+            int beg1 = 0, end1 = 0, beg2 = 0, end2 = 0;
+            if (r + 1 <= hr_hi) {
+                beg1 = __ldg(&ix.offsets[base + ix.nb + hb_lo]);
+                end1 = __ldg(&ix.offsets[base + ix.nb + hb_hi + 1]);
+            }
+            if (r + 2 <= hr_hi) {
+                beg2 = __ldg(&ix.offsets[base + 2 * ix.nb + hb_lo]);
+                end2 = __ldg(&ix.offsets[base + 2 * ix.nb + hb_hi + 1]);
+            }
+            const int n0 = end0 - beg0;
+            const int n01 = n0 + (end1 - beg1);
+            const int n = n01 + (end2 - beg2);
+            const int per_lane = (n + G - 1) / G;
+            for (int u0 = 0; u0 < per_lane; u0 += 4) {
+                float4 c[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int j = q + G * (u0 + u);
+                    const int pos = j < n0 ? beg0 + j : (j < n01 ? beg1 + (j - n0) : beg2 + (j - n01));
+                    c[u] = j < n ? __ldg(&ix.rec[2 * pos]) : make_float4(INFINITY, INFINITY, INFINITY, 0.0f);
+                }
+                unsigned mask = 0;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float ry = (__fsub_rn(c[u].x, hyh) - hyl) + tt * (hz - c[u].y);
+                    const float rz = c[u].y - hz;
+                    if (fabsf(ry) <= hW && fabsf(rz) <= hRz && !(fabsf(c[u].z - hdyp) > hgate)) mask |= 1u << u;
+                }
+                while (mask) {
+                    const int u = __ffs(mask) - 1;
+                    mask &= mask - 1u;
+                    const int j = q + G * (u0 + u);
+                    const int pos = j < n0 ? beg0 + j : (j < n01 ? beg1 + (j - n0) : beg2 + (j - n01));
+                    full_test<NH, EXT>(pos, ix, tt, hz, hyh, hyl, n2, hsyy, hsyz, hc11, hvres, P.resmode, hdyp,
+                                       hgate, P.cut, hscore, h, trig, he, L);
+                }
+            }
+        }
+    }
+    __syncwarp(gmask);  // the table is rewritten at the next layer
 }
 
 struct Snapshot {  // pre-transport copy of lane 0's state, in shared memory
@@ -633,6 +720,48 @@ struct Lane {
     int ids[kLayers];
     bool alive;
 };
+
+constexpr int kParkWords = 33;  // a lane's state (24) and bookkeeping (9) while its group scans
+
+__device__ __forceinline__ void park(float *pk, int S, const TrackState &s, const Lane &H)
+{
+    pk[0] = s.x.hi;
+    pk[S] = s.x.lo;
+    pk[2 * S] = s.y.hi;
+    pk[3 * S] = s.y.lo;
+    pk[4 * S] = s.z;
+    pk[5 * S] = s.f;
+    pk[6 * S] = s.t;
+    pk[7 * S] = s.k;
+#pragma unroll
+    for (int k = 0; k < 15; ++k) pk[(8 + k) * S] = s.c[k];
+    pk[23 * S] = __int_as_float(s.sector);
+    pk[24 * S] = H.chisum;
+    pk[25 * S] = __int_as_float(H.ntrk);
+    pk[26 * S] = __int_as_float(H.nmiss);
+#pragma unroll
+    for (int k = 0; k < kLayers; ++k) pk[(27 + k) * S] = __int_as_float(H.ids[k]);
+}
+
+__device__ __forceinline__ void unpark(const float *pk, int S, TrackState &s, Lane &H)
+{
+    s.x.hi = pk[0];
+    s.x.lo = pk[S];
+    s.y.hi = pk[2 * S];
+    s.y.lo = pk[3 * S];
+    s.z = pk[4 * S];
+    s.f = pk[5 * S];
+    s.t = pk[6 * S];
+    s.k = pk[7 * S];
+#pragma unroll
+    for (int k = 0; k < 15; ++k) s.c[k] = pk[(8 + k) * S];
+    s.sector = __float_as_int(pk[23 * S]);
+    H.chisum = pk[24 * S];
+    H.ntrk = __float_as_int(pk[25 * S]);
+    H.nmiss = __float_as_int(pk[26 * S]);
+#pragma unroll
+    for (int k = 0; k < kLayers; ++k) H.ids[k] = __float_as_int(pk[(27 + k) * S]);
+}
 
 // ---- processing order ---------------------------------------------------------
 // The follower takes seeds in order of decreasing |q/pT| (bins of 1/28 c/GeV;
@@ -900,9 +1029,17 @@ __device__ __forceinline__ bool layer_step(int pos, int l, int q, unsigned gmask
     if (G == 1) {
         if (live && chamber >= 0)
             scan_candidates<NH, EXT>(s, l, chamber, H.cbase, H.score, P, ix, vyy_max, vzz_max, dx_max, H.trig, L);
+    } else if (G >= 8) {
+        const bool mine = live && chamber >= 0;
+        group_road<G, EXT>(mine, s, l, chamber, H.cbase, H.score, P, ix, vyy_max, vzz_max, dx_max, road);
+        const int S = blockDim.x;
+        float *pk = road + (EXT ? kRoadWords : kRoadWords - 4) * S + threadIdx.x;
+        park(pk, S, s, H);
+        group_scan<G, NH, EXT>(mine, l, P, ix, gmask, H.trig, road, L);
+        unpark(pk, S, s, H);
     } else {
         scan_group<G, NH, EXT>(live && chamber >= 0, s, l, chamber, H.cbase, H.score, P, ix, vyy_max, vzz_max,
-                               dx_max, gmask, q, H.trig, road, L);
+                               dx_max, gmask, q, H.trig, L);
     }
     if (live && H.nmiss < P.maxmiss) L.insert(H.score + P.pmiss, q, kMissing, -1, 0.0f);
 
@@ -1123,7 +1260,8 @@ static int launch(const trd_ctx *ctx, const SeedsView &sv, const IndexView &ix, 
     }
     const int groups = block / G;
     // snapshots (24 floats per group), then the group scan's road table
-    const size_t smem = sizeof(float) * (24 * groups + (G >= 8 ? (EXT ? kRoadWords : kRoadWords - 4) * block : 0));
+    const size_t smem =
+        sizeof(float) * (24 * groups + (G >= 8 ? ((EXT ? kRoadWords : kRoadWords - 4) + kParkWords) * block : 0));
     void (*kernel)(SeedsView, IndexView, Params, ParkedView, int *) = k_follow<G, NH, MINB, EXT>;
     int per_sm = 0;
     TRD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem));
@@ -1164,6 +1302,8 @@ static int dispatch(const trd_ctx *ctx, const SeedsView &sv, const IndexView &iv
     // up to six hypotheses in a group of 8: lists of 6 (fewer registers)
     case 8 * 16 + 3: return nhyp <= 6 ? TRD_LAUNCH(8, 6, 3) : TRD_LAUNCH(8, 8, 3);
     case 8 * 16 + 4: return nhyp <= 6 ? TRD_LAUNCH(8, 6, 4) : TRD_LAUNCH(8, 8, 4);
+    case 8 * 16 + 5: return nhyp <= 6 ? TRD_LAUNCH(8, 6, 5) : TRD_LAUNCH(8, 8, 5);
+    case 8 * 16 + 6: return nhyp <= 6 ? TRD_LAUNCH(8, 6, 6) : TRD_LAUNCH(8, 8, 6);
     case 32 * 16 + 3: return TRD_LAUNCH(32, 8, 3);
     case 32 * 16 + 4: return TRD_LAUNCH(32, 8, 4);
     default: return TRD_EINVAL;
