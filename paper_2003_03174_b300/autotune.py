@@ -30,9 +30,9 @@ def search_space(n_hyp: int):
     lanes = 2 if n_hyp <= 2 else (4 if n_hyp <= 4 else 8)
     for g in sorted({lanes, min(8, 2 * lanes), 32}):
         if g >= n_hyp and g > 1 and (g, 128, 3) not in shapes:
-            # groups of 8 park their lanes' states during the scan, which
-            # lets 5 and 6 blocks per SM fit
-            shapes += [(g, 128, m) for m in ((3, 4, 5, 6) if g == 8 else (3, 4))]
+            # groups of 2 to 8 can park their lanes' states during the scan,
+            # which lets 5 and 6 blocks per SM fit
+            shapes += [(g, 128, m) for m in ((3, 4, 5, 6) if g <= 8 else (3, 4))]
     return shapes
 
 

@@ -723,6 +723,12 @@ struct Lane {
 
 constexpr int kParkWords = 33;  // a lane's state (24) and bookkeeping (9) while its group scans
 
+// Which instances scan through the road table with the lanes' states parked:
+// groups of 8 or more always; smaller groups with 5 or more blocks per SM,
+// whose register budget only that fits (with 3 or 4 blocks per SM their
+// shuffle broadcast is faster).
+__host__ __device__ constexpr bool parks(int G, int MINB) { return G >= 8 || (G > 1 && MINB >= 5); }
+
 __device__ __forceinline__ void park(float *pk, int S, const TrackState &s, const Lane &H)
 {
     pk[0] = s.x.hi;
@@ -1015,7 +1021,7 @@ __device__ __forceinline__ bool start_seed(int pos, int q, const SeedsView &sv, 
 
 // One layer of seed i for the group.  Returns true when the seed is finished
 // (result written).
-template <int G, int NH, bool EXT>
+template <int G, int NH, bool EXT, bool PARK>
 __device__ __forceinline__ bool layer_step(int pos, int l, int q, unsigned gmask, const IndexView &ix, const Params &P,
                                            float4 *res, float *sm, int stride, float *road, float vyy_max,
                                            float vzz_max, float dx_max, Lane &H)
@@ -1029,7 +1035,7 @@ __device__ __forceinline__ bool layer_step(int pos, int l, int q, unsigned gmask
     if (G == 1) {
         if (live && chamber >= 0)
             scan_candidates<NH, EXT>(s, l, chamber, H.cbase, H.score, P, ix, vyy_max, vzz_max, dx_max, H.trig, L);
-    } else if (G >= 8) {
+    } else if (PARK) {
         const bool mine = live && chamber >= 0;
         group_road<G, EXT>(mine, s, l, chamber, H.cbase, H.score, P, ix, vyy_max, vzz_max, dx_max, road);
         const int S = blockDim.x;
@@ -1171,7 +1177,7 @@ k_follow(SeedsView sv, IndexView ix, Params P, ParkedView pk, int *counter)
     const int lane = threadIdx.x & 31;
     const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
     float *sm = smem + g;
-    float *road = smem + 24 * groups;  // the group scan's road table (G >= 8)
+    float *road = smem + 24 * groups;  // the group scan's road table and parked states
     const float vyy_max = __uint_as_float(__ldg(&ix.stats[0]));
     const float vzz_max = __uint_as_float(__ldg(&ix.stats[1]));
     const float dx_max = EXT && ix.recx ? __uint_as_float(__ldg(&ix.stats[3])) : 0.0f;
@@ -1185,7 +1191,7 @@ k_follow(SeedsView sv, IndexView ix, Params P, ParkedView pk, int *counter)
         int i;
         bool have = pos < sv.n && start_seed<G>(pos, q, sv, pk, H, i);
         for (int l = 0; l < kLayers && __any_sync(0xffffffffu, have); ++l) {
-            if (have && layer_step<G, NH, EXT>(pos, l, q, gmask, ix, P, pk.rec, sm, groups, road, vyy_max,
+            if (have && layer_step<G, NH, EXT, parks(G, MINB)>(pos, l, q, gmask, ix, P, pk.rec, sm, groups, road, vyy_max,
                                                vzz_max, dx_max, H))
                 have = false;
         }
@@ -1261,7 +1267,7 @@ static int launch(const trd_ctx *ctx, const SeedsView &sv, const IndexView &ix, 
     const int groups = block / G;
     // snapshots (24 floats per group), then the group scan's road table
     const size_t smem =
-        sizeof(float) * (24 * groups + (G >= 8 ? ((EXT ? kRoadWords : kRoadWords - 4) + kParkWords) * block : 0));
+        sizeof(float) * (24 * groups + (parks(G, MINB) ? ((EXT ? kRoadWords : kRoadWords - 4) + kParkWords) * block : 0));
     void (*kernel)(SeedsView, IndexView, Params, ParkedView, int *) = k_follow<G, NH, MINB, EXT>;
     int per_sm = 0;
     TRD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem));
@@ -1296,9 +1302,13 @@ static int dispatch(const trd_ctx *ctx, const SeedsView &sv, const IndexView &iv
     case 1 * 16 + 8: return nhyp == 1 ? TRD_LAUNCH(1, 1, 8) : TRD_EINVAL;
     case 2 * 16 + 3: return TRD_LAUNCH(2, 2, 3);
     case 2 * 16 + 4: return TRD_LAUNCH(2, 2, 4);
+    case 2 * 16 + 5: return TRD_LAUNCH(2, 2, 5);
+    case 2 * 16 + 6: return TRD_LAUNCH(2, 2, 6);
     // up to three hypotheses in a group of 4: lists of 3
     case 4 * 16 + 3: return nhyp <= 3 ? TRD_LAUNCH(4, 3, 3) : TRD_LAUNCH(4, 4, 3);
     case 4 * 16 + 4: return nhyp <= 3 ? TRD_LAUNCH(4, 3, 4) : TRD_LAUNCH(4, 4, 4);
+    case 4 * 16 + 5: return nhyp <= 3 ? TRD_LAUNCH(4, 3, 5) : TRD_LAUNCH(4, 4, 5);
+    case 4 * 16 + 6: return nhyp <= 3 ? TRD_LAUNCH(4, 3, 6) : TRD_LAUNCH(4, 4, 6);
     // up to six hypotheses in a group of 8: lists of 6 (fewer registers)
     case 8 * 16 + 3: return nhyp <= 6 ? TRD_LAUNCH(8, 6, 3) : TRD_LAUNCH(8, 8, 3);
     case 8 * 16 + 4: return nhyp <= 6 ? TRD_LAUNCH(8, 6, 4) : TRD_LAUNCH(8, 8, 4);
