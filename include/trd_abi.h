@@ -226,8 +226,9 @@ TRD_API int trd_follow(trd_ctx_t *ctx, const trd_seeds_t *seeds, const trd_index
  *                     (0 = smallest power of two >= n_hyp; 1 needs n_hyp = 1)
  *   block_threads     64 or 128 (0 = 128)
  *   min_blocks_per_sm register budget: 128-thread blocks kept resident per SM
- *                     (0 = 4; 1 lane: 4, 5, 6 or 8; 2, 4 or 8 lanes: 3, 4, 5
- *                     or 6; 32 lanes: 3 or 4)
+ *                     (1 lane: 4, 5, 6 or 8; 2, 4 or 8 lanes: 3, 4, 5 or 6;
+ *                     32 lanes: 3 or 4; 0 = 4 for 1 or 32 lanes, 5 for 8,
+ *                     6 for 2 or 4)
  * The follower orders extensions by keys that hold a tracklet id in 28 bits,
  * so an index of one timeframe may hold at most 268,435,454 tracklets
  * (TRD_EINVAL beyond).                                                      */

@@ -1377,7 +1377,10 @@ int follow_launch(const trd_ctx *ctx, const trd_seeds_t *seeds, const IndexView 
     if (G < p->n_hyp) return TRD_EINVAL;
     // the selection keys hold 28-bit tracklet ids
     if (iv.max_tf_tracklets >= static_cast<int32_t>(trd::kKeyIdMask)) return TRD_EINVAL;
-    const int mb = min_blocks > 0 ? min_blocks : 4;
+    // default register budget: the fastest on the benchmark's workloads
+    // (one lane: 4 blocks per SM; groups of 2 and 4 with parked states: 6;
+    // groups of 8: 5; whole warps: 4)
+    const int mb = min_blocks > 0 ? min_blocks : (G == 1 || G == 32 ? 4 : (G == 8 ? 5 : 6));
     // without a caller scratch: one from the device's pool, ordered on s
     void *own = nullptr;
     if (sv.n > 0 && !parked) {
