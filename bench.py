@@ -76,12 +76,12 @@ REFIT_FLOPS_PER_LAYER = 460
 # is still in L2 when the kernel ends), valid only for the source measured.
 REFIT_TRAFFIC = {"source_sha256_16": "89b8201dbc53c40e", "bytes": 39.88e6}
 # DRAM bytes (read + write) of one trd_follow call on this workload from one
-# ncu capture per kernel (k_seed_key 0.82 MB, k_seed_prepare 24.11 MB,
-# k_follow 62.79 MB, k_results_gather 26.45 MB; ncu empties the caches
+# ncu capture per kernel (k_seed_key 0.82 MB, k_seed_prepare 23.98 MB,
+# k_follow 62.82 MB, k_results_gather 26.46 MB; ncu empties the caches
 # before each kernel, so the gather's reads of the staged results, L2 hits in
 # a plain run, count here), valid only for the kernel source it was measured
 # on: reported as null once follow.cu, trd_device.cuh or track_model.cuh change.
-FOLLOW_TRAFFIC = {"source_sha256_16": "3a88471c4cfb1395", "bytes": 114.17e6, "k_follow": 62.79e6}
+FOLLOW_TRAFFIC = {"source_sha256_16": "65a8227b1d664b2d", "bytes": 114.07e6, "k_follow": 62.82e6}
 # DRAM bytes (read 206.49 MB + write 12.93 MB) of one k_residuals launch on the
 # 100,000-track map from one ncu capture; the 450,000-track map holds ~3 GB on
 # the device and is not captured, so the figure is reported for the captured
@@ -320,30 +320,17 @@ def served_summary(inputs, args, ctx):
             "results_identical": m["results_identical"]}
 
 
-def _make_calibration(seed):
-    from synth import make_workload
-    return make_workload("calibration", seed=seed)
-
-
-def start_calibration_inputs():
-    """The calibration pass's workload (450k seeds, 2.24 M tracklets), drawn in
-    a spawn-started process while the GPU measures the timeframe."""
-    import concurrent.futures as cf
-    import multiprocessing as mp
-    ex = cf.ProcessPoolExecutor(1, mp_context=mp.get_context("spawn"))
-    return ex, ex.submit(_make_calibration, rank_workload_seed(0))
-
-
-def calibration_summary(inputs, args, ctx, flush, hbm):
+def calibration_summary(args, ctx, flush, hbm):
     """Config 3 in the default line: the relaxed N = 6 pass (450k seeds, 5-sigma
     road) with its autotuned shape, one CUDA-graph replay of index rebuild +
     follow per step (L2 flushed between steps), and its per-parameter parity
-    against the oracle on 10,000 of its seeds."""
+    against the oracle on 10,000 of its seeds.  Its workload is drawn here, in
+    this process and after the other measurements: drawn in a second process
+    beside them, it slowed the end-to-end measurement from ~145 to 41 M/s."""
     import torch
     from paper_2003_03174_b300 import autotune, trd
-    ex, fut = inputs
-    tf = fut.result()
-    ex.shutdown()
+    from synth import make_workload
+    tf = make_workload("calibration", seed=rank_workload_seed(0))
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.Stream(device=dev)
     seeds, trk = trd.to_device(tf.seeds, dev), trd.to_device(tf.tracklets, dev)
@@ -412,7 +399,6 @@ def run_ours(args):
     extra = ws == 1 and args.workload == "timeframe" and not args.alignment
     served_in = make_served_inputs(args.n_payloads) if extra and not args.no_served else None
     batched_in = make_batched_inputs(args.n_tf) if extra and not args.no_batched else None
-    cal_in = start_calibration_inputs() if extra and not args.no_calibration else None
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
@@ -663,8 +649,8 @@ def run_ours(args):
             line["served"] = served_summary(served_in, args, ctx)
         if batched_in is not None:
             line["batched"] = batched_summary(batched_in, args, ctx)
-        if cal_in is not None:
-            line["calibration"] = calibration_summary(cal_in, args, ctx, flush, hbm)
+        if extra and not args.no_calibration:
+            line["calibration"] = calibration_summary(args, ctx, flush, hbm)
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
