@@ -239,12 +239,15 @@ def test_full_calibration_parity(ctx):
     assert rep["same_path"] >= 0.99 * sel.size
 
 
-@pytest.mark.parametrize("n_hyp,shapes", [(6, ((8, 3), (32, 3), (32, 4), (8, 4))),
-                                          (3, ((4, 3), (4, 4), (8, 3), (32, 4)))])
+@pytest.mark.parametrize("n_hyp,shapes", [(6, ((8, 3), (32, 3), (32, 4), (8, 4), (8, 5), (8, 6))),
+                                          (3, ((4, 3), (4, 4), (4, 5), (4, 6), (8, 3), (8, 5), (32, 4))),
+                                          (2, ((2, 3), (2, 4), (2, 5), (2, 6), (4, 6)))])
 def test_lane_groups_do_not_change_multi_hypothesis_results(ctx, n_hyp, shapes):
-    """N hypotheses with 4 or 8 lanes per seed (lists sized to N or to the
-    group), and with a whole warp per seed: the same candidates, arithmetic
-    and order, so identical results."""
+    """N hypotheses with 2, 4 or 8 lanes per seed (lists sized to N or to the
+    group), and with a whole warp per seed, scanning by shuffled roads (3 or 4
+    blocks per SM) or by the road table with the lanes' states parked (groups
+    of 8, or 5 and 6 blocks per SM): the same candidates, arithmetic and
+    order, so identical results."""
     from paper_2003_03174_b300 import trd
     tf = make_workload("calibration", seed=9, n_seeds=4000)
     params = dict(tf.params, n_hyp=n_hyp)
