@@ -695,6 +695,21 @@ __device__ __forceinline__ bool cov_pd(const float *c)
 // A finished seed's result as one 128-byte record at its sorted position
 // (8 vector stores); k_results_gather moves it to the seed's input position.
 // Words: alpha, x, par[5], cov[15], chi2, then n_trk, n_miss, status, ids[6].
+// The one-lane kernel keeps the ids in the record (written per layer), not
+// in registers: stage all but them.
+__device__ __forceinline__ void stage_result_noids(float4 *res, int pos, const TrackState &s, float chi2, int ntrk,
+                                                   int nmiss, int status)
+{
+    float4 *r = res + 8 * static_cast<size_t>(pos);
+    r[0] = make_float4(sector_alpha_df(s.sector).hi, df_to_f(s.x), df_to_f(s.y), s.z);
+    r[1] = make_float4(s.f, s.t, s.k, s.c[0]);
+    r[2] = make_float4(s.c[1], s.c[2], s.c[3], s.c[4]);
+    r[3] = make_float4(s.c[5], s.c[6], s.c[7], s.c[8]);
+    r[4] = make_float4(s.c[9], s.c[10], s.c[11], s.c[12]);
+    r[5] = make_float4(s.c[13], s.c[14], chi2, __int_as_float(ntrk));
+    reinterpret_cast<float2 *>(r + 6)[0] = make_float2(__int_as_float(nmiss), __int_as_float(status));
+}
+
 __device__ __forceinline__ void stage_result(float4 *res, int pos, const TrackState &s, float chi2, int ntrk,
                                              int nmiss, int status, const int (&ids)[kLayers])
 {
@@ -848,7 +863,9 @@ __device__ __forceinline__ int sort_bin(float q2pt, int tf, int n_tf)
 //                             k_seed_prepare (input order)
 // Parked record (words): sector (int bits; -1 = finished), x.hi, x.lo, y.hi,
 // y.lo, z, snp, tgl, q2pt, c0..c14, input index (int bits); words 25..31
-// unused until the result is staged.
+// unused until the result is staged (the one-lane follower sets words 26..31,
+// the tracklet ids, to -1 when it takes the seed and writes each matched
+// layer's id there, so they need no registers).
 struct ParkedView {
     int32_t *bin_count;
     int32_t *counter;
@@ -1047,6 +1064,12 @@ __device__ __forceinline__ bool start_seed(int pos, int q, const SeedsView &sv, 
     L.nmiss = 0;
 #pragma unroll
     for (int k = 0; k < kLayers; ++k) L.ids[k] = -1;
+    if (G == 1) {  // the ids live in the record (words 26..31)
+        const float m1 = __int_as_float(-1);
+        float4 *r = pk.rec + 8 * static_cast<size_t>(pos);
+        reinterpret_cast<float2 *>(r + 6)[1] = make_float2(m1, m1);
+        r[7] = make_float4(m1, m1, m1, m1);
+    }
     return true;
 }
 
@@ -1128,7 +1151,10 @@ __device__ __forceinline__ bool layer_step(int pos, int l, int q, unsigned gmask
         if (q == 0) {
             TrackState b;
             load_state(sm, stride, b);
-            stage_result(res, pos, b, H.chisum, H.ntrk, H.nmiss, any_live ? TRD_ST_STOPPED : TRD_ST_PROP_FAIL, H.ids);
+            if (G == 1)
+                stage_result_noids(res, pos, b, H.chisum, H.ntrk, H.nmiss, any_live ? TRD_ST_STOPPED : TRD_ST_PROP_FAIL);
+            else
+                stage_result(res, pos, b, H.chisum, H.ntrk, H.nmiss, any_live ? TRD_ST_STOPPED : TRD_ST_PROP_FAIL, H.ids);
         }
         return true;
     }
@@ -1177,11 +1203,20 @@ __device__ __forceinline__ bool layer_step(int pos, int l, int q, unsigned gmask
         } else {
             H.nmiss += 1;
         }
+        if (G == 1) {
+            if (idl >= 0) reinterpret_cast<int *>(res + 8 * static_cast<size_t>(pos))[26 + l] = idl;
+        } else {
 #pragma unroll
-        for (int k = 0; k < kLayers; ++k) H.ids[k] = k == l ? idl : H.ids[k];
+            for (int k = 0; k < kLayers; ++k) H.ids[k] = k == l ? idl : H.ids[k];
+        }
     }
     if (l == kLayers - 1) {
-        if (q == 0) stage_result(res, pos, s, H.chisum, H.ntrk, H.nmiss, TRD_ST_OK, H.ids);
+        if (q == 0) {
+            if (G == 1)
+                stage_result_noids(res, pos, s, H.chisum, H.ntrk, H.nmiss, TRD_ST_OK);
+            else
+                stage_result(res, pos, s, H.chisum, H.ntrk, H.nmiss, TRD_ST_OK, H.ids);
+        }
         return true;
     }
     return false;
