@@ -216,6 +216,7 @@ k_index_scatter(const float *__restrict__ y, const float *__restrict__ z, const 
                 int n_tf, const int32_t *__restrict__ trig, const float *__restrict__ xs, float *__restrict__ recx)
 {
     trd::wait_prior_grid();
+    const bool wide = (reinterpret_cast<uintptr_t>(rec) & 31u) == 0;  // 32-byte stores need 32-byte alignment
     const int stride = gridDim.x * blockDim.x;
     for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += stride * kIlp) {
         // the records' contents are loaded before the position atomics, so
@@ -243,8 +244,18 @@ k_index_scatter(const float *__restrict__ y, const float *__restrict__ z, const 
         for (int u = 0; u < kIlp; ++u) {
             if (bk[u] < 0) continue;
             const int pos = at[u];
-            rec[2 * pos] = ra[u];
-            rec[2 * pos + 1] = rb[u];
+            if (wide) {
+                // the 32-byte record in one store (one L2 transaction where
+                // two 16-byte stores take two: the scattered stores and the
+                // atomics bound this kernel)
+                asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(rec + 2 * pos),
+                             "f"(ra[u].x), "f"(ra[u].y), "f"(ra[u].z), "f"(ra[u].w), "f"(rb[u].x), "f"(rb[u].y),
+                             "f"(rb[u].z), "f"(rb[u].w)
+                             : "memory");
+            } else {  // records only 16-byte aligned (a caller's buffer)
+                rec[2 * pos] = ra[u];
+                rec[2 * pos + 1] = rb[u];
+            }
             if (xs) recx[pos] = rx[u];
         }
     }

@@ -7,8 +7,10 @@ fixed array inside the library and writes the index into buffers the caller
 already owns.  This test calls it twice in a row through the C ABI, each time
 on a different timeframe, and checks every output against trd_index_build:
 identical bucket offsets, identical bucket membership, records that carry
-exactly their tracklet's values, and the same rejected count.  The file is
-named to be collected last.
+exactly their tracklet's values, and the same rejected count.  The second
+call's records start 16 bytes past a 32-byte boundary (the entry point asks
+for 16-byte alignment only; the scatter stores whole 32-byte records where
+the buffer allows it).  The file is named to be collected last.
 """
 import ctypes as C
 import math
@@ -43,7 +45,7 @@ def _with_invalid(trk, k):
     return {key: np.concatenate([trk[key], bad[key]]) for key in trk}
 
 
-def _check_one(ctx, trk_np, w, stream):
+def _check_one(ctx, trk_np, w, stream, shift=0):
     from paper_2003_03174_b300 import trd
     fn = _noalloc_fn()
     dev = trd.to_device(trk_np)
@@ -52,7 +54,10 @@ def _check_one(ctx, trk_np, w, stream):
     n_buckets = 540 * 18 * nb
     # caller-owned outputs (the test allocates them; the entry point does not)
     offsets = torch.full((n_buckets + 1,), -7, dtype=torch.int32, device="cuda")
-    records = torch.full((max(n, 1), 8), float("nan"), dtype=torch.float32, device="cuda")
+    # shift floats past the allocation's start (torch aligns it to 512 bytes)
+    buf = torch.full((max(n, 1) * 8 + shift,), float("nan"), dtype=torch.float32, device="cuda")
+    records = buf[shift:].view(-1, 8)
+    assert records.data_ptr() % 32 == 4 * shift % 32
     stats = torch.full((4,), 12345, dtype=torch.int32, device="cuda")
     ts = trd.tracklets_struct(dev)
     # the fills and copies above ran on torch's current stream; the call runs
@@ -100,7 +105,7 @@ def test_noalloc_index_matches_index_build_on_two_calls_in_a_row():
     first = _with_invalid(make_workload("timeframe", seed=31, n_seeds=60_000).tracklets, 30)
     second = make_workload("tiny", seed=32).tracklets  # smaller: stale scratch must not leak
     _check_one(ctx, first, 2.0, stream)
-    _check_one(ctx, second, 1.5, stream)
+    _check_one(ctx, second, 1.5, stream, shift=4)
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
