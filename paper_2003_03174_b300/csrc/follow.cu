@@ -829,7 +829,7 @@ constexpr int kSortBins = 128;        // momentum bins of one timeframe
 constexpr int kMaxSortBins = 1024;    // bins of a batch of timeframes (128 per timeframe up to 8)
 constexpr float kSortBinsPerUnit = 28.0f;
 constexpr int kKeyThreads = 256;
-constexpr int kKeyItems = 8;
+constexpr int kKeyItems = 2;  // seeds per thread: 391 blocks for 200k seeds (8 per thread left 98, fewer than the SMs)
 constexpr int kParkedWords = 25;  // words of a parked record
 
 // A batch of timeframes is taken timeframe by timeframe (each one's tracklet
