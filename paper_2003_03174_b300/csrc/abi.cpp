@@ -74,7 +74,7 @@ int index_alloc(trd_ctx *ctx, int32_t capacity, float y_bin_width, int32_t n_tf,
               cudaMalloc(&x->stats, sizeof(uint32_t) * 4) == cudaSuccess &&
               cudaMalloc(&x->bucket, sizeof(int32_t) * cap) == cudaSuccess &&
               cudaMalloc(&x->counts, sizeof(int32_t) * x->n_buckets) == cudaSuccess &&
-              cudaMalloc(&x->partials, sizeof(int32_t) * (x->n_partials + 1)) == cudaSuccess &&
+              cudaMalloc(&x->partials, sizeof(int32_t) * 2 * (x->n_partials + 1)) == cudaSuccess &&
               (n_tf == 1 || cudaMalloc(&x->toff, sizeof(int32_t) * (n_tf + 1)) == cudaSuccess) &&
               cudaEventCreateWithFlags(&x->built, cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {

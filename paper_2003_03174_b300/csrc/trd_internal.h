@@ -37,7 +37,7 @@ struct trd_index {
     int32_t *counts;    // [n_buckets], zero between builds (each build's scan re-zeroes them)
     bool counts_zero;   // the counters are zero for the next build (set by a build whose scan
                         // was enqueued, or by the batch before its capture)
-    int32_t *partials;  // [scan blocks + 1]
+    int32_t *partials;  // [scan blocks + 1] tile sums, then [scan blocks + 1] each tile's last counter
     int32_t n_partials;
     cudaStream_t stream;  // stream of the last build
     cudaEvent_t built;

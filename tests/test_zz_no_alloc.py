@@ -10,7 +10,8 @@ identical bucket offsets, identical bucket membership, records that carry
 exactly their tracklet's values, and the same rejected count.  The second
 call's records start 16 bytes past a 32-byte boundary (the entry point asks
 for 16-byte alignment only; the scatter stores whole 32-byte records where
-the buffer allows it).  The file is named to be collected last.
+the buffer allows it), and its offsets 4 bytes past a 16-byte boundary (the
+scan writes four offsets per 16-byte store where the buffer allows it).  The file is named to be collected last.
 """
 import ctypes as C
 import math
@@ -45,7 +46,7 @@ def _with_invalid(trk, k):
     return {key: np.concatenate([trk[key], bad[key]]) for key in trk}
 
 
-def _check_one(ctx, trk_np, w, stream, shift=0):
+def _check_one(ctx, trk_np, w, stream, shift=0, off_shift=0):
     from paper_2003_03174_b300 import trd
     fn = _noalloc_fn()
     dev = trd.to_device(trk_np)
@@ -53,7 +54,9 @@ def _check_one(ctx, trk_np, w, stream, shift=0):
     nb = int(math.ceil(np.float32(132.0) / np.float32(w)))
     n_buckets = 540 * 18 * nb
     # caller-owned outputs (the test allocates them; the entry point does not)
-    offsets = torch.full((n_buckets + 1,), -7, dtype=torch.int32, device="cuda")
+    off_buf = torch.full((n_buckets + 1 + off_shift,), -7, dtype=torch.int32, device="cuda")
+    offsets = off_buf[off_shift:]
+    assert offsets.data_ptr() % 16 == 4 * off_shift % 16
     # shift floats past the allocation's start (torch aligns it to 512 bytes)
     buf = torch.full((max(n, 1) * 8 + shift,), float("nan"), dtype=torch.float32, device="cuda")
     records = buf[shift:].view(-1, 8)
@@ -105,7 +108,7 @@ def test_noalloc_index_matches_index_build_on_two_calls_in_a_row():
     first = _with_invalid(make_workload("timeframe", seed=31, n_seeds=60_000).tracklets, 30)
     second = make_workload("tiny", seed=32).tracklets  # smaller: stale scratch must not leak
     _check_one(ctx, first, 2.0, stream)
-    _check_one(ctx, second, 1.5, stream, shift=4)
+    _check_one(ctx, second, 1.5, stream, shift=4, off_shift=1)
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
