@@ -945,6 +945,25 @@ __global__ void __launch_bounds__(256) k_seed_prepare(SeedsView sv, Params P, Re
     __shared__ int s_off[kMaxSortBins];
     static_assert(kParkedWords % 2 == 1, "an odd row length keeps the lanes' rows in distinct banks");
     __shared__ float s_rec[256 / 32][32][kParkedWords];  // each warp's records
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = sv.n;
+    // the seed's inputs and rank, loaded before the bin scan so that their
+    // latency overlaps it
+    TrackState s;
+    float alpha = 0.0f;
+    int rank = 0;
+    if (i < n) {
+        alpha = sv.alpha[i];
+        s.x = {sv.x[i], 0.0f};
+        s.y = {sv.y[i], 0.0f};
+        s.z = sv.z[i];
+        s.f = sv.snp[i];
+        s.t = sv.tgl[i];
+        s.k = sv.q2pt[i];
+#pragma unroll
+        for (int k = 0; k < 15; ++k) s.c[k] = sv.cov[k * n + i];
+        rank = pk.rank[i];
+    }
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
         const int per = pk.nbins / 32;
@@ -968,25 +987,13 @@ __global__ void __launch_bounds__(256) k_seed_prepare(SeedsView sv, Params P, Re
         }
     }
     __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int n = sv.n;
     // 0: parked, 1: ended here, 2: beyond n (no early exits: the warp writes
     // its seeds' records together below)
     int state = 2, pos = -1;
     float *t = s_rec[threadIdx.x >> 5][threadIdx.x & 31];
     if (i < n) {
-        pos = s_off[sort_bin(sv.q2pt[i], tf_of(i, sv.soff, sv.n_tf), sv.n_tf)] + pk.rank[i];
-        TrackState s;
-        const float alpha = sv.alpha[i];
-        const float sx = sv.x[i], sy = sv.y[i];
-        s.x = {sx, 0.0f};
-        s.y = {sy, 0.0f};
-        s.z = sv.z[i];
-        s.f = sv.snp[i];
-        s.t = sv.tgl[i];
-        s.k = sv.q2pt[i];
-#pragma unroll
-        for (int k = 0; k < 15; ++k) s.c[k] = sv.cov[k * n + i];
+        pos = s_off[sort_bin(s.k, tf_of(i, sv.soff, sv.n_tf), sv.n_tf)] + rank;
+        const float sx = s.x.hi, sy = s.y.hi;
         state = 1;
         if (!(fabsf(s.f) < kMaxSnp) || !cov_pd(s.c)) {
             write_seed_result(o, sv, n, i, TRD_ST_SEED_INVALID);
