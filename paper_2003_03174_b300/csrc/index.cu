@@ -32,6 +32,7 @@ constexpr int kCountThreads = 256;
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 constexpr int kScanTile = kScanThreads * kScanItems;
+constexpr int kDirectTiles = 1024;  // up to this many scan tiles, each apply block adds up the sums before it
 
 constexpr int kIlp = 4;  // tracklets per thread per loop iteration (loads issued together)
 
@@ -177,10 +178,39 @@ k_scan_reduce(const int32_t *__restrict__ in, int n, int32_t *__restrict__ parti
     }
 }
 
+// Exclusive scan of the m tile sums in place, one block: for an index of
+// more than kDirectTiles tiles (a batch of timeframes), where every apply
+// block adding up the sums before it would cost O(m^2) loads.
+__global__ void __launch_bounds__(kScanThreads) k_scan_partials(int32_t *__restrict__ p, int m)
+{
+    trd::wait_prior_grid();
+    __shared__ int s_w[kScanThreads / 32];
+    int carry = 0;
+    for (int base = 0; base < m; base += kScanTile) {
+        const int j = base + threadIdx.x * kScanItems;
+        int v[kScanItems];
+        int sum = 0;
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            v[k] = j + k < m ? p[j + k] : 0;
+            sum += v[k];
+        }
+        int total;
+        int run = carry + block_exclusive_scan(sum, s_w, &total);  // its last barrier ends the reads
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            if (j + k < m) p[j + k] = run;
+            run += v[k];
+        }
+        carry += total;
+    }
+}
+
 // out[b + 1] = exclusive prefix of the counters at b (the scatter's cursor for
 // bucket b), out[0] = 0.  A block's base is the sum of the partial sums of the
-// tiles before it (a few hundred at most; one warp adds them), so no separate
-// scan of the partials is launched.  The counters are zeroed after they are
+// tiles before it: added up here by one warp for up to kDirectTiles tiles (no
+// separate scan of the partials is launched), else already scanned by
+// k_scan_partials (scanned != 0).  The counters are zeroed after they are
 // read, so every build leaves them ready for the next one (they start zeroed).
 // Each thread takes four consecutive counters with one 16-byte load, zeroes
 // them with one 16-byte store and writes out[4t .. 4t + 3] (the prefixes at
@@ -193,14 +223,16 @@ static_assert(kScanItems == 4, "one 16-byte vector of counters per thread");
 static_assert((trd::kChambers * trd::kRowsPerStack) % 4 == 0, "bucket counts come in whole vectors");
 __global__ void __launch_bounds__(kScanThreads)
 k_scan_apply(int32_t *__restrict__ in, int n, const int32_t *__restrict__ partials,
-             const int32_t *__restrict__ lastc, int32_t *__restrict__ out)
+             const int32_t *__restrict__ lastc, int32_t *__restrict__ out, int scanned)
 {
     trd::wait_prior_grid();
     __shared__ int s_w[kScanThreads / 32];
     __shared__ int s_last[kScanThreads / 32];
     __shared__ int s_base;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (threadIdx.x < 32) {
+    if (scanned) {
+        if (threadIdx.x == 0) s_base = partials[blockIdx.x];
+    } else if (threadIdx.x < 32) {
         int b = 0;
         for (int j = threadIdx.x; j < static_cast<int>(blockIdx.x); j += 32) b += partials[j];
         for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
@@ -316,8 +348,10 @@ int index_rebuild_launch(trd_index *idx, const trd_tracklets_t *t, cudaStream_t 
     int32_t *lastc = idx->partials + idx->n_partials + 1;
     TRD_CUDA_TRY(launch_after(k_scan_reduce, dim3(m), dim3(kScanThreads), 0, s, idx->counts, idx->n_buckets,
                               idx->partials, lastc));
+    const int scanned = m > kDirectTiles;
+    if (scanned) TRD_CUDA_TRY(launch_after(k_scan_partials, dim3(1), dim3(kScanThreads), 0, s, idx->partials, m));
     TRD_CUDA_TRY(launch_after(k_scan_apply, dim3(m), dim3(kScanThreads), 0, s, idx->counts, idx->n_buckets,
-                              idx->partials, static_cast<const int32_t *>(lastc), idx->offsets));
+                              idx->partials, static_cast<const int32_t *>(lastc), idx->offsets, scanned));
     idx->counts_zero = true;  // the scan just enqueued leaves them zero
     if (n > 0) {
         TRD_CUDA_TRY(launch_after(k_index_scatter, dim3(grid_n), dim3(kCountThreads), 0, s, t->y, t->z, t->dy,
@@ -453,7 +487,8 @@ extern "C" int trd_index_build_noalloc(const trd_tracklets_t *t, float y_bin_wid
     }
     k_scan_reduce<<<m, kScanThreads, 0, s>>>(counts, n_buckets, partials, lastc);
     TRD_CUDA_TRY(cudaGetLastError());
-    k_scan_apply<<<m, kScanThreads, 0, s>>>(counts, n_buckets, partials, lastc, offsets);
+    static_assert(kNoAllocMaxPartials - 1 <= kDirectTiles, "the allocation-free build adds up tile sums directly");
+    k_scan_apply<<<m, kScanThreads, 0, s>>>(counts, n_buckets, partials, lastc, offsets, 0);
     TRD_CUDA_TRY(cudaGetLastError());
     if (n > 0) {
         k_index_scatter<<<grid_n, kCountThreads, 0, s>>>(t->y, t->z, t->dy, t->vyy, t->vzz, t->vyz, n, bucket,

@@ -121,8 +121,11 @@ def _bucket_reference(trk, w):
     return (ch * 18 + row) * nb + yb, nb
 
 
-@pytest.mark.parametrize("w", [2.0, 0.7, 0.25])
+@pytest.mark.parametrize("w", [2.0, 0.7, 0.25, 0.05])
 def test_index_buckets_are_exact(ctx, w):
+    # 0.25 and 0.05 cm make more scan tiles than the apply kernel adds up
+    # itself (1,253 and 6,265), so their tile sums go through the one-block
+    # scan (two passes of it at 0.05 cm)
     tf = make_workload("timeframe", seed=11, n_seeds=30_000)
     from paper_2003_03174_b300 import trd
     idx = ctx.index_build(trd.to_device(tf.tracklets), w)
