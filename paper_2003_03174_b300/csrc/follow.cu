@@ -1281,12 +1281,20 @@ __global__ void __launch_bounds__(256) k_results_gather(int n, ParkedView pk, Re
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int pos = i < n ? pk.inv[i] : -1;
-    // record j of the warp read by all lanes, one 128-byte line per load
+    // record j of the warp read by all lanes, one 128-byte line per load,
+    // sixteen lines in flight at a time (a seed that ended in the pre-pass
+    // reads record 0 in its place, and its row is not used)
     const float *recw = reinterpret_cast<const float *>(pk.rec);
-#pragma unroll 8
-    for (int j = 0; j < 32; ++j) {
-        const int pj = __shfl_sync(0xffffffffu, pos, j);
-        if (pj >= 0) s_res[w][j][lane] = recw[32 * static_cast<size_t>(pj) + lane];
+#pragma unroll
+    for (int j0 = 0; j0 < 32; j0 += 16) {
+        float v[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int pj = max(__shfl_sync(0xffffffffu, pos, j0 + u), 0);
+            v[u] = recw[32 * static_cast<size_t>(pj) + lane];
+        }
+#pragma unroll
+        for (int u = 0; u < 16; ++u) s_res[w][j0 + u][lane] = v[u];
     }
     __syncwarp();
     if (pos < 0) return;
