@@ -77,12 +77,12 @@ REFIT_FLOPS_PER_LAYER = 460
 # is still in L2 when the kernel ends), valid only for the source measured.
 REFIT_TRAFFIC = {"source_sha256_16": "89b8201dbc53c40e", "bytes": 39.88e6}
 # DRAM bytes (read + write) of one trd_follow call on this workload from one
-# ncu capture per kernel (k_seed_key 0.81 MB, k_seed_prepare 23.28 MB,
-# k_follow 62.66 MB, k_results_gather 26.42 MB; ncu empties the caches
+# ncu capture per kernel (k_seed_key 0.81 MB, k_seed_prepare 23.33 MB,
+# k_follow 62.63 MB, k_results_gather 26.43 MB; ncu empties the caches
 # before each kernel, so the gather's reads of the staged results, L2 hits in
 # a plain run, count here), valid only for the kernel source it was measured
 # on: reported as null once follow.cu, trd_device.cuh or track_model.cuh change.
-FOLLOW_TRAFFIC = {"source_sha256_16": "520b43f79796ab0c", "bytes": 113.17e6, "k_follow": 62.66e6}
+FOLLOW_TRAFFIC = {"source_sha256_16": "d073120fd6b09d41", "bytes": 113.20e6, "k_follow": 62.63e6}
 # DRAM bytes (read 206.49 MB + write 12.93 MB) of one k_residuals launch on the
 # 100,000-track map from one ncu capture; the 450,000-track map holds ~3 GB on
 # the device and is not captured, so the figure is reported for the captured
